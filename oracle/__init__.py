@@ -1,0 +1,12 @@
+"""Plain, slow FP64 CPU oracle for THC-driven matrix-free CP-ALS.
+
+TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's CPU
+baseline / reference arm may import this package. The library path never calls it,
+and it shares no code with the CUDA path (only the seeded input generators in
+thc_inputs/ serve both).
+
+Modules:
+  thc_cpd  - explicit tensors, matrix-free MTTKRP, factor-form loss, CP-ALS.
+  mlp      - FP64 forward/backward of the extrapolation MLP.
+  split    - bit-level reference of the BF16 / TF32 operand split.
+"""

@@ -1,0 +1,123 @@
+/*
+ * thc_cpd.h - C ABI of the GB300 (sm_103a) library for THC-driven matrix-free CP-ALS.
+ *
+ * The library fits an order-4 CP decomposition (Eq. cp4)
+ *     Gt[i,a,j,b] = sum_r lam_r A1[i,r] A2[a,r] A3[j,r] A4[b,r]
+ * to the (o,v,o,v) block of a THC-factorised two-electron integral tensor (Eq. THC)
+ *     G[i,a,j,b]  = sum_PQ Xo[i,P] Xv[a,P] Z[P,Q] Xo[j,Q] Xv[b,Q]
+ * by alternating least squares on the loss ||G - Gt||_F^2 (Eq. loss and Eq. lossF,
+ * Sec. 2.1). G is never formed: every MTTKRP runs through the THC factors.
+ *
+ * Conventions shared by every entry point
+ *   - All matrices are row-major FP64 arrays in DEVICE memory owned by the caller:
+ *       Xo  o  x Rt        Xv  v x Rt        Z  Rt x Rt (need not be symmetric)
+ *       A[0] = A1  o x R   A[1] = A2  v x R  A[2] = A3  o x R   A[3] = A4  v x R
+ *       lam  R             M  n_mode x R
+ *     A is passed as a HOST array of 4 device pointers.
+ *   - Modes are numbered 0..3 for the tensor indices (i, a, j, b); n = (o, v, o, v).
+ *   - loss = ||G - Gt||_F^2 (no 1/2), fit = 1 - ||G - Gt|| / ||G||.
+ *   - Work is enqueued on opts->stream (NULL = legacy default stream). Scalar results
+ *     (loss, fit, norms) are returned in HOST memory, so those calls synchronise the
+ *     stream before returning.
+ *   - Device workspace is allocated per call with the stream-ordered allocator
+ *     (cudaMallocAsync) and released before return. The library never frees caller
+ *     memory.
+ *   - Errors: a status code is returned and thc_cpd_last_error() gives a message
+ *     (per host thread). Arguments are validated before any work is enqueued; on an
+ *     argument error no device memory is touched. A CUDA error leaves outputs
+ *     unspecified.
+ *   - Shapes: 1 <= o, v, Rt, R and (o + v) * R, Rt * R, R * R below 2^31.
+ */
+#ifndef THC_CPD_H
+#define THC_CPD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    THC_CPD_OK = 0,
+    THC_CPD_ERR_ARG = 1,        /* null pointer, bad mode, bad option */
+    THC_CPD_ERR_SHAPE = 2,      /* non-positive or too large dimension */
+    THC_CPD_ERR_CUDA = 3,       /* a CUDA runtime or driver call failed */
+    THC_CPD_ERR_NONFINITE = 4,  /* a result came out NaN / Inf */
+    THC_CPD_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    THC_CPD_ERR_ALLOC = 6,      /* device workspace allocation failed */
+    THC_CPD_ERR_UNSUPPORTED = 7 /* option not available on this device */
+} thc_cpd_status;
+
+typedef enum {
+    THC_CPD_FP64 = 0,      /* every step in FP64 */
+    THC_CPD_BF16X3 = 1,    /* MTTKRP GEMMs on tcgen05 tensor cores with each operand split
+                              into two BF16 words (hi*hi + hi*lo + lo*hi), FP32
+                              accumulation in TMEM; Gram, solve and loss stay FP64 */
+    THC_CPD_TF32X3 = 2     /* as BF16X3 with two TF32 words per operand */
+} thc_cpd_precision;
+
+typedef struct thc_cpd_opts {
+    int precision;       /* thc_cpd_precision */
+    int loss_every;      /* mixed precision only: evaluate the FP64 loss every n sweeps
+                            (0: every sweep when tol > 0, else only after the last) */
+    void* stream;        /* cudaStream_t */
+    double* history;     /* optional HOST buffer of 2*max_sweeps doubles: (loss, fit)
+                            per sweep, NaN for sweeps whose loss was not evaluated */
+    int flags_out;       /* out: bit 0 = pseudo-inverse fallback used at least once,
+                                 bit 1 = a sweep was rolled back and replayed */
+    int reserved;
+} thc_cpd_opts;
+
+/* ||G||_F^2 = sum_PQ Z[P,Q] (S Z S)[P,Q], S = (Xo^T Xo) o (Xv^T Xv): the THC norm in
+ * O(Rt^3), the contraction pattern of the J term of Eq. thc_Ej. Result in *normG2_host. */
+thc_cpd_status thc_cpd_thc_norm2(int o, int v, int Rt,
+                                 const double* Xo, const double* Xv, const double* Z,
+                                 double* normG2_host, const thc_cpd_opts* opts);
+
+/* Matrix-free MTTKRP of mode `mode` (0..3), the gradient building block of Eq. lossF:
+ *   M1 = Xo (W2 o (Z   (W3 o W4)))     M2 = Xv (W1 o (Z   (W3 o W4)))
+ *   M3 = Xo (W4 o (Z^T (W1 o W2)))     M4 = Xv (W3 o (Z^T (W1 o W2)))
+ * with W_k = X_k^T A_k. lam is not applied. M (device, n_mode x R) is overwritten.
+ * opts->precision selects FP64 or a split tensor-core path. */
+thc_cpd_status thc_cpd_mttkrp(int o, int v, int Rt, int R,
+                              const double* Xo, const double* Xv, const double* Z,
+                              const double* const A[4], int mode, double* M,
+                              const thc_cpd_opts* opts);
+
+/* Loss in factor form (Eq. lossF): ||G||^2 - 2 <G, Gt> + lam^T (G1 o G2 o G3 o G4) lam,
+ * evaluated in FP64 for every precision. lam may be NULL (all ones). normG2 <= 0 makes
+ * the call compute ||G||^2 itself. Outputs in host memory (either may be NULL). */
+thc_cpd_status thc_cpd_loss(int o, int v, int Rt, int R,
+                            const double* Xo, const double* Xv, const double* Z,
+                            const double* const A[4], const double* lam, double normG2,
+                            double* loss_host, double* fit_host, const thc_cpd_opts* opts);
+
+/* One ALS sweep: for modes 0..3 in order, M_k by the matrix-free MTTKRP, H_k the
+ * Hadamard product of the other three Gram matrices, A_k <- M_k H_k^{-1} by Cholesky
+ * (pseudo-inverse from a symmetric eigendecomposition if a pivot is <= R*eps*max H_ii),
+ * then lam_r = ||A_k[:,r]||, A_k[:,r] /= lam_r. A and lam (device) are updated in place;
+ * the incoming lam is absorbed by the first update. Loss and fit of the result are
+ * returned (FP64). normG2 <= 0 makes the call compute ||G||^2. */
+thc_cpd_status thc_cpd_als_sweep(int o, int v, int Rt, int R,
+                                 const double* Xo, const double* Xv, const double* Z,
+                                 double* const A[4], double* lam, double normG2,
+                                 double* loss_host, double* fit_host, thc_cpd_opts* opts);
+
+/* CP-ALS: up to max_sweeps sweeps, stopping after sweep s when |fit_s - fit_{s-1}| < tol
+ * (tol <= 0: run all sweeps). A holds the start point on entry and the normalised
+ * factors on exit; lam receives the weights. sweeps_done, loss_host and fit_host (host,
+ * may be NULL) receive the sweep count and the final FP64 loss and fit. */
+thc_cpd_status thc_cpd_als(int o, int v, int Rt, int R,
+                           const double* Xo, const double* Xv, const double* Z,
+                           double* const A[4], double* lam, int max_sweeps, double tol,
+                           int* sweeps_done, double* loss_host, double* fit_host,
+                           thc_cpd_opts* opts);
+
+/* Message for the last non-OK status returned on this host thread. */
+const char* thc_cpd_last_error(void);
+
+/* Library version string. */
+const char* thc_cpd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THC_CPD_H */

@@ -1,0 +1,82 @@
+"""ctypes loader for the in-tree libthc_cpd.so (the C ABI of include/thc_cpd.h).
+
+There is no fallback: if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libthc_cpd.so")
+
+OK, ERR_ARG, ERR_SHAPE, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_ALLOC, ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
+                5: "ERR_TIMEOUT", 6: "ERR_ALLOC", 7: "ERR_UNSUPPORTED"}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+
+# every symbol include/thc_cpd.h declares
+EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
+           "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version")
+
+
+class ThcCpdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int),
+                ("loss_every", ctypes.c_int),
+                ("stream", ctypes.c_void_p),
+                ("history", ctypes.POINTER(ctypes.c_double)),
+                ("flags_out", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+P = ctypes.c_void_p
+D = ctypes.c_double
+I = ctypes.c_int
+DP = ctypes.POINTER(ctypes.c_double)
+IP = ctypes.POINTER(ctypes.c_int)
+PTR4 = ctypes.c_void_p * 4
+OPTS = ctypes.POINTER(Opts)
+
+_SIGS = {
+    "thc_cpd_thc_norm2": [I, I, I, P, P, P, DP, OPTS],
+    "thc_cpd_mttkrp": [I, I, I, I, P, P, P, PTR4, I, P, OPTS],
+    "thc_cpd_loss": [I, I, I, I, P, P, P, PTR4, P, D, DP, DP, OPTS],
+    "thc_cpd_als_sweep": [I, I, I, I, P, P, P, PTR4, P, D, DP, DP, OPTS],
+    "thc_cpd_als": [I, I, I, I, P, P, P, PTR4, P, I, D, IP, DP, DP, OPTS],
+}
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load (once) and return the library; raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ThcCpdError(ERR_UNSUPPORTED, f"{p} is not built; run __graft_entry__.build() or "
+                                           "python -m paper_2502_17683_gb300.build")
+    lib = ctypes.CDLL(p)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.thc_cpd_last_error.restype = ctypes.c_char_p
+    lib.thc_cpd_last_error.argtypes = []
+    lib.thc_cpd_version.restype = ctypes.c_char_p
+    lib.thc_cpd_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def check(status: int) -> None:
+    if status != OK:
+        msg = load().thc_cpd_last_error().decode(errors="replace")
+        raise ThcCpdError(status, msg)

@@ -1,0 +1,125 @@
+"""Thin Python binding of the C ABI (include/thc_cpd.h) over torch CUDA tensors.
+
+Functions carry the C names and only marshal arguments: every step of the method runs
+in the library's CUDA kernels. Tensors must be contiguous float64 tensors on one CUDA
+device; factor tensors are updated in place where the C ABI says so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import PRECISIONS, PTR4, Opts, ThcCpdError, check, load, ERR_ARG
+
+__all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
+           "thc_cpd_als", "thc_cpd_version", "Opts"]
+
+
+def _dev(t: torch.Tensor, name: str, shape=None) -> int:
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise ThcCpdError(ERR_ARG, f"{name} must be a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ThcCpdError(ERR_ARG, f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ThcCpdError(ERR_ARG, f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _opts(precision="fp64", stream=None, loss_every=0, history=None) -> Opts:
+    o = Opts()
+    if isinstance(precision, str):
+        if precision not in PRECISIONS:
+            raise ThcCpdError(ERR_ARG, f"unknown precision {precision!r}")
+        precision = PRECISIONS[precision]
+    o.precision = int(precision)
+    o.loss_every = int(loss_every)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    o.history = history
+    return o
+
+
+def _dims(Xo, Xv, Z):
+    o, Rt = Xo.shape
+    v = Xv.shape[0]
+    return o, v, Rt
+
+
+def _ptr4(A, dims, R):
+    if len(A) != 4:
+        raise ThcCpdError(ERR_ARG, "A must hold four factor matrices")
+    return PTR4(*[_dev(a, f"A[{k}]", (dims[k], R)) for k, a in enumerate(A)])
+
+
+def thc_cpd_version() -> str:
+    return load().thc_cpd_version().decode()
+
+
+def thc_cpd_thc_norm2(Xo, Xv, Z, stream=None) -> float:
+    o, v, Rt = _dims(Xo, Xv, Z)
+    out = ctypes.c_double()
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_thc_norm2(o, v, Rt, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                                   _dev(Z, "Z", (Rt, Rt)), ctypes.byref(out), ctypes.byref(opts)))
+    return out.value
+
+
+def thc_cpd_mttkrp(Xo, Xv, Z, A, mode: int, M=None, precision="fp64", stream=None):
+    o, v, Rt = _dims(Xo, Xv, Z)
+    R = A[0].shape[1]
+    dims = (o, v, o, v)
+    if M is None:
+        M = torch.empty(dims[mode] if 0 <= mode < 4 else 1, R, dtype=torch.float64, device=Xo.device)
+    opts = _opts(precision, stream)
+    check(load().thc_cpd_mttkrp(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                                _dev(Z, "Z", (Rt, Rt)), _ptr4(A, dims, R), int(mode),
+                                _dev(M, "M"), ctypes.byref(opts)))
+    return M
+
+
+def thc_cpd_loss(Xo, Xv, Z, A, lam=None, normG2: float = 0.0, stream=None):
+    o, v, Rt = _dims(Xo, Xv, Z)
+    R = A[0].shape[1]
+    loss, fit = ctypes.c_double(), ctypes.c_double()
+    opts = _opts("fp64", stream)
+    lp = None if lam is None else _dev(lam, "lam", (R,))
+    check(load().thc_cpd_loss(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                              _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R), lp,
+                              float(normG2), ctypes.byref(loss), ctypes.byref(fit),
+                              ctypes.byref(opts)))
+    return loss.value, fit.value
+
+
+def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", stream=None):
+    o, v, Rt = _dims(Xo, Xv, Z)
+    R = A[0].shape[1]
+    loss, fit = ctypes.c_double(), ctypes.c_double()
+    opts = _opts(precision, stream)
+    check(load().thc_cpd_als_sweep(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                                   _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R),
+                                   _dev(lam, "lam", (R,)), float(normG2), ctypes.byref(loss),
+                                   ctypes.byref(fit), ctypes.byref(opts)))
+    return dict(loss=loss.value, fit=fit.value, flags=opts.flags_out)
+
+
+def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision="fp64",
+                stream=None, loss_every: int = 0, history: bool = False):
+    o, v, Rt = _dims(Xo, Xv, Z)
+    R = A[0].shape[1]
+    loss, fit, done = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    hist = (ctypes.c_double * max(1, 2 * max_sweeps))() if history else None
+    opts = _opts(precision, stream, loss_every,
+                 ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None)
+    check(load().thc_cpd_als(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                             _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R),
+                             _dev(lam, "lam", (R,)), int(max_sweeps), float(tol),
+                             ctypes.byref(done), ctypes.byref(loss), ctypes.byref(fit),
+                             ctypes.byref(opts)))
+    out = dict(sweeps=done.value, loss=loss.value, fit=fit.value, flags=opts.flags_out)
+    if hist is not None:
+        h = list(hist)[: 2 * done.value]
+        out["losses"] = h[0::2]
+        out["fits"] = h[1::2]
+    return out

@@ -1,0 +1,553 @@
+// C ABI of the THC-CPD library: argument checks, workspace, and the host-side order of
+// the kernels of one ALS sweep (textbook CP-ALS on Eq. lossF, Sec. 2.1).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+
+#include "thc_cpd.h"
+#include "f64.cuh"
+#include "mixed.cuh"
+
+namespace {
+
+using namespace thc;
+
+thread_local std::string g_err;
+
+thc_cpd_status set_err(thc_cpd_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return set_err(THC_CPD_ERR_CUDA, "%s failed at %s:%d: %s", #call, __FILE__,     \
+                           __LINE__, cudaGetErrorString(e_));                               \
+    } while (0)
+
+#define CKS(expr)                              \
+    do {                                       \
+        thc_cpd_status s_ = (expr);            \
+        if (s_ != THC_CPD_OK) return s_;       \
+    } while (0)
+
+struct Shape {
+    int o, v, Rt, R;
+    int n[4];
+    int nmax;
+};
+
+thc_cpd_status check_shape(int o, int v, int Rt, int R, Shape* s) {
+    if (o < 1 || v < 1 || Rt < 1 || R < 1)
+        return set_err(THC_CPD_ERR_SHAPE, "dimensions must be >= 1 (o=%d v=%d Rt=%d R=%d)", o, v, Rt, R);
+    const long lim = 0x7fffffffL;
+    if ((long)(o + v) * R >= lim || (long)Rt * R >= lim || (long)R * R >= lim ||
+        (long)Rt * Rt >= lim || (long)(R + std::max(o, v)) * R >= lim)
+        return set_err(THC_CPD_ERR_SHAPE, "dimensions too large (o=%d v=%d Rt=%d R=%d)", o, v, Rt, R);
+    s->o = o;
+    s->v = v;
+    s->Rt = Rt;
+    s->R = R;
+    s->n[0] = o;
+    s->n[1] = v;
+    s->n[2] = o;
+    s->n[3] = v;
+    s->nmax = std::max(o, v);
+    return THC_CPD_OK;
+}
+
+thc_cpd_status check_ptrs(const double* Xo, const double* Xv, const double* Z,
+                          const double* const* A) {
+    if (!Xo || !Xv || !Z) return set_err(THC_CPD_ERR_ARG, "Xo, Xv and Z must be non-null");
+    if (A) {
+        for (int k = 0; k < 4; ++k)
+            if (!A[k]) return set_err(THC_CPD_ERR_ARG, "A[%d] is null", k);
+    }
+    return THC_CPD_OK;
+}
+
+thc_cpd_status check_prec(const thc_cpd_opts* opts) {
+    const int p = opts ? opts->precision : THC_CPD_FP64;
+    if (p != THC_CPD_FP64 && p != THC_CPD_BF16X3 && p != THC_CPD_TF32X3)
+        return set_err(THC_CPD_ERR_ARG, "unknown precision %d", p);
+    if (p != THC_CPD_FP64 && !mixed_supported())
+        return set_err(THC_CPD_ERR_UNSUPPORTED, "split tensor-core precision needs an sm_103 device");
+    return THC_CPD_OK;
+}
+
+cudaStream_t stream_of(const thc_cpd_opts* o) {
+    return o ? (cudaStream_t)o->stream : (cudaStream_t)0;
+}
+
+// Pinned host copy of the device scalars (one per host thread).
+DevScalars* host_scalars() {
+    thread_local DevScalars* h = nullptr;
+    if (!h) {
+        if (cudaMallocHost((void**)&h, sizeof(DevScalars)) != cudaSuccess) h = nullptr;
+    }
+    return h;
+}
+
+// Everything one call needs on the device, carved from a single stream-ordered block.
+struct Ctx {
+    Shape s;
+    const double* X[4];
+    const double* Z;
+    cudaStream_t st;
+    int prec;
+    void* block = nullptr;
+    double* W[4] = {};
+    double* G[4] = {};
+    double* Y = nullptr;
+    double* Haug = nullptr;
+    double* LinvD = nullptr;
+    double* part = nullptr;
+    size_t part_cap = 0;
+    double* red = nullptr;
+    double* ones = nullptr;
+    DevScalars* sc = nullptr;
+    DevScalars* sc_snap = nullptr;
+    double* Asnap[4] = {};
+    double* lamsnap = nullptr;
+    // ||G||^2 set-up
+    double* S = nullptr;
+    double* T = nullptr;
+    double* U = nullptr;
+    // checked replay (pseudo-inverse) buffers
+    double* Hsave = nullptr;
+    double* Msave = nullptr;
+    double* pV = nullptr;
+    double* pw = nullptr;
+    double* pT = nullptr;
+    void* safe_block = nullptr;
+    MixedWs mx;
+
+    ~Ctx() {
+        if (safe_block) cudaFreeAsync(safe_block, st);
+        if (block) cudaFreeAsync(block, st);
+    }
+};
+
+enum : unsigned { NEED_ALS = 1, NEED_NORM = 2, NEED_SAFE = 4 };
+
+thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* Xv,
+                        const double* Z, const thc_cpd_opts* opts, unsigned need) {
+    c.s = s;
+    c.X[0] = Xo;
+    c.X[1] = Xv;
+    c.X[2] = Xo;
+    c.X[3] = Xv;
+    c.Z = Z;
+    c.st = stream_of(opts);
+    c.prec = opts ? opts->precision : THC_CPD_FP64;
+    const int Rt = s.Rt, R = s.R, nmax = s.nmax;
+    size_t pc = 0;
+    for (int k = 0; k < 2; ++k) {
+        const int n = s.n[k];
+        pc = std::max(pc, dgemm_part_need(Rt, R, n));
+        pc = std::max(pc, dgemm_part_need(n, R, Rt));
+        pc = std::max(pc, dgemm_part_need(R, R, n));
+        pc = std::max(pc, dgemm_part_need(Rt, Rt, n));
+    }
+    pc = std::max(pc, dgemm_part_need(Rt, R, Rt));
+    if (need & NEED_NORM) pc = std::max(pc, dgemm_part_need(Rt, Rt, Rt));
+    if (need & NEED_SAFE) pc = std::max(pc, dgemm_part_need(nmax, R, R));
+    c.part_cap = pc;
+    size_t bytes = 0;
+    const size_t RtR = (size_t)Rt * R, RR = (size_t)R * R;
+    bytes += 4 * Arena::need<double>(RtR);                 // W
+    bytes += 4 * Arena::need<double>(RR);                  // G
+    bytes += Arena::need<double>(RtR);                     // Y
+    bytes += Arena::need<double>((size_t)(R + nmax) * R);  // Haug
+    bytes += Arena::need<double>((size_t)cdiv(R, 32) * 1024);
+    bytes += Arena::need<double>(pc);
+    bytes += Arena::need<double>(loss_red_need() + 2 * kNumSM * 2);
+    bytes += Arena::need<double>(R);
+    bytes += 2 * Arena::need<DevScalars>(1);
+    if (need & NEED_ALS) {
+        bytes += 2 * Arena::need<double>((size_t)s.o * R) + 2 * Arena::need<double>((size_t)s.v * R);
+        bytes += Arena::need<double>(R);
+    }
+    if (need & NEED_NORM) bytes += 3 * Arena::need<double>((size_t)Rt * Rt);
+    const bool mixed = c.prec != THC_CPD_FP64;
+    if (mixed) bytes += mixed_ws_bytes(s.o, s.v, Rt, R);
+    CK(cudaMallocAsync(&c.block, bytes, c.st));
+    Arena ar;
+    ar.base = (char*)c.block;
+    ar.cap = bytes;
+    for (int k = 0; k < 4; ++k) c.W[k] = ar.take<double>(RtR);
+    for (int k = 0; k < 4; ++k) c.G[k] = ar.take<double>(RR);
+    c.Y = ar.take<double>(RtR);
+    c.Haug = ar.take<double>((size_t)(R + nmax) * R);
+    c.LinvD = ar.take<double>((size_t)cdiv(R, 32) * 1024);
+    c.part = ar.take<double>(pc);
+    c.red = ar.take<double>(loss_red_need() + 2 * kNumSM * 2);
+    c.ones = ar.take<double>(R);
+    c.sc = ar.take<DevScalars>(1);
+    c.sc_snap = ar.take<DevScalars>(1);
+    if (need & NEED_ALS) {
+        for (int k = 0; k < 4; ++k) c.Asnap[k] = ar.take<double>((size_t)s.n[k] * R);
+        c.lamsnap = ar.take<double>(R);
+    }
+    if (need & NEED_NORM) {
+        c.S = ar.take<double>((size_t)Rt * Rt);
+        c.T = ar.take<double>((size_t)Rt * Rt);
+        c.U = ar.take<double>((size_t)Rt * Rt);
+    }
+    if (mixed) mixed_ws_carve(c.mx, ar, s.o, s.v, Rt, R);
+    fill(c.st, c.ones, R, 1.0);
+    CK(cudaGetLastError());
+    return THC_CPD_OK;
+}
+
+thc_cpd_status ctx_safe_buffers(Ctx& c) {
+    if (c.Hsave) return THC_CPD_OK;
+    const int R = c.s.R, nmax = c.s.nmax;
+    const size_t RR = (size_t)R * R;
+    const size_t TT = std::max(RR, (size_t)nmax * R);  // pinv scratch T is n x R
+    size_t bytes = 2 * Arena::need<double>(RR) + Arena::need<double>(TT) +
+                   2 * Arena::need<double>((size_t)nmax * R) + Arena::need<double>(R);
+    void* p = nullptr;
+    CK(cudaMallocAsync(&p, bytes, c.st));
+    Arena ar;
+    ar.base = (char*)p;
+    ar.cap = bytes;
+    c.Hsave = ar.take<double>(RR);
+    c.pV = ar.take<double>(RR);
+    c.pT = ar.take<double>(TT);
+    c.Msave = ar.take<double>((size_t)nmax * R);
+    (void)ar.take<double>((size_t)nmax * R);
+    c.pw = ar.take<double>(R);
+    c.safe_block = p;
+    return THC_CPD_OK;
+}
+
+// ---- building blocks -----------------------------------------------------------------
+void compute_normG2(Ctx& c) {
+    const int o = c.s.o, v = c.s.v, Rt = c.s.Rt;
+    // S = (Xo^T Xo) o (Xv^T Xv); U = S Z S; ||G||^2 = sum Z o U
+    dgemm(c.st, true, Rt, Rt, o, c.X[0], Rt, c.X[0], nullptr, Rt, c.T, Rt, nullptr, true, c.part, c.part_cap);
+    dgemm(c.st, true, Rt, Rt, v, c.X[1], Rt, c.X[1], nullptr, Rt, c.S, Rt, c.T, true, c.part, c.part_cap);
+    dgemm(c.st, false, Rt, Rt, Rt, c.S, Rt, c.Z, nullptr, Rt, c.T, Rt, nullptr, false, c.part, c.part_cap);
+    dgemm(c.st, false, Rt, Rt, Rt, c.T, Rt, c.S, nullptr, Rt, c.U, Rt, nullptr, false, c.part, c.part_cap);
+    sum_hadamard_normG2(c.st, (long)Rt * Rt, c.Z, c.U, c.red, c.sc);
+}
+
+void project_fp64(Ctx& c, int k, const double* Ak) {
+    dgemm(c.st, true, c.s.Rt, c.s.R, c.s.n[k], c.X[k], c.s.Rt, Ak, nullptr, c.s.R, c.W[k], c.s.R,
+          nullptr, false, c.part, c.part_cap);
+}
+
+void gram_fp64(Ctx& c, int k, const double* Ak) {
+    dgemm(c.st, true, c.s.R, c.s.R, c.s.n[k], Ak, c.s.R, Ak, nullptr, c.s.R, c.G[k], c.s.R, nullptr,
+          true, c.part, c.part_cap);
+}
+
+// Y = Z (W3 o W4) for modes 0,1 and Y = Z^T (W1 o W2) for modes 2,3
+void zgemm_fp64(Ctx& c, int half) {
+    const int Rt = c.s.Rt, R = c.s.R;
+    if (half == 0)
+        dgemm(c.st, false, Rt, R, Rt, c.Z, Rt, c.W[2], c.W[3], R, c.Y, R, nullptr, false, c.part, c.part_cap);
+    else
+        dgemm(c.st, true, Rt, R, Rt, c.Z, Rt, c.W[0], c.W[1], R, c.Y, R, nullptr, false, c.part, c.part_cap);
+}
+
+int partner_of(int k) { return k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 3 : 2; }
+
+// M_k = X_k (W_partner o Y)
+void backproject_fp64(Ctx& c, int k, double* M) {
+    dgemm(c.st, false, c.s.n[k], c.s.R, c.s.Rt, c.X[k], c.s.Rt, c.W[partner_of(k)], c.Y, c.s.R, M,
+          c.s.R, nullptr, false, c.part, c.part_cap);
+}
+
+void others(int k, int* a, int* b, int* d) {
+    int t[3], j = 0;
+    for (int m = 0; m < 4; ++m)
+        if (m != k) t[j++] = m;
+    *a = t[0];
+    *b = t[1];
+    *d = t[2];
+}
+
+// W_k and G_k for every mode from the current factors (start of a run / after rollback)
+void refresh_state(Ctx& c, const double* const A[4]) {
+    for (int k = 0; k < 4; ++k) {
+        if (c.prec == THC_CPD_FP64)
+            project_fp64(c, k, A[k]);
+        else
+            mixed_project(c.mx, c.st, c.s.o, c.s.v, c.s.Rt, c.s.R, k, A[k], c.W, nullptr, c.prec);
+        gram_fp64(c, k, A[k]);
+    }
+}
+
+// One mode update. M_k is formed in the Haug rows; returns with A[k], lam, G_k, W_k new.
+thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool safe,
+                           int* used_pinv) {
+    const int R = c.s.R, n = c.s.n[k];
+    double* Mrows = c.Haug + (size_t)R * R;
+    if (c.prec == THC_CPD_FP64)
+        backproject_fp64(c, k, safe ? c.Msave : Mrows);
+    else
+        mixed_backproject(c.mx, c.st, c.s.o, c.s.v, c.s.Rt, R, k, safe ? c.Msave : Mrows, c.prec);
+    int a, b, d;
+    others(k, &a, &b, &d);
+    hadamard3(c.st, R, c.G[a], c.G[b], c.G[d], safe ? c.Hsave : c.Haug, c.sc);
+    if (safe) {
+        CK(cudaMemcpyAsync(Mrows, c.Msave, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, c.st));
+        CK(cudaMemcpyAsync(c.Haug, c.Hsave, sizeof(double) * R * R, cudaMemcpyDeviceToDevice, c.st));
+    }
+    chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.sc, k);
+    if (safe) {
+        DevScalars* h = host_scalars();
+        if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
+        CK(cudaMemcpyAsync(h, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.st));
+        CK(cudaStreamSynchronize(c.st));
+        if (h->fail_mask & (1 << k)) {
+            int sweeps = 0;
+            CK(pinv_solve(c.st, R, n, c.Hsave, c.Msave, A[k], c.pV, c.pw, c.pT, &sweeps));
+            *used_pinv = 1;
+            int zero = 0;
+            CK(cudaMemcpyAsync(&c.sc->fail_mask, &zero, sizeof(int), cudaMemcpyHostToDevice, c.st));
+            CK(cudaStreamSynchronize(c.st));
+        }
+    }
+    normalise_columns(c.st, n, R, A[k], lam);
+    gram_fp64(c, k, A[k]);
+    if (c.prec == THC_CPD_FP64)
+        project_fp64(c, k, A[k]);
+    else
+        mixed_project(c.mx, c.st, c.s.o, c.s.v, c.s.Rt, R, k, A[k], c.W, c.Y, c.prec);
+    CK(cudaGetLastError());
+    return THC_CPD_OK;
+}
+
+// One sweep over modes 0..3 (+ the FP64 loss when eval_loss).
+thc_cpd_status sweep(Ctx& c, double* const A[4], double* lam, bool safe, bool eval_loss,
+                     double tol, int* used_pinv) {
+    for (int k = 0; k < 4; ++k) {
+        if (k == 0 || k == 2) {
+            if (c.prec == THC_CPD_FP64)
+                zgemm_fp64(c, k / 2);
+            else
+                mixed_zgemm(c.mx, c.st, c.s.Rt, c.s.R, k / 2, c.W, c.prec);
+        }
+        CKS(mode_update(c, A, lam, k, safe, used_pinv));
+    }
+    if (eval_loss) {
+        if (c.prec == THC_CPD_FP64) {
+            loss_eval(c.st, c.s.Rt, c.s.R, c.Y, c.W[2], c.W[3], lam, c.G, c.red, c.sc, tol);
+        } else {
+            // the loss is a cancelling difference: FP64 projections and Z product
+            for (int k = 0; k < 4; ++k) project_fp64(c, k, A[k]);
+            zgemm_fp64(c, 1);
+            loss_eval(c.st, c.s.Rt, c.s.R, c.Y, c.W[2], c.W[3], lam, c.G, c.red, c.sc, tol);
+        }
+    }
+    CK(cudaGetLastError());
+    return THC_CPD_OK;
+}
+
+thc_cpd_status read_scalars(Ctx& c, DevScalars* out) {
+    DevScalars* h = host_scalars();
+    if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
+    CK(cudaMemcpyAsync(h, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    *out = *h;
+    return THC_CPD_OK;
+}
+
+thc_cpd_status obtain_norm(Ctx& c, double normG2, double* out) {
+    if (normG2 > 0.0) {
+        scalars_init(c.st, c.sc, normG2);
+        *out = normG2;
+        return THC_CPD_OK;
+    }
+    scalars_init(c.st, c.sc, 0.0);
+    compute_normG2(c);
+    DevScalars h;
+    CKS(read_scalars(c, &h));
+    *out = h.normG2;
+    if (!isfinite(h.normG2) || !(h.normG2 > 0.0))
+        return set_err(THC_CPD_ERR_NONFINITE, "||G||^2 = %g is not a positive finite number", h.normG2);
+    return THC_CPD_OK;
+}
+
+// The ALS driver shared by thc_cpd_als and thc_cpd_als_sweep.
+thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                       const double* Z, double* const A[4], double* lam, int max_sweeps,
+                       double tol, double normG2, int* sweeps_done, double* loss_host,
+                       double* fit_host, thc_cpd_opts* opts) {
+    Shape s;
+    CKS(check_shape(o, v, Rt, R, &s));
+    CKS(check_ptrs(Xo, Xv, Z, A));
+    CKS(check_prec(opts));
+    if (!lam) return set_err(THC_CPD_ERR_ARG, "lam must be non-null");
+    if (max_sweeps < 0) return set_err(THC_CPD_ERR_ARG, "max_sweeps must be >= 0");
+    if (opts) opts->flags_out = 0;
+    Ctx c;
+    CKS(ctx_init(c, s, Xo, Xv, Z, opts, NEED_ALS | (normG2 > 0.0 ? 0u : NEED_NORM)));
+    double nG2 = 0.0;
+    CKS(obtain_norm(c, normG2, &nG2));
+    refresh_state(c, A);
+    const int loss_every = (opts && opts->loss_every > 0) ? opts->loss_every : 0;
+    int flags = 0;
+    int done_sweeps = 0;
+    DevScalars h;
+    h.loss = nan("");
+    h.fit = nan("");
+    for (int sw = 1; sw <= max_sweeps; ++sw) {
+        bool eval = true;
+        if (c.prec != THC_CPD_FP64) {
+            if (loss_every > 0)
+                eval = (sw % loss_every == 0) || sw == max_sweeps;
+            else
+                eval = tol > 0.0 || sw == max_sweeps;
+        }
+        for (int k = 0; k < 4; ++k)
+            CK(cudaMemcpyAsync(c.Asnap[k], A[k], sizeof(double) * s.n[k] * R,
+                               cudaMemcpyDeviceToDevice, c.st));
+        CK(cudaMemcpyAsync(c.lamsnap, lam, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
+        CK(cudaMemcpyAsync(c.sc_snap, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+        int used = 0;
+        CKS(sweep(c, A, lam, false, eval, tol, &used));
+        CKS(read_scalars(c, &h));
+        if (h.fail_mask) {
+            // a Cholesky pivot failed somewhere in this sweep: roll back and replay the
+            // sweep with a host check after every factorisation
+            for (int k = 0; k < 4; ++k)
+                CK(cudaMemcpyAsync(A[k], c.Asnap[k], sizeof(double) * s.n[k] * R,
+                                   cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(lam, c.lamsnap, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(c.sc, c.sc_snap, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+            refresh_state(c, A);
+            CKS(ctx_safe_buffers(c));
+            CKS(sweep(c, A, lam, true, eval, tol, &used));
+            CKS(read_scalars(c, &h));
+            flags |= 2;
+        }
+        if (used) flags |= 1;
+        done_sweeps = sw;
+        if (opts && opts->history) {
+            opts->history[2 * (sw - 1)] = eval ? h.loss : nan("");
+            opts->history[2 * (sw - 1) + 1] = eval ? h.fit : nan("");
+        }
+        if (eval && (h.nonfinite || !isfinite(h.loss))) {
+            if (opts) opts->flags_out = flags;
+            if (sweeps_done) *sweeps_done = done_sweeps;
+            return set_err(THC_CPD_ERR_NONFINITE, "loss became non-finite at sweep %d", sw);
+        }
+        if (h.done) break;
+    }
+    if (opts) opts->flags_out = flags;
+    if (sweeps_done) *sweeps_done = done_sweeps;
+    if (loss_host) *loss_host = h.loss;
+    if (fit_host) *fit_host = h.fit;
+    CK(cudaStreamSynchronize(c.st));
+    return THC_CPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* thc_cpd_last_error(void) { return g_err.c_str(); }
+
+const char* thc_cpd_version(void) { return "thc_cpd 0.1 (sm_103a)"; }
+
+thc_cpd_status thc_cpd_thc_norm2(int o, int v, int Rt, const double* Xo, const double* Xv,
+                                 const double* Z, double* normG2_host, const thc_cpd_opts* opts) {
+    Shape s;
+    CKS(check_shape(o, v, Rt, 1, &s));
+    CKS(check_ptrs(Xo, Xv, Z, nullptr));
+    if (!normG2_host) return set_err(THC_CPD_ERR_ARG, "normG2_host must be non-null");
+    thc_cpd_opts o2 = opts ? *opts : thc_cpd_opts{};
+    o2.precision = THC_CPD_FP64;
+    Ctx c;
+    CKS(ctx_init(c, s, Xo, Xv, Z, &o2, NEED_NORM));
+    return obtain_norm(c, 0.0, normG2_host);
+}
+
+thc_cpd_status thc_cpd_mttkrp(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                              const double* Z, const double* const A[4], int mode, double* M,
+                              const thc_cpd_opts* opts) {
+    Shape s;
+    CKS(check_shape(o, v, Rt, R, &s));
+    CKS(check_ptrs(Xo, Xv, Z, A));
+    CKS(check_prec(opts));
+    if (mode < 0 || mode > 3) return set_err(THC_CPD_ERR_ARG, "mode must be 0..3, got %d", mode);
+    if (!M) return set_err(THC_CPD_ERR_ARG, "M must be non-null");
+    Ctx c;
+    CKS(ctx_init(c, s, Xo, Xv, Z, opts, 0));
+    if (c.prec == THC_CPD_FP64) {
+        for (int k = 0; k < 4; ++k)
+            if (k != mode) project_fp64(c, k, A[k]);
+        zgemm_fp64(c, mode / 2);
+        backproject_fp64(c, mode, M);
+    } else {
+        for (int k = 0; k < 4; ++k)
+            if (k != mode) mixed_project(c.mx, c.st, o, v, Rt, R, k, A[k], c.W, nullptr, c.prec);
+        // the projection epilogues above produce the Hadamard operands of this mode
+        mixed_zgemm(c.mx, c.st, Rt, R, mode / 2, c.W, c.prec);
+        if (mode == 1 || mode == 3) {
+            // partner product for the second mode of the half: W_partner o Y
+            mixed_partner(c.mx, c.st, Rt, R, mode, c.W, c.prec);
+        }
+        mixed_backproject(c.mx, c.st, o, v, Rt, R, mode, M, c.prec);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c.st));
+    return THC_CPD_OK;
+}
+
+thc_cpd_status thc_cpd_loss(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                            const double* Z, const double* const A[4], const double* lam,
+                            double normG2, double* loss_host, double* fit_host,
+                            const thc_cpd_opts* opts) {
+    Shape s;
+    CKS(check_shape(o, v, Rt, R, &s));
+    CKS(check_ptrs(Xo, Xv, Z, A));
+    thc_cpd_opts o2 = opts ? *opts : thc_cpd_opts{};
+    o2.precision = THC_CPD_FP64;  // the loss is always evaluated in FP64
+    Ctx c;
+    CKS(ctx_init(c, s, Xo, Xv, Z, &o2, normG2 > 0.0 ? 0u : NEED_NORM));
+    double nG2;
+    CKS(obtain_norm(c, normG2, &nG2));
+    for (int k = 0; k < 4; ++k) {
+        project_fp64(c, k, A[k]);
+        gram_fp64(c, k, A[k]);
+    }
+    zgemm_fp64(c, 1);
+    loss_eval(c.st, Rt, R, c.Y, c.W[2], c.W[3], lam ? lam : c.ones, c.G, c.red, c.sc, 0.0);
+    DevScalars h;
+    CKS(read_scalars(c, &h));
+    if (loss_host) *loss_host = h.loss;
+    if (fit_host) *fit_host = h.fit;
+    if (!isfinite(h.loss)) return set_err(THC_CPD_ERR_NONFINITE, "loss is not finite");
+    return THC_CPD_OK;
+}
+
+thc_cpd_status thc_cpd_als_sweep(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                                 const double* Z, double* const A[4], double* lam, double normG2,
+                                 double* loss_host, double* fit_host, thc_cpd_opts* opts) {
+    return run_als(o, v, Rt, R, Xo, Xv, Z, A, lam, 1, 0.0, normG2, nullptr, loss_host, fit_host, opts);
+}
+
+thc_cpd_status thc_cpd_als(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                           const double* Z, double* const A[4], double* lam, int max_sweeps,
+                           double tol, int* sweeps_done, double* loss_host, double* fit_host,
+                           thc_cpd_opts* opts) {
+    return run_als(o, v, Rt, R, Xo, Xv, Z, A, lam, max_sweeps, tol, 0.0, sweeps_done, loss_host,
+                   fit_host, opts);
+}
+
+}  // extern "C"

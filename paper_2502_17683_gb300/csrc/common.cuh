@@ -1,0 +1,49 @@
+// Shared host/device helpers for the THC-CPD library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+
+namespace thc {
+
+// Launch-time constants sized for GB300: 152 SMs, FP64 throughput about two DFMA per
+// clock per SM, so every FP64 kernel aims for at least two resident CTAs per SM.
+constexpr int kNumSM = 152;
+constexpr int kTargetCTAs = 2 * kNumSM;
+
+// Device-side scalars of one ALS run (one struct per problem).
+struct DevScalars {
+    double normG2;     // ||G||^2
+    double loss;       // loss after the last evaluated sweep
+    double fit;        // fit after the last evaluated sweep
+    double inner;      // <G, Gt>
+    double cpdn2;      // ||Gt||^2
+    double prev_fit;   // fit of the previous evaluated sweep (NaN before the first)
+    double maxdiag;    // max_i H_ii of the current normal matrix
+    double pad0;
+    int fail_mask;     // bit k: Cholesky pivot failure in mode k of this sweep
+    int done;          // convergence reached
+    int nonfinite;     // a loss/fit came out non-finite
+    int pad1;
+};
+
+// Bump allocator over one cudaMallocAsync block; every carve is 256-byte aligned.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0, off = 0;
+    template <class T>
+    T* take(size_t n) {
+        size_t bytes = (n * sizeof(T) + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += bytes;
+        return p;
+    }
+    template <class T>
+    static size_t need(size_t n) { return (n * sizeof(T) + 255) & ~size_t(255); }
+};
+
+inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace thc

@@ -1,0 +1,57 @@
+// FP64 kernels of the THC-CPD path: launchers (definitions in f64_kernels.cu).
+#pragma once
+#include "common.cuh"
+
+namespace thc {
+
+// C[M x N] = op(A)[M x K] * (B o B2)[K x N], optionally C = E o (that product).
+//   op(A)[m,k] = trans_a ? A[k*lda + m] : A[m*lda + k];  B, B2 row-major with ldb.
+//   symm: C is symmetric (A^T A-like); only lower tiles are computed and mirrored.
+// Split-K partials go to `part` (capacity part_cap doubles); deterministic reduction.
+void dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, int lda,
+           const double* B, const double* B2, int ldb, double* C, int ldc,
+           const double* E, bool symm, double* part, size_t part_cap);
+
+// Split-K partial capacity (doubles) that dgemm may use for an M x N output.
+size_t dgemm_part_need(int M, int N, int K);
+
+// H = Ga o Gb o Gc (R x R) written to H (ld R); sc->maxdiag = max_i H_ii.
+void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const double* Gc,
+               double* H, DevScalars* sc);
+
+// In-place solve of A H = M for A (n x R), H SPD (R x R).
+//   Haug: (R + n) x R, rows 0..R-1 hold H (lower triangle read), rows R.. hold M.
+//   On return Haug's M rows hold M L^{-T}; A (n x R, ld R) receives M H^{-1}.
+//   A pivot <= R * eps * sc->maxdiag sets bit `mode` of sc->fail_mask (the result is then
+//   garbage and the caller replays the mode with the pseudo-inverse).
+//   LinvD: workspace of cdiv(R,32)*32*32 doubles.
+void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* LinvD,
+                DevScalars* sc, int mode);
+
+// lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column).
+void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam);
+
+// Loss in factor form after a sweep: inner = sum lam_r Y[Q,r] W3[Q,r] W4[Q,r],
+// cpdn2 = lam^T (G1 o G2 o G3 o G4) lam; loss, fit, convergence into sc.
+void loss_eval(cudaStream_t st, int Rt, int R, const double* Y, const double* W3,
+               const double* W4, const double* lam, const double* const G[4],
+               double* red, DevScalars* sc, double tol);
+size_t loss_red_need();
+
+// sc->normG2 = sum Z o U (U = S Z S computed by the caller).
+void sum_hadamard_normG2(cudaStream_t st, long n, const double* Z, const double* U,
+                         double* red, DevScalars* sc);
+
+// Initialise the scalars struct (normG2 kept if keep_norm).
+void scalars_init(cudaStream_t st, DevScalars* sc, double normG2);
+
+// Jacobi eigen-decomposition based pseudo-inverse solve: A = M pinv(H).
+//   H (R x R, full symmetric, destroyed), M (n x R), V workspace R x R, w R,
+//   T workspace n x R. Returns cudaError of the last launch.
+cudaError_t pinv_solve(cudaStream_t st, int R, int n, double* H, const double* M,
+                       double* A, double* V, double* w, double* T, int* host_sweeps);
+
+// fill lam with ones
+void fill(cudaStream_t st, double* p, long n, double v);
+
+}  // namespace thc

@@ -1,0 +1,625 @@
+// FP64 kernels of THC-driven CP-ALS for GB300 (sm_103a).
+//
+// GB300 executes FP64 at roughly two DFMA per clock per SM (about 1 TFLOP/s for the
+// chip), so these kernels are bound by the FP64 pipe, not by HBM: data stays L2
+// resident (the 129 MB L2 holds every per-problem buffer of the paper-shaped
+// workloads), tiles are small so that every SM gets work, and split-K with a
+// fixed-order reduction keeps results deterministic.
+#include <float.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "f64.cuh"
+
+namespace thc {
+
+// ------------------------------------------------------------------------------------
+// generic FP64 GEMM: C = op(A) (B o B2) [o E]
+// ------------------------------------------------------------------------------------
+template <int BM, int BN, int BK, int TM, int TN, bool TA, bool HADB, bool SYMM>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_dgemm(int M, int N, int K, const double* __restrict__ A, int lda,
+        const double* __restrict__ B, const double* __restrict__ B2, int ldb,
+        double* __restrict__ C, int ldc, const double* __restrict__ E,
+        int kchunk, double* __restrict__ part) {
+    constexpr int TX = BN / TN;
+    constexpr int TY = BM / TM;
+    constexpr int NT = TX * TY;
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (SYMM && by < bx) return;  // strictly upper tile of a symmetric result
+    const int m0 = by * BM, n0 = bx * BN;
+    const int kbeg = bz * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    double acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int idx = tid; idx < BM * BK; idx += NT) {
+            int r, c;
+            if (TA) { r = idx % BM; c = idx / BM; } else { r = idx / BK; c = idx % BK; }
+            const int m = m0 + r, k = k0 + c;
+            double val = 0.0;
+            if (m < M && k < kend) val = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+            As[c][r] = val;
+        }
+        for (int idx = tid; idx < BN * BK; idx += NT) {
+            const int r = idx % BN, c = idx / BN;
+            const int n = n0 + r, k = k0 + c;
+            double val = 0.0;
+            if (n < N && k < kend) {
+                const size_t o = (size_t)k * ldb + n;
+                val = B[o];
+                if (HADB) val *= B2[o];
+            }
+            Bs[c][r] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * TY];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * TX];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int m = m0 + ty + i * TY;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int n = n0 + tx + j * TX;
+            if (n >= N) continue;
+            if (part) {
+                part[((size_t)bz * M + m) * N + n] = acc[i][j];
+            } else {
+                double val = acc[i][j];
+                if (E) val *= E[(size_t)m * ldc + n];
+                C[(size_t)m * ldc + n] = val;
+                if (SYMM) C[(size_t)n * ldc + m] = val;
+            }
+        }
+    }
+}
+
+__global__ void k_splitk_reduce(int M, int N, int splits, const double* __restrict__ part,
+                                double* __restrict__ C, int ldc, const double* __restrict__ E,
+                                int symm_tile) {
+    const long total = (long)M * N;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        const int m = (int)(idx / N), n = (int)(idx % N);
+        if (symm_tile > 0 && (m / symm_tile) < (n / symm_tile)) continue;
+        double s = 0.0;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * total + idx];
+        if (E) s *= E[(size_t)m * ldc + n];
+        C[(size_t)m * ldc + n] = s;
+        if (symm_tile > 0) C[(size_t)n * ldc + m] = s;
+    }
+}
+
+namespace {
+struct GemmPlan {
+    int BM, BN, splits, kchunk, tiles;
+};
+
+GemmPlan plan_gemm(int M, int N, int K, bool symm) {
+    GemmPlan p;
+    p.BN = 64;
+    if (K <= 0) {
+        p.BM = (!symm && M <= 32) ? 32 : 64;
+        p.splits = 1;
+        p.kchunk = 0;
+        p.tiles = 1;
+        return p;
+    }
+    p.BM = (!symm && M <= 32) ? 32 : 64;
+    const int tm = cdiv(M, p.BM), tn = cdiv(N, p.BN);
+    p.tiles = symm ? (tm * (tm + 1)) / 2 : tm * tn;
+    int splits = 1;
+    if (p.tiles < kTargetCTAs) splits = cdiv(kTargetCTAs, p.tiles);
+    splits = std::max(1, std::min(splits, cdiv(K, 64)));
+    int kchunk = ((cdiv(K, splits) + 15) / 16) * 16;
+    p.kchunk = kchunk;
+    p.splits = cdiv(K, kchunk);
+    return p;
+}
+
+template <int BM, bool TA, bool HADB, bool SYMM>
+void launch_gemm(cudaStream_t st, const GemmPlan& p, int M, int N, int K, const double* A,
+                 int lda, const double* B, const double* B2, int ldb, double* C, int ldc,
+                 const double* E, double* part) {
+    constexpr int BN = 64, BK = 16, TN = 4, TM = BM / 16;
+    dim3 grid(cdiv(N, BN), cdiv(M, BM), p.splits);
+    k_dgemm<BM, BN, BK, TM, TN, TA, HADB, SYMM><<<grid, (BM / TM) * (BN / TN), 0, st>>>(
+        M, N, K, A, lda, B, B2, ldb, C, ldc, E, p.kchunk, p.splits > 1 ? part : nullptr);
+}
+
+template <int BM>
+void dispatch_gemm(cudaStream_t st, const GemmPlan& p, bool ta, bool hadb, bool symm, int M,
+                   int N, int K, const double* A, int lda, const double* B, const double* B2,
+                   int ldb, double* C, int ldc, const double* E, double* part) {
+#define THC_G(TA_, HB_, SY_)                                                              \
+    if (ta == TA_ && hadb == HB_ && symm == SY_) {                                        \
+        launch_gemm<BM, TA_, HB_, SY_>(st, p, M, N, K, A, lda, B, B2, ldb, C, ldc, E, part); \
+        return;                                                                           \
+    }
+    THC_G(false, false, false)
+    THC_G(false, true, false)
+    THC_G(true, false, false)
+    THC_G(true, true, false)
+    THC_G(true, false, true)
+    THC_G(false, false, true)
+#undef THC_G
+}
+}  // namespace
+
+size_t dgemm_part_need(int M, int N, int K) {
+    GemmPlan p = plan_gemm(M, N, K, false);
+    GemmPlan q = plan_gemm(M, N, K, true);
+    size_t a = p.splits > 1 ? (size_t)p.splits * M * N : 0;
+    size_t b = q.splits > 1 ? (size_t)q.splits * M * N : 0;
+    return std::max(a, b);
+}
+
+void dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, int lda,
+           const double* B, const double* B2, int ldb, double* C, int ldc, const double* E,
+           bool symm, double* part, size_t part_cap) {
+    if (M <= 0 || N <= 0) return;
+    GemmPlan p = plan_gemm(M, N, K, symm);
+    if (p.splits > 1 && (size_t)p.splits * M * N > part_cap) {
+        p.splits = 1;
+        p.kchunk = K;
+    }
+    if (K <= 0) {  // empty contraction: C = 0
+        p.splits = 1;
+        p.kchunk = 0;
+    }
+    const bool hadb = B2 != nullptr;
+    if (p.BM == 32)
+        dispatch_gemm<32>(st, p, trans_a, hadb, symm, M, N, K, A, lda, B, B2, ldb, C, ldc, E, part);
+    else
+        dispatch_gemm<64>(st, p, trans_a, hadb, symm, M, N, K, A, lda, B, B2, ldb, C, ldc, E, part);
+    if (p.splits > 1) {
+        const long total = (long)M * N;
+        int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSM);
+        k_splitk_reduce<<<blocks, 256, 0, st>>>(M, N, p.splits, part, C, ldc, E, symm ? p.BM : 0);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Hadamard product of three Gram matrices (the ALS normal matrix) + max diagonal
+// ------------------------------------------------------------------------------------
+__device__ double block_reduce_sum(double v, double* sh) {
+    // fixed-order reduction: warp shuffles then one warp over the partials
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+__device__ double block_reduce_max(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+__global__ void k_hadamard3(int R, const double* __restrict__ Ga, const double* __restrict__ Gb,
+                            const double* __restrict__ Gc, double* __restrict__ H,
+                            DevScalars* sc) {
+    const long n = (long)R * R;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x)
+        H[i] = Ga[i] * Gb[i] * Gc[i];
+    if (blockIdx.x == 0) {
+        __shared__ double sh[32];
+        double mx = 0.0;
+        for (int i = threadIdx.x; i < R; i += blockDim.x) {
+            const size_t d = (size_t)i * R + i;
+            mx = fmax(mx, Ga[d] * Gb[d] * Gc[d]);
+        }
+        mx = block_reduce_max(mx, sh);
+        if (threadIdx.x == 0) sc->maxdiag = mx;
+    }
+}
+
+void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const double* Gc,
+               double* H, DevScalars* sc) {
+    const long n = (long)R * R;
+    int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    k_hadamard3<<<blocks, 256, 0, st>>>(R, Ga, Gb, Gc, H, sc);
+}
+
+// ------------------------------------------------------------------------------------
+// Blocked right-looking Cholesky of H with the forward solve of the M rows fused in
+// (the M rows ride along as extra rows of the panel), then a blocked backward solve
+// with inverted diagonal blocks.
+// ------------------------------------------------------------------------------------
+constexpr int NB = 32;          // block size of the factorisation
+constexpr int PANEL_ROWS = 32;  // panel rows per CTA
+constexpr int UT = 32;          // trailing-update tile
+
+__global__ void __launch_bounds__(128)
+k_chol_panel(double* __restrict__ H, int R, int nrows, int j0, int jb, DevScalars* sc, int mode) {
+    __shared__ double D[NB][NB + 1];
+    __shared__ double X[PANEL_ROWS][NB + 1];
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    const double tau = (double)R * DBL_EPSILON * sc->maxdiag;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        D[r][c] = (r < jb && c <= r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < jb; ++c) {
+        if (tid == 0) {
+            double d = D[c][c];
+            if (!(d > tau) || !isfinite(d)) {  // NaN fails the comparison
+                bad = 1;
+                d = 1.0;  // keep going; the caller discards this mode's result
+            }
+            D[c][c] = sqrt(d);
+        }
+        __syncthreads();
+        const double piv = D[c][c];
+        for (int r = c + 1 + tid; r < jb; r += blockDim.x) D[r][c] /= piv;
+        __syncthreads();
+        for (int e = tid; e < jb * jb; e += blockDim.x) {
+            const int r = e / jb, s = e % jb;
+            if (s > c && s <= r) D[r][s] -= D[r][c] * D[s][c];
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0) {
+        if (tid == 0 && bad) atomicOr(&sc->fail_mask, 1 << mode);
+        for (int e = tid; e < jb * jb; e += blockDim.x) {
+            const int r = e / jb, c = e % jb;
+            if (c <= r) H[(size_t)(j0 + r) * R + j0 + c] = D[r][c];
+        }
+        return;
+    }
+    const int row0 = j0 + jb + (blockIdx.x - 1) * PANEL_ROWS;
+    for (int e = tid; e < PANEL_ROWS * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        const int i = row0 + r;
+        X[r][c] = (i < nrows && c < jb) ? H[(size_t)i * R + j0 + c] : 0.0;
+    }
+    __syncthreads();
+    // X L^T = B, column by column
+    for (int c = 0; c < jb; ++c) {
+        for (int r = tid; r < PANEL_ROWS; r += blockDim.x) X[r][c] /= D[c][c];
+        __syncthreads();
+        for (int e = tid; e < PANEL_ROWS * jb; e += blockDim.x) {
+            const int r = e / jb, t = e % jb;
+            if (t > c) X[r][t] -= X[r][c] * D[t][c];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < PANEL_ROWS * jb; e += blockDim.x) {
+        const int r = e / jb, c = e % jb;
+        const int i = row0 + r;
+        if (i < nrows) H[(size_t)i * R + j0 + c] = X[r][c];
+    }
+}
+
+// Trailing update H[i][c] -= sum_s H[i][j0+s] H[c][j0+s] for i >= j1 (rows of H and of
+// the appended M block), j1 <= c < R, lower triangle only for rows of H.
+__global__ void __launch_bounds__(256)
+k_chol_update(double* __restrict__ H, int R, int nrows, int j0, int jb, int nHtiles) {
+    const int j1 = j0 + jb;
+    int r0, rend;
+    if ((int)blockIdx.y < nHtiles) {
+        r0 = j1 + blockIdx.y * UT;
+        rend = min(R, r0 + UT);
+    } else {
+        r0 = R + (blockIdx.y - nHtiles) * UT;
+        rend = min(nrows, r0 + UT);
+    }
+    const int c0 = j1 + blockIdx.x * UT;
+    if (c0 >= R || r0 >= rend) return;
+    const bool hrows = r0 < R;
+    if (hrows && c0 > rend - 1) return;  // tile strictly above the diagonal
+    __shared__ double As[UT][NB + 1];
+    __shared__ double Bs[UT][NB + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < UT * NB; e += 256) {
+        const int r = e / NB, s = e % NB;
+        As[r][s] = (r0 + r < rend && s < jb) ? H[(size_t)(r0 + r) * R + j0 + s] : 0.0;
+        Bs[r][s] = (c0 + r < R && s < jb) ? H[(size_t)(c0 + r) * R + j0 + s] : 0.0;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+#pragma unroll 8
+    for (int s = 0; s < NB; ++s) {
+        const double x0 = As[ty][s], x1 = As[ty + 16][s];
+        const double y0 = Bs[tx][s], y1 = Bs[tx + 16][s];
+        a00 = fma(x0, y0, a00);
+        a01 = fma(x0, y1, a01);
+        a10 = fma(x1, y0, a10);
+        a11 = fma(x1, y1, a11);
+    }
+    const double acc[2][2] = {{a00, a01}, {a10, a11}};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int row = r0 + ty + 16 * i;
+        if (row >= rend) continue;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int col = c0 + tx + 16 * j;
+            if (col >= R) continue;
+            if (hrows && col > row) continue;
+            H[(size_t)row * R + col] -= acc[i][j];
+        }
+    }
+}
+
+// Inverse of each lower-triangular diagonal block L_JJ (one CTA per block, one column
+// of the inverse per thread).
+__global__ void __launch_bounds__(32) k_tri_inv_diag(const double* __restrict__ H, int R,
+                                                     double* __restrict__ LinvD) {
+    __shared__ double L[NB][NB + 1];
+    __shared__ double X[NB][NB + 1];
+    const int J = blockIdx.x, c0 = J * NB, jb = min(NB, R - c0), t = threadIdx.x;
+    for (int r = 0; r < NB; ++r) {
+        L[r][t] = (r < jb && t <= r) ? H[(size_t)(c0 + r) * R + c0 + t] : 0.0;
+        X[r][t] = 0.0;
+    }
+    __syncwarp();
+    if (t < jb) {
+        X[t][t] = 1.0 / L[t][t];
+        for (int r = t + 1; r < jb; ++r) {
+            double s = 0.0;
+            for (int q = t; q < r; ++q) s = fma(L[r][q], X[q][t], s);
+            X[r][t] = -s / L[r][r];
+        }
+    }
+    __syncwarp();
+    double* out = LinvD + (size_t)J * NB * NB;
+    for (int r = 0; r < NB; ++r) out[r * NB + t] = X[r][t];
+}
+
+// T_J = Linv_JJ L[J, 0:c0_J), written over L[J, 0:c0_J) (one column per thread).
+__global__ void __launch_bounds__(128) k_bsolve_prep(double* __restrict__ H, int R,
+                                                     const double* __restrict__ LinvD) {
+    const int J = blockIdx.y + 1;
+    const int c0 = J * NB;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c0) return;
+    const int jb = min(NB, R - c0);
+    double l[NB];
+#pragma unroll
+    for (int s = 0; s < NB; ++s) l[s] = (s < jb) ? H[(size_t)(c0 + s) * R + c] : 0.0;
+    const double* Li = LinvD + (size_t)J * NB * NB;
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+        if (a >= jb) break;
+        double t = 0.0;
+#pragma unroll
+        for (int s = 0; s <= a; ++s) t = fma(Li[a * NB + s], l[s], t);
+        H[(size_t)(c0 + a) * R + c] = t;
+    }
+}
+
+// Backward step J of A L = Y: A[:, J] = Y_J Linv_JJ and Y[:, 0:c0) -= Y_J T_J.
+__global__ void __launch_bounds__(128)
+k_bsolve_step(double* __restrict__ Yf, double* __restrict__ A, int R,
+              const double* __restrict__ H, const double* __restrict__ LinvD, int J) {
+    const int c0 = J * NB, jb = min(NB, R - c0);
+    const int r = blockIdx.y;
+    __shared__ double y[NB];
+    if (threadIdx.x < NB) y[threadIdx.x] = (threadIdx.x < jb) ? Yf[(size_t)r * R + c0 + threadIdx.x] : 0.0;
+    __syncthreads();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < c0) {
+        double s = 0.0;
+        for (int a = 0; a < jb; ++a) s = fma(y[a], H[(size_t)(c0 + a) * R + q], s);
+        Yf[(size_t)r * R + q] -= s;
+    } else if (q < c0 + jb) {
+        const int c = q - c0;
+        const double* Li = LinvD + (size_t)J * NB * NB;
+        double s = 0.0;
+        for (int a = c; a < jb; ++a) s = fma(y[a], Li[a * NB + c], s);
+        A[(size_t)r * R + c0 + c] = s;
+    }
+}
+
+void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* LinvD,
+                DevScalars* sc, int mode) {
+    const int nrows = R + n;
+    for (int j0 = 0; j0 < R; j0 += NB) {
+        const int jb = std::min(NB, R - j0);
+        const int below = nrows - (j0 + jb);
+        k_chol_panel<<<1 + cdiv(below, PANEL_ROWS), 128, 0, st>>>(Haug, R, nrows, j0, jb, sc, mode);
+        const int j1 = j0 + jb;
+        if (j1 < nrows && j1 < R) {
+            const int nH = cdiv(R - j1, UT);
+            dim3 grid(cdiv(R - j1, UT), nH + cdiv(n, UT));
+            k_chol_update<<<grid, 256, 0, st>>>(Haug, R, nrows, j0, jb, nH);
+        }
+    }
+    const int nJ = cdiv(R, NB);
+    k_tri_inv_diag<<<nJ, 32, 0, st>>>(Haug, R, LinvD);
+    if (nJ > 1) {
+        dim3 grid(cdiv((nJ - 1) * NB, 128), nJ - 1);
+        k_bsolve_prep<<<grid, 128, 0, st>>>(Haug, R, LinvD);
+    }
+    if (n <= 0) return;
+    double* Yf = Haug + (size_t)R * R;
+    for (int J = nJ - 1; J >= 0; --J) {
+        const int c0 = J * NB, jb = std::min(NB, R - c0);
+        dim3 grid(cdiv(c0 + jb, 128), n);
+        k_bsolve_step<<<grid, 128, 0, st>>>(Yf, A, R, Haug, LinvD, J);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// column normalisation, loss, norms
+// ------------------------------------------------------------------------------------
+__global__ void k_normalise(int n, int R, double* __restrict__ A, double* __restrict__ lam) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double x = A[(size_t)i * R + r];
+        s = fma(x, x, s);
+    }
+    const double l = sqrt(s);
+    lam[r] = l;
+    if (l > 0.0)
+        for (int i = 0; i < n; ++i) A[(size_t)i * R + r] /= l;
+}
+
+void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam) {
+    k_normalise<<<cdiv(R, 128), 128, 0, st>>>(n, R, A, lam);
+}
+
+constexpr int RED_BLOCKS = 2 * kNumSM;
+constexpr int RED_THREADS = 256;
+
+size_t loss_red_need() { return 2 * RED_BLOCKS; }
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_loss_partials(int Rt, int R, const double* __restrict__ Y, const double* __restrict__ W3,
+                const double* __restrict__ W4, const double* __restrict__ lam,
+                const double* __restrict__ G1, const double* __restrict__ G2,
+                const double* __restrict__ G3, const double* __restrict__ G4,
+                double* __restrict__ red) {
+    __shared__ double sh[32];
+    const long stride = (long)gridDim.x * blockDim.x;
+    const long g = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    const long n1 = (long)Rt * R;
+    for (long i = g; i < n1; i += stride) {
+        const int r = (int)(i % R);
+        s1 = fma(lam[r] * Y[i], W3[i] * W4[i], s1);
+    }
+    const long n2 = (long)R * R;
+    for (long i = g; i < n2; i += stride) {
+        const int r = (int)(i / R), c = (int)(i % R);
+        s2 = fma(lam[r] * lam[c], G1[i] * G2[i] * G3[i] * G4[i], s2);
+    }
+    s1 = block_reduce_sum(s1, sh);
+    s2 = block_reduce_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        red[2 * blockIdx.x] = s1;
+        red[2 * blockIdx.x + 1] = s2;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_loss_final(const double* __restrict__ red, int nb, DevScalars* sc, double tol) {
+    __shared__ double sh[32];
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        s1 += red[2 * i];
+        s2 += red[2 * i + 1];
+    }
+    s1 = block_reduce_sum(s1, sh);
+    s2 = block_reduce_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        const double nG2 = sc->normG2;
+        const double loss = nG2 - 2.0 * s1 + s2;
+        const double fit = 1.0 - sqrt(fmax(loss, 0.0)) / sqrt(nG2);
+        sc->inner = s1;
+        sc->cpdn2 = s2;
+        sc->loss = loss;
+        if (!isfinite(loss)) sc->nonfinite = 1;
+        const double prev = sc->prev_fit;
+        if (tol > 0.0 && isfinite(prev) && fabs(fit - prev) < tol) sc->done = 1;
+        sc->prev_fit = fit;
+        sc->fit = fit;
+    }
+}
+
+void loss_eval(cudaStream_t st, int Rt, int R, const double* Y, const double* W3,
+               const double* W4, const double* lam, const double* const G[4], double* red,
+               DevScalars* sc, double tol) {
+    k_loss_partials<<<RED_BLOCKS, RED_THREADS, 0, st>>>(Rt, R, Y, W3, W4, lam, G[0], G[1],
+                                                         G[2], G[3], red);
+    k_loss_final<<<1, RED_THREADS, 0, st>>>(red, RED_BLOCKS, sc, tol);
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_sumprod_partials(long n, const double* __restrict__ a, const double* __restrict__ b,
+                   double* __restrict__ red) {
+    __shared__ double sh[32];
+    const long stride = (long)gridDim.x * blockDim.x;
+    double s = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += stride)
+        s = fma(a[i], b[i], s);
+    s = block_reduce_sum(s, sh);
+    if (threadIdx.x == 0) red[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_norm_final(const double* __restrict__ red, int nb, DevScalars* sc) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += red[i];
+    s = block_reduce_sum(s, sh);
+    if (threadIdx.x == 0) sc->normG2 = s;
+}
+
+void sum_hadamard_normG2(cudaStream_t st, long n, const double* Z, const double* U,
+                         double* red, DevScalars* sc) {
+    k_sumprod_partials<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, Z, U, red);
+    k_norm_final<<<1, RED_THREADS, 0, st>>>(red, RED_BLOCKS, sc);
+}
+
+__global__ void k_scalars_init(DevScalars* sc, double normG2) {
+    sc->normG2 = normG2;
+    sc->loss = nan("");
+    sc->fit = nan("");
+    sc->inner = 0.0;
+    sc->cpdn2 = 0.0;
+    sc->prev_fit = nan("");
+    sc->maxdiag = 0.0;
+    sc->fail_mask = 0;
+    sc->done = 0;
+    sc->nonfinite = 0;
+}
+
+void scalars_init(cudaStream_t st, DevScalars* sc, double normG2) {
+    k_scalars_init<<<1, 1, 0, st>>>(sc, normG2);
+}
+
+__global__ void k_fill(double* p, long n, double v) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+void fill(cudaStream_t st, double* p, long n, double v) {
+    if (n <= 0) return;
+    k_fill<<<(int)std::min<long>(cdiv(n, 256), 1024), 256, 0, st>>>(p, n, v);
+}
+
+}  // namespace thc

@@ -1,0 +1,79 @@
+"""The C-ABI library loads, exports every entry point include/*.h declares, and rejects
+bad arguments before touching a device (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import _lib
+    return _lib.load()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(thc_cpd_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for n in ("thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep", "thc_cpd_als"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2502_17683_gb300 import _lib
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(_lib.EXPORTS) == set(declared_symbols())
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.thc_cpd_version()
+
+
+def _call_mttkrp(lib, o, v, Rt, R, mode, ptr=1, Aptrs=(1, 1, 1, 1), M=1, prec=0):
+    from paper_2502_17683_gb300._lib import PTR4, Opts
+    opts = Opts()
+    opts.precision = prec
+    return lib.thc_cpd_mttkrp(o, v, Rt, R, ptr, ptr, ptr, PTR4(*Aptrs), mode, M, ctypes.byref(opts))
+
+
+def test_argument_validation_happens_before_device_work(lib):
+    from paper_2502_17683_gb300 import _lib
+    # invalid shapes / modes / null pointers / precision are reported without any CUDA call
+    assert _call_mttkrp(lib, 0, 5, 5, 5, 0) == _lib.ERR_SHAPE
+    assert _call_mttkrp(lib, 5, 5, -1, 5, 0) == _lib.ERR_SHAPE
+    assert _call_mttkrp(lib, 5, 5, 5, 1 << 20, 0) == _lib.ERR_SHAPE
+    assert _call_mttkrp(lib, 5, 5, 5, 5, 4) == _lib.ERR_ARG
+    assert _call_mttkrp(lib, 5, 5, 5, 5, 0, ptr=None) == _lib.ERR_ARG
+    assert _call_mttkrp(lib, 5, 5, 5, 5, 0, Aptrs=(1, None, 1, 1)) == _lib.ERR_ARG
+    assert _call_mttkrp(lib, 5, 5, 5, 5, 0, M=None) == _lib.ERR_ARG
+    assert _call_mttkrp(lib, 5, 5, 5, 5, 0, prec=9) == _lib.ERR_ARG
+    assert b"mode" in lib.thc_cpd_last_error() or b"precision" in lib.thc_cpd_last_error()
+    out = ctypes.c_double()
+    assert lib.thc_cpd_thc_norm2(3, 4, 5, None, 1, 1, ctypes.byref(out), None) == _lib.ERR_ARG
+    assert lib.thc_cpd_thc_norm2(3, 4, 5, 1, 1, 1, None, None) == _lib.ERR_ARG
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path):
+    from paper_2502_17683_gb300 import _lib
+    with pytest.raises(_lib.ThcCpdError):
+        saved = _lib._lib
+        _lib._lib = None
+        try:
+            _lib.load(str(tmp_path / "missing.so"))
+        finally:
+            _lib._lib = saved

@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""ALS sweeps/s of THC-driven matrix-free CP-ALS on one GB300.
+
+Workload (one step): thc_cpd_als on the o=20, v=100, R_thc=480, R_cp=720 THC block
+(synthetic THC factors, seed 0; 50 sweeps, no early stop), restarted from the same
+start factors every step. value = sweeps/s over all ranks (each rank solves its own
+independent problem: weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16x3|tf32x3]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W = dict(o=20, v=100, Rt=480, R=720, sweeps=50, seed=0)
+WORKLOAD = "THC-driven CP-ALS, o=20 v=100 R_thc=480 R_cp=720, 50 sweeps per step"
+METRIC = "ALS sweeps/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=None,
+                    help="sweeps per step (profiling captures only; the bench line uses 50)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# nominal dense rates (TFLOP/s) used to carry the measured bf16 peak over to other dtypes
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sweeps_per_s(seconds: float, seed: int):
+    """The FP64 CPU oracle as it stands, on the host cores, over a bounded number of sweeps
+    of the same workload from the same start point."""
+    from oracle import thc_cpd as O
+    from thc_inputs import make_problem
+    p = make_problem(W["o"], W["v"], W["Rt"], W["R"], seed=seed)
+    nG2 = O.thc_norm2(p.Xo, p.Xv, p.Z)
+    A, lam = p.A, None
+    t0 = time.perf_counter()
+    A, lam, _, _, _ = O.als_sweep(p.Xo, p.Xv, p.Z, A, lam, nG2)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(seconds / max(t1, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        A, lam, _, _, _ = O.als_sweep(p.Xo, p.Xv, p.Z, A, lam, nG2)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sweeps_per_s(per_step / 4, W["seed"])
+    vals, sweeps, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        v, n, dt = oracle_sweeps_per_s(per_step, W["seed"])
+        vals.append(v)
+        sweeps += n
+        secs += dt
+    value = sweeps / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, **{k: W[k] for k in ("o", "v", "Rt", "R")},
+                   "note": "each step is a bounded sample of sweeps of the workload"},
+        "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": f"{sweeps} sweeps over {args.steps} steps, "
+                         "numpy/OpenBLAS FP64 matrix-free ALS"},
+        "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import api
+    from thc_inputs import make_problem
+
+    precision = args.precision or "fp64"
+    if args.sweeps:
+        W["sweeps"] = args.sweeps
+    p = make_problem(W["o"], W["v"], W["Rt"], W["R"], seed=W["seed"] + rank)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    Xo, Xv, Z = t(p.Xo), t(p.Xv), t(p.Z)
+    A0 = [t(a) for a in p.A]
+    A = [a.clone() for a in A0]
+    lam = torch.ones(W["R"], dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision=precision)
+
+    def reset():
+        for a, a0 in zip(A, A0):
+            a.copy_(a0)
+
+    for _ in range(args.warmup):
+        reset()
+        out = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time per step, L2 flushed between steps) ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = api.thc_cpd_launch_count()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            reset()
+            ev[k][0].record(stream)
+            out = step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = api.thc_cpd_launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    sweeps_total = world * args.steps * W["sweeps"]
+    value = sweeps_total / (ms / 1000.0)
+    fit = out["fit"]
+
+    # ---- end to end through the public API with host buffers ----
+    hp = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    hXo, hXv, hZ = hp(p.Xo), hp(p.Xv), hp(p.Z)
+    hA = [hp(a) for a in p.A]
+    oA = [torch.empty_like(a).pin_memory() for a in hA]
+    olam = torch.empty(W["R"], dtype=torch.float64).pin_memory()
+    h2d = sum(x.numel() * 8 for x in [hXo, hXv, hZ] + hA)
+    d2h = sum(x.numel() * 8 for x in oA) + olam.numel() * 8
+    dXo, dXv, dZ = torch.empty_like(Xo), torch.empty_like(Xv), torch.empty_like(Z)
+
+    def e2e_step():
+        dXo.copy_(hXo, non_blocking=True)
+        dXv.copy_(hXv, non_blocking=True)
+        dZ.copy_(hZ, non_blocking=True)
+        for a, h in zip(A, hA):
+            a.copy_(h, non_blocking=True)
+        api.thc_cpd_als(dXo, dXv, dZ, A, lam, W["sweeps"], 0.0, precision=precision)
+        for o_, a in zip(oA, A):
+            o_.copy_(a, non_blocking=True)
+        olam.copy_(lam, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        e2e_step()
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms2 = sum(a.elapsed_time(b) for a, b in ev2)
+    if world > 1:
+        tt = torch.tensor([ms2], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms2 = float(tt.item())
+    e2e_value = sweeps_total / (ms2 / 1000.0)
+
+    # ---- roofline: per-kernel-class CUDA events over one more profiled step ----
+    pk, pk_kind = peaks()
+    reset()
+    api.thc_cpd_profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = api.thc_cpd_profile_read()
+    api.thc_cpd_profile(False)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["flops"] / (d["ms"] / 1000.0) / 1e12 if d["ms"] > 0 else 0.0
+    if dom == "tc_gemm":
+        peak = pk["bf16_tflops_sustained"]
+        note = "bf16 sustained, " + pk_kind
+    elif dom == "elementwise":
+        peak = None
+        note = pk_kind
+    else:
+        peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        note = f"{pk_kind} bf16 burst x nominal fp64/bf16 ratio"
+    roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                "traffic": None, "peak_source": note,
+                "classes_ms_per_step": {k: round(v["ms"], 3) for k, v in prof.items()}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == "fp64" else f"{precision}+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "o": W["o"], "v": W["v"], "R_thc": W["Rt"],
+                   "R_cp": W["R"], "sweeps_per_step": W["sweeps"], "precision": precision,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "fit": fit,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roofline,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, n, dt = oracle_sweeps_per_s(args.cpu_seconds, W["seed"])
+        line["cpu_baseline"] = {"value": v, "unit": "sweeps/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"{n} sweeps of the same workload ({dt:.1f} s), "
+                                          "numpy/OpenBLAS FP64, default thread count"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

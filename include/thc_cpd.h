@@ -111,6 +111,32 @@ thc_cpd_status thc_cpd_als(int o, int v, int Rt, int R,
                            int* sweeps_done, double* loss_host, double* fit_host,
                            thc_cpd_opts* opts);
 
+/* ---- launch accounting and kernel timing (tracing support; the paper has no
+ * counterpart: it reports wall-times only) ---------------------------------------- */
+
+/* Kernels this library has launched since it was loaded (all threads). */
+long thc_cpd_launch_count(void);
+
+/* Per kernel class: summed CUDA-event time of the launch groups, their algorithmic
+ * FLOPs and bytes, and the number of groups. Classes: 0 FP64 GEMM, 1 Cholesky
+ * (factorisation with the fused forward solve), 2 backward solve, 3 element-wise and
+ * reduction kernels, 4 tensor-core GEMM. */
+typedef struct thc_cpd_kstat {
+    double ms;
+    double flops;
+    double bytes;
+    long groups;
+} thc_cpd_kstat;
+
+/* enable != 0 starts recording CUDA events around every launch group (process-wide)
+ * and clears earlier records; 0 stops recording. Adds host overhead: leave it off in
+ * timed runs whose throughput is reported. */
+void thc_cpd_profile(int enable);
+
+/* Fills out[0..min(max_classes,5)) (waits for the recorded events); returns the count
+ * filled or -1 on a CUDA error. */
+int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes);
+
 /* Message for the last non-OK status returned on this host thread. */
 const char* thc_cpd_last_error(void);
 

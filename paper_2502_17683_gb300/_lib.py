@@ -17,13 +17,20 @@ PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 
 # every symbol include/thc_cpd.h declares
 EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
-           "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version")
+           "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version", "thc_cpd_launch_count",
+           "thc_cpd_profile", "thc_cpd_profile_read")
+KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
 
 
 class ThcCpdError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("groups", ctypes.c_long)]
 
 
 class Opts(ctypes.Structure):
@@ -72,6 +79,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.thc_cpd_last_error.argtypes = []
     lib.thc_cpd_version.restype = ctypes.c_char_p
     lib.thc_cpd_version.argtypes = []
+    lib.thc_cpd_launch_count.restype = ctypes.c_long
+    lib.thc_cpd_launch_count.argtypes = []
+    lib.thc_cpd_profile.restype = None
+    lib.thc_cpd_profile.argtypes = [ctypes.c_int]
+    lib.thc_cpd_profile_read.restype = ctypes.c_int
+    lib.thc_cpd_profile_read.argtypes = [ctypes.POINTER(KStat), ctypes.c_int]
     _lib = lib
     return lib
 

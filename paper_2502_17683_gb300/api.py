@@ -10,10 +10,12 @@ import ctypes
 
 import torch
 
-from ._lib import PRECISIONS, PTR4, Opts, ThcCpdError, check, load, ERR_ARG
+from ._lib import (ERR_ARG, KCLASS_NAMES, PRECISIONS, PTR4, KStat, Opts, ThcCpdError, check,
+                   load)
 
 __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
-           "thc_cpd_als", "thc_cpd_version", "Opts"]
+           "thc_cpd_als", "thc_cpd_version", "thc_cpd_launch_count", "thc_cpd_profile",
+           "thc_cpd_profile_read", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -123,3 +125,22 @@ def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision=
         out["losses"] = h[0::2]
         out["fits"] = h[1::2]
     return out
+
+
+def thc_cpd_launch_count() -> int:
+    return int(load().thc_cpd_launch_count())
+
+
+def thc_cpd_profile(enable: bool) -> None:
+    load().thc_cpd_profile(1 if enable else 0)
+
+
+def thc_cpd_profile_read() -> dict:
+    """Per kernel class: dict(ms, flops, bytes, groups) summed over recorded groups."""
+    n = len(KCLASS_NAMES)
+    buf = (KStat * n)()
+    got = load().thc_cpd_profile_read(buf, n)
+    if got < 0:
+        raise ThcCpdError(3, "profile read failed")
+    return {KCLASS_NAMES[i]: dict(ms=buf[i].ms, flops=buf[i].flops, bytes=buf[i].bytes,
+                                  groups=buf[i].groups) for i in range(got)}

@@ -169,7 +169,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     bytes += 4 * Arena::need<double>(RR);                  // G
     bytes += Arena::need<double>(RtR);                     // Y
     bytes += Arena::need<double>((size_t)(R + nmax) * R);  // Haug
-    bytes += Arena::need<double>((size_t)cdiv(R, 32) * 1024);
+    bytes += Arena::need<double>((size_t)R * 32 + R);  // panel X and D^{-1}
     bytes += Arena::need<double>(pc);
     bytes += Arena::need<double>(loss_red_need() + 2 * kNumSM * 2);
     bytes += Arena::need<double>(R);
@@ -189,7 +189,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     for (int k = 0; k < 4; ++k) c.G[k] = ar.take<double>(RR);
     c.Y = ar.take<double>(RtR);
     c.Haug = ar.take<double>((size_t)(R + nmax) * R);
-    c.LinvD = ar.take<double>((size_t)cdiv(R, 32) * 1024);
+    c.LinvD = ar.take<double>((size_t)R * 32 + R);
     c.part = ar.take<double>(pc);
     c.red = ar.take<double>(loss_red_need() + 2 * kNumSM * 2);
     c.ones = ar.take<double>(R);
@@ -306,7 +306,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
         CK(cudaMemcpyAsync(Mrows, c.Msave, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, c.st));
         CK(cudaMemcpyAsync(c.Haug, c.Hsave, sizeof(double) * R * R, cudaMemcpyDeviceToDevice, c.st));
     }
-    chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.sc, k);
+    chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * 32, c.sc, k);
     if (safe) {
         DevScalars* h = host_scalars();
         if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");

@@ -19,13 +19,13 @@ size_t dgemm_part_need(int M, int N, int K);
 void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const double* Gc,
                double* H, DevScalars* sc);
 
-// In-place solve of A H = M for A (n x R), H SPD (R x R).
+// In-place solve of A H = M for A (n x R), H SPD (R x R), by LDL^T with the M rows
+// carried along (fused forward solve) and a unit backward solve.
 //   Haug: (R + n) x R, rows 0..R-1 hold H (lower triangle read), rows R.. hold M.
-//   On return Haug's M rows hold M L^{-T}; A (n x R, ld R) receives M H^{-1}.
+//   P: R x 32 panel workspace, dinv: R doubles.
 //   A pivot <= R * eps * sc->maxdiag sets bit `mode` of sc->fail_mask (the result is then
 //   garbage and the caller replays the mode with the pseudo-inverse).
-//   LinvD: workspace of cdiv(R,32)*32*32 doubles.
-void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* LinvD,
+void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode);
 
 // lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column).

@@ -11,6 +11,7 @@
 #include <algorithm>
 
 #include "f64.cuh"
+#include "prof.cuh"
 
 namespace thc {
 
@@ -189,6 +190,8 @@ void dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, 
         p.kchunk = 0;
     }
     const bool hadb = B2 != nullptr;
+    ProfScope prof(st, KC_DGEMM, (symm ? 1.0 : 2.0) * M * (double)N * K);
+    count_launch(p.splits > 1 ? 2 : 1);
     if (p.BM == 32)
         dispatch_gemm<32>(st, p, trans_a, hadb, symm, M, N, K, A, lda, B, B2, ldb, C, ldc, E, part);
     else
@@ -253,86 +256,128 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
                double* H, DevScalars* sc) {
     const long n = (long)R * R;
     int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    ProfScope prof(st, KC_AUX, 2.0 * n, 32.0 * n);
+    count_launch();
     k_hadamard3<<<blocks, 256, 0, st>>>(R, Ga, Gb, Gc, H, sc);
 }
 
 // ------------------------------------------------------------------------------------
-// Blocked right-looking Cholesky of H with the forward solve of the M rows fused in
-// (the M rows ride along as extra rows of the panel), then a blocked backward solve
-// with inverted diagonal blocks.
+// Solve of the ALS normal equations A H = M: blocked right-looking LDL^T factorisation
+// of H (the square-root-free form of the Cholesky factorisation, same pivots) with the
+// M rows carried along as extra rows, so that the forward solve is fused into the
+// factorisation; then a blocked backward solve with the unit lower factor.
+//
+// GB300 issues one FP64 warp-instruction per SM sub-partition every 64 clocks, whatever
+// the number of active lanes, and FP64 divide / sqrt cost 400-700 clocks. So the
+// sequential part (one pivot per column) uses a single Newton-Raphson reciprocal per
+// pivot and no sqrt or divide; row substitutions run one row per warp with the
+// column values passed by shuffles.
+//
+//   H = L D L^T (L unit lower).  For the appended rows B = M: after elimination they
+//   hold Y = M L^{-T} D^{-1}; then A = Y L^{-1} by the backward solve (unit L).
+//   Storage after the factorisation: strictly-lower L and diag(D) in H, D^{-1} in dinv,
+//   Y in the appended rows; P (R x 32) holds the unscaled panel X = L D of the current
+//   block column for the trailing update.
 // ------------------------------------------------------------------------------------
 constexpr int NB = 32;          // block size of the factorisation
-constexpr int PANEL_ROWS = 32;  // panel rows per CTA
+constexpr int PANEL_ROWS = 8;   // panel rows per CTA (two per warp)
 constexpr int UT = 32;          // trailing-update tile
 
-__global__ void __launch_bounds__(128)
-k_chol_panel(double* __restrict__ H, int R, int nrows, int j0, int jb, DevScalars* sc, int mode) {
-    __shared__ double D[NB][NB + 1];
-    __shared__ double X[PANEL_ROWS][NB + 1];
+// Reciprocal by Newton-Raphson (y <- y + y (1 - d y), quadratic convergence) from an
+// FP32 seed: two steps take a 24-bit seed past FP64 precision. Outside the FP32 range
+// the plain division is used.
+__device__ __forceinline__ double recip_nr(double d) {
+    if (!(fabs(d) > 1e-30 && fabs(d) < 1e30)) return 1.0 / d;
+    double y = (double)__frcp_rn((float)d);
+    double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-d, y, 1.0);
+    return fma(y, e, y);
+}
+
+// LDL^T of the jb x jb diagonal block held in Ds (lower part); on return Ls holds the
+// unit-lower L_jj (strictly lower part), Ds[c][c] the pivots d_c and dinv_s[c] = 1/d_c.
+// Returns (in thread 0) whether a pivot failed the test d > tau.
+__device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* dinv_s, int jb,
+                         double tau) {
     __shared__ int bad;
     const int tid = threadIdx.x;
-    const double tau = (double)R * DBL_EPSILON * sc->maxdiag;
     if (tid == 0) bad = 0;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int r = e / NB, c = e % NB;
-        D[r][c] = (r < jb && c <= r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
-    }
-    __syncthreads();
     for (int c = 0; c < jb; ++c) {
         if (tid == 0) {
-            double d = D[c][c];
+            double d = Ds[c][c];
             if (!(d > tau) || !isfinite(d)) {  // NaN fails the comparison
                 bad = 1;
-                d = 1.0;  // keep going; the caller discards this mode's result
+                d = 1.0;  // keep going; the caller replays this mode with the pseudo-inverse
+                Ds[c][c] = d;
             }
-            D[c][c] = sqrt(d);
+            dinv_s[c] = recip_nr(d);
         }
         __syncthreads();
-        const double piv = D[c][c];
-        for (int r = c + 1 + tid; r < jb; r += blockDim.x) D[r][c] /= piv;
+        const double inv = dinv_s[c];
+        for (int r = c + 1 + tid; r < jb; r += blockDim.x) Ls[r][c] = Ds[r][c] * inv;
         __syncthreads();
-        for (int e = tid; e < jb * jb; e += blockDim.x) {
-            const int r = e / jb, s = e % jb;
-            if (s > c && s <= r) D[r][s] -= D[r][c] * D[s][c];
+        // trailing update of the block: D[r][s] -= L[r][c] * X[s][c], c < s <= r
+        const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+        const int s = c + 1 + lane;
+        if (s < jb) {
+            const double xs = Ds[s][c];
+            for (int r = s + w; r < jb; r += nw) Ds[r][s] = fma(-Ls[r][c], xs, Ds[r][s]);
         }
         __syncthreads();
     }
+    return bad;
+}
+
+__global__ void __launch_bounds__(128)
+k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__ dinv, int R,
+            int nrows, int j0, int jb, DevScalars* sc, int mode) {
+    __shared__ double Ds[NB][NB + 1];
+    __shared__ double Ls[NB][NB + 1];
+    __shared__ double dinv_s[NB];
+    const int tid = threadIdx.x;
+    const double tau = (double)R * DBL_EPSILON * sc->maxdiag;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        Ds[r][c] = (r < jb && c <= r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
+        Ls[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int bad = ldl_block(Ds, Ls, dinv_s, jb, tau);
     if (blockIdx.x == 0) {
         if (tid == 0 && bad) atomicOr(&sc->fail_mask, 1 << mode);
         for (int e = tid; e < jb * jb; e += blockDim.x) {
             const int r = e / jb, c = e % jb;
-            if (c <= r) H[(size_t)(j0 + r) * R + j0 + c] = D[r][c];
+            if (c < r) H[(size_t)(j0 + r) * R + j0 + c] = Ls[r][c];
+            else if (c == r) H[(size_t)(j0 + r) * R + j0 + c] = Ds[r][r];
         }
+        if (tid < jb) dinv[j0 + tid] = dinv_s[tid];
         return;
     }
-    const int row0 = j0 + jb + (blockIdx.x - 1) * PANEL_ROWS;
-    for (int e = tid; e < PANEL_ROWS * NB; e += blockDim.x) {
-        const int r = e / NB, c = e % NB;
-        const int i = row0 + r;
-        X[r][c] = (i < nrows && c < jb) ? H[(size_t)i * R + j0 + c] : 0.0;
-    }
-    __syncthreads();
-    // X L^T = B, column by column
-    for (int c = 0; c < jb; ++c) {
-        for (int r = tid; r < PANEL_ROWS; r += blockDim.x) X[r][c] /= D[c][c];
-        __syncthreads();
-        for (int e = tid; e < PANEL_ROWS * jb; e += blockDim.x) {
-            const int r = e / jb, t = e % jb;
-            if (t > c) X[r][t] -= X[r][c] * D[t][c];
+    // rows below the block: unit-triangular substitution X L_jj^T = B (one row per warp),
+    // then L = X D^{-1}; X goes to P for the trailing update (rows of H only)
+    const int lane = tid & 31, w = tid >> 5;
+    const int j1 = j0 + jb;
+    for (int rr = w; rr < PANEL_ROWS; rr += blockDim.x >> 5) {
+        const int i = j1 + (blockIdx.x - 1) * PANEL_ROWS + rr;
+        if (i >= nrows) break;
+        double b = (lane < jb) ? H[(size_t)i * R + j0 + lane] : 0.0;
+        for (int c = 0; c < jb; ++c) {
+            const double xc = __shfl_sync(0xffffffffu, b, c);
+            if (lane > c) b = fma(-xc, Ls[lane][c], b);
         }
-        __syncthreads();
-    }
-    for (int e = tid; e < PANEL_ROWS * jb; e += blockDim.x) {
-        const int r = e / jb, c = e % jb;
-        const int i = row0 + r;
-        if (i < nrows) H[(size_t)i * R + j0 + c] = X[r][c];
+        if (lane < jb) {
+            H[(size_t)i * R + j0 + lane] = b * dinv_s[lane];
+            if (i < R) P[(size_t)i * NB + lane] = b;
+        }
     }
 }
 
-// Trailing update H[i][c] -= sum_s H[i][j0+s] H[c][j0+s] for i >= j1 (rows of H and of
-// the appended M block), j1 <= c < R, lower triangle only for rows of H.
+// Trailing update H[i][c] -= sum_s L[i][j0+s] X[c][s] for i >= j1 (rows of H and of the
+// appended M block), j1 <= c < R, lower triangle only for rows of H.
 __global__ void __launch_bounds__(256)
-k_chol_update(double* __restrict__ H, int R, int nrows, int j0, int jb, int nHtiles) {
+k_ldl_update(double* __restrict__ H, const double* __restrict__ P, int R, int nrows, int j0,
+             int jb, int nHtiles) {
     const int j1 = j0 + jb;
     int r0, rend;
     if ((int)blockIdx.y < nHtiles) {
@@ -352,7 +397,7 @@ k_chol_update(double* __restrict__ H, int R, int nrows, int j0, int jb, int nHti
     for (int e = tid; e < UT * NB; e += 256) {
         const int r = e / NB, s = e % NB;
         As[r][s] = (r0 + r < rend && s < jb) ? H[(size_t)(r0 + r) * R + j0 + s] : 0.0;
-        Bs[r][s] = (c0 + r < R && s < jb) ? H[(size_t)(c0 + r) * R + j0 + s] : 0.0;
+        Bs[r][s] = (c0 + r < R && s < jb) ? P[(size_t)(c0 + r) * NB + s] : 0.0;
     }
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;
@@ -381,102 +426,69 @@ k_chol_update(double* __restrict__ H, int R, int nrows, int j0, int jb, int nHti
     }
 }
 
-// Inverse of each lower-triangular diagonal block L_JJ (one CTA per block, one column
-// of the inverse per thread).
-__global__ void __launch_bounds__(32) k_tri_inv_diag(const double* __restrict__ H, int R,
-                                                     double* __restrict__ LinvD) {
-    __shared__ double L[NB][NB + 1];
-    __shared__ double X[NB][NB + 1];
-    const int J = blockIdx.x, c0 = J * NB, jb = min(NB, R - c0), t = threadIdx.x;
-    for (int r = 0; r < NB; ++r) {
-        L[r][t] = (r < jb && t <= r) ? H[(size_t)(c0 + r) * R + c0 + t] : 0.0;
-        X[r][t] = 0.0;
-    }
-    __syncwarp();
-    if (t < jb) {
-        X[t][t] = 1.0 / L[t][t];
-        for (int r = t + 1; r < jb; ++r) {
-            double s = 0.0;
-            for (int q = t; q < r; ++q) s = fma(L[r][q], X[q][t], s);
-            X[r][t] = -s / L[r][r];
-        }
-    }
-    __syncwarp();
-    double* out = LinvD + (size_t)J * NB * NB;
-    for (int r = 0; r < NB; ++r) out[r * NB + t] = X[r][t];
-}
-
-// T_J = Linv_JJ L[J, 0:c0_J), written over L[J, 0:c0_J) (one column per thread).
-__global__ void __launch_bounds__(128) k_bsolve_prep(double* __restrict__ H, int R,
-                                                     const double* __restrict__ LinvD) {
-    const int J = blockIdx.y + 1;
-    const int c0 = J * NB;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= c0) return;
-    const int jb = min(NB, R - c0);
-    double l[NB];
-#pragma unroll
-    for (int s = 0; s < NB; ++s) l[s] = (s < jb) ? H[(size_t)(c0 + s) * R + c] : 0.0;
-    const double* Li = LinvD + (size_t)J * NB * NB;
-#pragma unroll
-    for (int a = 0; a < NB; ++a) {
-        if (a >= jb) break;
-        double t = 0.0;
-#pragma unroll
-        for (int s = 0; s <= a; ++s) t = fma(Li[a * NB + s], l[s], t);
-        H[(size_t)(c0 + a) * R + c] = t;
-    }
-}
-
-// Backward step J of A L = Y: A[:, J] = Y_J Linv_JJ and Y[:, 0:c0) -= Y_J T_J.
+// Backward step J of A L = Y (unit lower L): warp 0 solves A_J L_JJ = Y_J for row r by
+// substitution, then every CTA applies Y[r, q] -= sum_c A_J[c] L[c0+c][q] to its chunk of
+// columns q < c0; CTA 0 stores A_J.
 __global__ void __launch_bounds__(128)
-k_bsolve_step(double* __restrict__ Yf, double* __restrict__ A, int R,
-              const double* __restrict__ H, const double* __restrict__ LinvD, int J) {
+k_bsolve_unit(double* __restrict__ Yf, double* __restrict__ A, int R,
+              const double* __restrict__ H, int J) {
     const int c0 = J * NB, jb = min(NB, R - c0);
     const int r = blockIdx.y;
-    __shared__ double y[NB];
-    if (threadIdx.x < NB) y[threadIdx.x] = (threadIdx.x < jb) ? Yf[(size_t)r * R + c0 + threadIdx.x] : 0.0;
+    __shared__ double Lj[NB][NB + 1];
+    __shared__ double a_s[NB];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, t = e % NB;
+        Lj[i][t] = (i < jb && t < i) ? H[(size_t)(c0 + i) * R + c0 + t] : 0.0;
+    }
     __syncthreads();
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < 32) {
+        double y = (lane < jb) ? Yf[(size_t)r * R + c0 + lane] : 0.0;
+        for (int c = jb - 1; c >= 0; --c) {
+            const double ac = __shfl_sync(0xffffffffu, y, c);
+            if (lane < c) y = fma(-ac, Lj[c][lane], y);
+        }
+        a_s[lane] = y;
+        if (blockIdx.x == 0 && lane < jb) A[(size_t)r * R + c0 + lane] = y;
+    }
+    __syncthreads();
+    const int q = blockIdx.x * blockDim.x + tid;
     if (q < c0) {
         double s = 0.0;
-        for (int a = 0; a < jb; ++a) s = fma(y[a], H[(size_t)(c0 + a) * R + q], s);
+        for (int c = 0; c < jb; ++c) s = fma(a_s[c], H[(size_t)(c0 + c) * R + q], s);
         Yf[(size_t)r * R + q] -= s;
-    } else if (q < c0 + jb) {
-        const int c = q - c0;
-        const double* Li = LinvD + (size_t)J * NB * NB;
-        double s = 0.0;
-        for (int a = c; a < jb; ++a) s = fma(y[a], Li[a * NB + c], s);
-        A[(size_t)r * R + c0 + c] = s;
     }
 }
 
-void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* LinvD,
+void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode) {
     const int nrows = R + n;
-    for (int j0 = 0; j0 < R; j0 += NB) {
-        const int jb = std::min(NB, R - j0);
-        const int below = nrows - (j0 + jb);
-        k_chol_panel<<<1 + cdiv(below, PANEL_ROWS), 128, 0, st>>>(Haug, R, nrows, j0, jb, sc, mode);
-        const int j1 = j0 + jb;
-        if (j1 < nrows && j1 < R) {
-            const int nH = cdiv(R - j1, UT);
-            dim3 grid(cdiv(R - j1, UT), nH + cdiv(n, UT));
-            k_chol_update<<<grid, 256, 0, st>>>(Haug, R, nrows, j0, jb, nH);
+    {
+        ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
+        for (int j0 = 0; j0 < R; j0 += NB) {
+            const int jb = std::min(NB, R - j0);
+            const int below = nrows - (j0 + jb);
+            k_ldl_panel<<<1 + cdiv(below, PANEL_ROWS), 128, 0, st>>>(Haug, P, dinv, R, nrows, j0,
+                                                                     jb, sc, mode);
+            count_launch();
+            const int j1 = j0 + jb;
+            if (j1 < R) {
+                const int nH = cdiv(R - j1, UT);
+                dim3 grid(cdiv(R - j1, UT), nH + cdiv(n, UT));
+                k_ldl_update<<<grid, 256, 0, st>>>(Haug, P, R, nrows, j0, jb, nH);
+                count_launch();
+            }
         }
     }
-    const int nJ = cdiv(R, NB);
-    k_tri_inv_diag<<<nJ, 32, 0, st>>>(Haug, R, LinvD);
-    if (nJ > 1) {
-        dim3 grid(cdiv((nJ - 1) * NB, 128), nJ - 1);
-        k_bsolve_prep<<<grid, 128, 0, st>>>(Haug, R, LinvD);
-    }
     if (n <= 0) return;
+    ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
+    const int nJ = cdiv(R, NB);
     double* Yf = Haug + (size_t)R * R;
     for (int J = nJ - 1; J >= 0; --J) {
-        const int c0 = J * NB, jb = std::min(NB, R - c0);
-        dim3 grid(cdiv(c0 + jb, 128), n);
-        k_bsolve_step<<<grid, 128, 0, st>>>(Yf, A, R, Haug, LinvD, J);
+        const int c0 = J * NB;
+        dim3 grid(std::max(1, cdiv(c0, 128)), n);
+        k_bsolve_unit<<<grid, 128, 0, st>>>(Yf, A, R, Haug, J);
+        count_launch();
     }
 }
 
@@ -498,6 +510,8 @@ __global__ void k_normalise(int n, int R, double* __restrict__ A, double* __rest
 }
 
 void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam) {
+    ProfScope prof(st, KC_AUX, 3.0 * n * R, 24.0 * n * R);
+    count_launch();
     k_normalise<<<cdiv(R, 128), 128, 0, st>>>(n, R, A, lam);
 }
 
@@ -562,6 +576,8 @@ k_loss_final(const double* __restrict__ red, int nb, DevScalars* sc, double tol)
 void loss_eval(cudaStream_t st, int Rt, int R, const double* Y, const double* W3,
                const double* W4, const double* lam, const double* const G[4], double* red,
                DevScalars* sc, double tol) {
+    ProfScope prof(st, KC_AUX, 4.0 * Rt * R + 6.0 * R * R, 24.0 * Rt * R + 32.0 * R * R);
+    count_launch(2);
     k_loss_partials<<<RED_BLOCKS, RED_THREADS, 0, st>>>(Rt, R, Y, W3, W4, lam, G[0], G[1],
                                                          G[2], G[3], red);
     k_loss_final<<<1, RED_THREADS, 0, st>>>(red, RED_BLOCKS, sc, tol);
@@ -590,6 +606,8 @@ k_norm_final(const double* __restrict__ red, int nb, DevScalars* sc) {
 
 void sum_hadamard_normG2(cudaStream_t st, long n, const double* Z, const double* U,
                          double* red, DevScalars* sc) {
+    ProfScope prof(st, KC_AUX, 2.0 * n, 16.0 * n);
+    count_launch(2);
     k_sumprod_partials<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, Z, U, red);
     k_norm_final<<<1, RED_THREADS, 0, st>>>(red, RED_BLOCKS, sc);
 }
@@ -608,6 +626,7 @@ __global__ void k_scalars_init(DevScalars* sc, double normG2) {
 }
 
 void scalars_init(cudaStream_t st, DevScalars* sc, double normG2) {
+    count_launch();
     k_scalars_init<<<1, 1, 0, st>>>(sc, normG2);
 }
 
@@ -619,6 +638,7 @@ __global__ void k_fill(double* p, long n, double v) {
 
 void fill(cudaStream_t st, double* p, long n, double v) {
     if (n <= 0) return;
+    count_launch();
     k_fill<<<(int)std::min<long>(cdiv(n, 256), 1024), 256, 0, st>>>(p, n, v);
 }
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "f64.cuh"
+#include "prof.cuh"
 
 namespace thc {
 
@@ -144,6 +145,7 @@ cudaError_t pinv_solve(cudaStream_t st, int R, int n, double* H, const double* M
     const int Rp = R + (R & 1);
     std::vector<double> hbuf(2);
     k_identity<<<256, 256, 0, st>>>(V, R);
+    count_launch();
     int sweeps = 0;
     // rotation parameters (Rp doubles) followed by the two norms of the convergence test
     double* csbuf = nullptr;
@@ -156,8 +158,10 @@ cudaError_t pinv_solve(cudaStream_t st, int R, int n, double* H, const double* M
             dim3 g(cdiv(R, 128), Rp / 2);
             k_jacobi_rows<<<g, 128, 0, st>>>(H, R, Rp, round, csbuf);
             k_jacobi_cols<<<g, 128, 0, st>>>(H, V, R, Rp, round, csbuf);
+            count_launch(3);
         }
         k_offnorm<<<1, 256, 0, st>>>(H, R, d_off);
+        count_launch();
         e = cudaMemcpyAsync(hbuf.data(), d_off, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) break;
         e = cudaStreamSynchronize(st);
@@ -173,6 +177,7 @@ cudaError_t pinv_solve(cudaStream_t st, int R, int n, double* H, const double* M
         dgemm(st, false, n, R, R, M, R, V, nullptr, R, T, R, nullptr, false, nullptr, 0);
         dim3 g(cdiv(R, 128), n);
         k_pinv_apply<<<g, 128, 0, st>>>(T, w, V, A, n, R);
+        count_launch(2);
         e = cudaGetLastError();
     }
     cudaFreeAsync(csbuf, st);

@@ -62,8 +62,12 @@ typedef struct thc_cpd_opts {
     double* history;     /* optional HOST buffer of 2*max_sweeps doubles: (loss, fit)
                             per sweep, NaN for sweeps whose loss was not evaluated */
     int flags_out;       /* out: bit 0 = pseudo-inverse fallback used at least once,
-                                 bit 1 = a sweep was rolled back and replayed */
-    int reserved;
+                                 bit 1 = a sweep was rolled back and replayed,
+                                 bit 2 = the run switched to FP64 sweeps (polish) */
+    int polish_sweeps;   /* split precision, tol <= 0 only: the last polish_sweeps of the
+                            max_sweeps run in FP64. With tol > 0 the run switches to FP64
+                            by itself once |fit_s - fit_{s-1}| < 10 tol and stops at tol,
+                            so that it ends on a fixed point of FP64 ALS */
 } thc_cpd_opts;
 
 /* ||G||_F^2 = sum_PQ Z[P,Q] (S Z S)[P,Q], S = (Xo^T Xo) o (Xv^T Xv): the THC norm in
@@ -110,6 +114,14 @@ thc_cpd_status thc_cpd_als(int o, int v, int Rt, int R,
                            double* const A[4], double* lam, int max_sweeps, double tol,
                            int* sweeps_done, double* loss_host, double* fit_host,
                            thc_cpd_opts* opts);
+
+/* C (M x N, FP64, row-major, device) = A (M x K) B (N x K)^T with A and B row-major FP64
+ * device matrices split into two words per value (opts->precision THC_CPD_BF16X3 or
+ * THC_CPD_TF32X3) and multiplied on the tcgen05 tensor cores with FP32 accumulation:
+ * hi*hi + hi*lo + lo*hi. The contraction kernel of the split-precision MTTKRP
+ * (Sec. 2.1 gradients of Eq. lossF), exposed for testing and reuse. Synchronises. */
+thc_cpd_status thc_cpd_split_gemm(int M, int N, int K, const double* A, const double* B,
+                                  double* C, const thc_cpd_opts* opts);
 
 /* ---- launch accounting and kernel timing (tracing support; the paper has no
  * counterpart: it reports wall-times only) ---------------------------------------- */

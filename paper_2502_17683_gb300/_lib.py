@@ -18,7 +18,7 @@ PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 # every symbol include/thc_cpd.h declares
 EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version", "thc_cpd_launch_count",
-           "thc_cpd_profile", "thc_cpd_profile_read")
+           "thc_cpd_profile", "thc_cpd_profile_read", "thc_cpd_split_gemm")
 KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
 
 
@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p),
                 ("history", ctypes.POINTER(ctypes.c_double)),
                 ("flags_out", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("polish_sweeps", ctypes.c_int)]
 
 
 P = ctypes.c_void_p
@@ -56,6 +56,7 @@ _SIGS = {
     "thc_cpd_loss": [I, I, I, I, P, P, P, PTR4, P, D, DP, DP, OPTS],
     "thc_cpd_als_sweep": [I, I, I, I, P, P, P, PTR4, P, D, DP, DP, OPTS],
     "thc_cpd_als": [I, I, I, I, P, P, P, PTR4, P, I, D, IP, DP, DP, OPTS],
+    "thc_cpd_split_gemm": [I, I, I, P, P, P, OPTS],
 }
 
 _lib = None

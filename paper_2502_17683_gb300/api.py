@@ -15,7 +15,7 @@ from ._lib import (ERR_ARG, KCLASS_NAMES, PRECISIONS, PTR4, KStat, Opts, ThcCpdE
 
 __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_version", "thc_cpd_launch_count", "thc_cpd_profile",
-           "thc_cpd_profile_read", "Opts"]
+           "thc_cpd_profile_read", "thc_cpd_split_gemm", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -28,8 +28,9 @@ def _dev(t: torch.Tensor, name: str, shape=None) -> int:
     return t.data_ptr()
 
 
-def _opts(precision="fp64", stream=None, loss_every=0, history=None) -> Opts:
+def _opts(precision="fp64", stream=None, loss_every=0, history=None, polish_sweeps=0) -> Opts:
     o = Opts()
+    o.polish_sweeps = int(polish_sweeps)
     if isinstance(precision, str):
         if precision not in PRECISIONS:
             raise ThcCpdError(ERR_ARG, f"unknown precision {precision!r}")
@@ -107,13 +108,14 @@ def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", 
 
 
 def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision="fp64",
-                stream=None, loss_every: int = 0, history: bool = False):
+                stream=None, loss_every: int = 0, history: bool = False, polish_sweeps: int = 0):
     o, v, Rt = _dims(Xo, Xv, Z)
     R = A[0].shape[1]
     loss, fit, done = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     hist = (ctypes.c_double * max(1, 2 * max_sweeps))() if history else None
     opts = _opts(precision, stream, loss_every,
-                 ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None)
+                 ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
+                 polish_sweeps)
     check(load().thc_cpd_als(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
                              _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R),
                              _dev(lam, "lam", (R,)), int(max_sweeps), float(tol),
@@ -125,6 +127,18 @@ def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision=
         out["losses"] = h[0::2]
         out["fits"] = h[1::2]
     return out
+
+
+def thc_cpd_split_gemm(A, B, precision="bf16x3", C=None, stream=None):
+    """C = A @ B.T on the tensor cores with split operands (FP64 in and out)."""
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.empty(M, N, dtype=torch.float64, device=A.device)
+    opts = _opts(precision, stream)
+    check(load().thc_cpd_split_gemm(M, N, K, _dev(A, "A"), _dev(B, "B", (N, K)), _dev(C, "C", (M, N)),
+                                    ctypes.byref(opts)))
+    return C
 
 
 def thc_cpd_launch_count() -> int:

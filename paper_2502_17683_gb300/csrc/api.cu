@@ -180,7 +180,8 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     }
     if (need & NEED_NORM) bytes += 3 * Arena::need<double>((size_t)Rt * Rt);
     const bool mixed = c.prec != THC_CPD_FP64;
-    if (mixed) bytes += mixed_ws_bytes(s.o, s.v, Rt, R);
+    const bool tf32 = c.prec == THC_CPD_TF32X3;
+    if (mixed) bytes += mixed_ws_bytes(tf32, s.o, s.v, Rt, R);
     CK(cudaMallocAsync(&c.block, bytes, c.st));
     Arena ar;
     ar.base = (char*)c.block;
@@ -204,7 +205,10 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
         c.T = ar.take<double>((size_t)Rt * Rt);
         c.U = ar.take<double>((size_t)Rt * Rt);
     }
-    if (mixed) mixed_ws_carve(c.mx, ar, s.o, s.v, Rt, R);
+    if (mixed) {
+        mixed_ws_carve(c.mx, ar, tf32, s.o, s.v, Rt, R);
+        CK(mixed_setup(c.mx, c.st, Xo, Xv, Z));
+    }
     fill(c.st, c.ones, R, 1.0);
     CK(cudaGetLastError());
     return THC_CPD_OK;
@@ -285,7 +289,7 @@ void refresh_state(Ctx& c, const double* const A[4]) {
         if (c.prec == THC_CPD_FP64)
             project_fp64(c, k, A[k]);
         else
-            mixed_project(c.mx, c.st, c.s.o, c.s.v, c.s.Rt, c.s.R, k, A[k], c.W, nullptr, c.prec);
+            mixed_project(c.mx, c.st, k, A[k], false);
         gram_fp64(c, k, A[k]);
     }
 }
@@ -298,7 +302,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
     if (c.prec == THC_CPD_FP64)
         backproject_fp64(c, k, safe ? c.Msave : Mrows);
     else
-        mixed_backproject(c.mx, c.st, c.s.o, c.s.v, c.s.Rt, R, k, safe ? c.Msave : Mrows, c.prec);
+        CK(mixed_backproject(c.mx, c.st, k, safe ? c.Msave : Mrows));
     int a, b, d;
     others(k, &a, &b, &d);
     hadamard3(c.st, R, c.G[a], c.G[b], c.G[d], safe ? c.Hsave : c.Haug, c.sc);
@@ -326,7 +330,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
     if (c.prec == THC_CPD_FP64)
         project_fp64(c, k, A[k]);
     else
-        mixed_project(c.mx, c.st, c.s.o, c.s.v, c.s.Rt, R, k, A[k], c.W, c.Y, c.prec);
+        CK(mixed_project(c.mx, c.st, k, A[k], true));
     CK(cudaGetLastError());
     return THC_CPD_OK;
 }
@@ -339,7 +343,7 @@ thc_cpd_status sweep(Ctx& c, double* const A[4], double* lam, bool safe, bool ev
             if (c.prec == THC_CPD_FP64)
                 zgemm_fp64(c, k / 2);
             else
-                mixed_zgemm(c.mx, c.st, c.s.Rt, c.s.R, k / 2, c.W, c.prec);
+                CK(mixed_zgemm(c.mx, c.st, k / 2));
         }
         CKS(mode_update(c, A, lam, k, safe, used_pinv));
     }
@@ -400,12 +404,24 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     CKS(obtain_norm(c, normG2, &nG2));
     refresh_state(c, A);
     const int loss_every = (opts && opts->loss_every > 0) ? opts->loss_every : 0;
+    const int polish = (opts && opts->polish_sweeps > 0 && tol <= 0.0) ? opts->polish_sweeps : 0;
+    const bool split_run = c.prec != THC_CPD_FP64;
     int flags = 0;
     int done_sweeps = 0;
     DevScalars h;
     h.loss = nan("");
     h.fit = nan("");
+    double fit1 = nan(""), fit2 = nan("");  // fits of the last two evaluated sweeps
     for (int sw = 1; sw <= max_sweeps; ++sw) {
+        // split precision hands over to FP64 sweeps (polish) near convergence or for the
+        // last polish_sweeps of a fixed-length run
+        if (split_run && c.prec != THC_CPD_FP64 &&
+            ((polish > 0 && sw > max_sweeps - polish) ||
+             (tol > 0.0 && isfinite(fit1) && isfinite(fit2) && fabs(fit1 - fit2) < 10.0 * tol))) {
+            c.prec = THC_CPD_FP64;
+            refresh_state(c, A);
+            flags |= 4;
+        }
         bool eval = true;
         if (c.prec != THC_CPD_FP64) {
             if (loss_every > 0)
@@ -437,6 +453,10 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
         }
         if (used) flags |= 1;
         done_sweeps = sw;
+        if (eval) {
+            fit2 = fit1;
+            fit1 = h.fit;
+        }
         if (opts && opts->history) {
             opts->history[2 * (sw - 1)] = eval ? h.loss : nan("");
             opts->history[2 * (sw - 1) + 1] = eval ? h.fit : nan("");
@@ -453,6 +473,10 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     if (loss_host) *loss_host = h.loss;
     if (fit_host) *fit_host = h.fit;
     CK(cudaStreamSynchronize(c.st));
+    if (c.prec != THC_CPD_FP64) {
+        if (int e = mixed_take_error())
+            return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
+    }
     return THC_CPD_OK;
 }
 
@@ -494,18 +518,63 @@ thc_cpd_status thc_cpd_mttkrp(int o, int v, int Rt, int R, const double* Xo, con
         zgemm_fp64(c, mode / 2);
         backproject_fp64(c, mode, M);
     } else {
-        for (int k = 0; k < 4; ++k)
-            if (k != mode) mixed_project(c.mx, c.st, o, v, Rt, R, k, A[k], c.W, nullptr, c.prec);
-        // the projection epilogues above produce the Hadamard operands of this mode
-        mixed_zgemm(c.mx, c.st, Rt, R, mode / 2, c.W, c.prec);
-        if (mode == 1 || mode == 3) {
-            // partner product for the second mode of the half: W_partner o Y
-            mixed_partner(c.mx, c.st, Rt, R, mode, c.W, c.prec);
+        // projections of the three other modes; their epilogues leave the Hadamard
+        // operand of the Z-GEMM (P) in place, the Z-GEMM epilogue the one of modes 0/2
+        // the Hadamard operand P of the wanted half must be written last:
+        // half 0 needs P34 (from mode 3), half 1 needs P12 (from mode 1)
+        static const int order[2][4] = {{0, 1, 2, 3}, {3, 0, 1, 2}};
+        for (int i = 0; i < 4; ++i) {
+            const int k = order[mode / 2][i];
+            if (k != mode) CK(mixed_project(c.mx, c.st, k, A[k], false));
         }
-        mixed_backproject(c.mx, c.st, o, v, Rt, R, mode, M, c.prec);
+        CK(mixed_zgemm(c.mx, c.st, mode / 2));
+        if (mode == 1 || mode == 3) CK(mixed_partner(c.mx, c.st, mode));
+        CK(mixed_backproject(c.mx, c.st, mode, M));
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c.st));
+    if (int e = mixed_take_error())
+        return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
+    return THC_CPD_OK;
+}
+
+thc_cpd_status thc_cpd_split_gemm(int M, int N, int K, const double* A, const double* B, double* C,
+                                  const thc_cpd_opts* opts) {
+    if (M < 1 || N < 1 || K < 1 || (long)M * K >= 0x7fffffffL || (long)N * K >= 0x7fffffffL ||
+        (long)M * N >= 0x7fffffffL)
+        return set_err(THC_CPD_ERR_SHAPE, "bad GEMM shape %d x %d x %d", M, N, K);
+    if (!A || !B || !C) return set_err(THC_CPD_ERR_ARG, "A, B and C must be non-null");
+    CKS(check_prec(opts));
+    const int prec = opts ? opts->precision : THC_CPD_FP64;
+    if (prec == THC_CPD_FP64) return set_err(THC_CPD_ERR_ARG, "split GEMM needs a split precision");
+    const bool tf32 = prec == THC_CPD_TF32X3;
+    cudaStream_t st = stream_of(opts);
+    const int esz = tf32 ? 4 : 2, pitch = split_pitch(tf32, K);
+    const size_t a = Arena::need<uint8_t>((size_t)M * pitch * esz);
+    const size_t b = Arena::need<uint8_t>((size_t)N * pitch * esz);
+    void* block = nullptr;
+    CK(cudaMallocAsync(&block, 2 * a + 2 * b, st));
+    Arena ar;
+    ar.base = (char*)block;
+    SplitMat sa, sb;
+    sa.hi = ar.take<uint8_t>((size_t)M * pitch * esz);
+    sa.lo = ar.take<uint8_t>((size_t)M * pitch * esz);
+    sb.hi = ar.take<uint8_t>((size_t)N * pitch * esz);
+    sb.lo = ar.take<uint8_t>((size_t)N * pitch * esz);
+    sa.rows = M; sb.rows = N;
+    sa.cols = sb.cols = K;
+    sa.pitch = sb.pitch = pitch;
+    split_rows(st, tf32, A, K, M, K, sa);
+    split_rows(st, tf32, B, K, N, K, sb);
+    TcEpilogue ep;
+    ep.out_f64t = C;  // D'[n][m] = B[n] . A[m] stored transposed: C[m][n]
+    ep.ld_f64t = N;
+    cudaError_t e = tc_gemm(st, tf32, sb, sa, N, M, K, ep);
+    cudaFreeAsync(block, st);
+    CK(e);
+    CK(cudaStreamSynchronize(st));
+    if (int te = mixed_take_error())
+        return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", te);
     return THC_CPD_OK;
 }
 

@@ -1,0 +1,478 @@
+// tcgen05 split-operand GEMM for sm_103a (see tc_gemm.cuh).
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "prof.cuh"
+#include "tc_gemm.cuh"
+
+namespace thc {
+
+__device__ int g_tc_error = 0;
+
+namespace {
+
+constexpr int BM = 128;             // MMA M (one CTA, cta_group::1)
+constexpr int KBYTES = 128;         // bytes of K per stage (one 128-byte swizzle atom)
+constexpr int TILE_A = BM * KBYTES;  // 16 KB
+constexpr int TMEM_COLS = 256;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr int NTHREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM, warps 2..5: epilogue
+
+// ---- PTX wrappers ------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: records `code` in the error word and returns false when it gives up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int code) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(&g_tc_error, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+template <bool TF32>
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+    if (TF32) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    }
+}
+
+// 32 lanes x 32 bits, 16 consecutive columns per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA with the
+// 128-byte swizzle: 8-row x 128-byte atoms, 1024 bytes apart (stride byte offset);
+// the leading byte offset is unused for this layout; descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: D FP32, A/B BF16 (kind::f16) or TF32 (kind::tf32), both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(bool tf32, int M, int N) {
+    return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+struct KArgs {
+    int M, N, nkb, BN, stages;
+    TcEpilogue ep;
+    void* out_hi;
+    void* out_lo;
+    int ld_split;
+};
+
+template <bool TF32>
+__device__ __forceinline__ void store_split(void* hi, void* lo, size_t idx, float x) {
+    if (TF32) {
+        // round to the 10-bit TF32 mantissa (nearest, ties away), residual likewise
+        const uint32_t u = __float_as_uint(x);
+        const float h = __uint_as_float((u + 0x1000u) & 0xFFFFE000u);
+        const float r = x - h;
+        const uint32_t ur = __float_as_uint(r);
+        const float l = __uint_as_float((ur + 0x1000u) & 0xFFFFE000u);
+        ((float*)hi)[idx] = h;
+        ((float*)lo)[idx] = l;
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        ((__nv_bfloat16*)hi)[idx] = h;
+        ((__nv_bfloat16*)lo)[idx] = l;
+    }
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+          const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+          const KArgs args) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte alignment for the swizzled tiles
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int BN = args.BN, S = args.stages;
+    const int tileB = BN * KBYTES;
+    const int stage_bytes = 2 * TILE_A + 2 * tileB;
+    uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
+    uint64_t* empty = full + S;
+    uint64_t* tmem_full = empty + S;
+    uint32_t* tmem_slot = (uint32_t*)(tmem_full + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kel = TF32 ? 32 : 64;  // elements per 128-byte K block
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tmem_full, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        const uint32_t tx = (uint32_t)stage_bytes;
+        for (int kb = 0; kb < args.nkb; ++kb) {
+            const int s = kb % S;
+            if (!mbar_wait(&empty[s], ((kb / S) & 1) ^ 1, 1)) break;
+            uint8_t* st = smem + (size_t)s * stage_bytes;
+            mbar_expect_tx(&full[s], tx);
+            tma_load_2d(st, &tAh, &full[s], kb * kel, m0);
+            tma_load_2d(st + TILE_A, &tAl, &full[s], kb * kel, m0);
+            tma_load_2d(st + 2 * TILE_A, &tBh, &full[s], kb * kel, n0);
+            tma_load_2d(st + 2 * TILE_A + tileB, &tBl, &full[s], kb * kel, n0);
+        }
+        // drain: wait until the consumer released every stage still in flight
+        for (int kb = max(0, args.nkb - S); kb < args.nkb; ++kb)
+            mbar_wait(&empty[kb % S], (kb / S) & 1, 2);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = make_idesc(TF32, BM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < args.nkb && ok; ++kb) {
+            const int s = kb % S;
+            if (!mbar_wait(&full[s], (kb / S) & 1, 3)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            uint8_t* st = smem + (size_t)s * stage_bytes;
+            const uint64_t ah = sw128_desc(smem_u32(st));
+            const uint64_t al = sw128_desc(smem_u32(st + TILE_A));
+            const uint64_t bh = sw128_desc(smem_u32(st + 2 * TILE_A));
+            const uint64_t bl = sw128_desc(smem_u32(st + 2 * TILE_A + tileB));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {  // 4 MMAs of 32 bytes of K per stage
+                const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                tc_mma<TF32>(tmem, ah + o, bh + o, idesc, (kb | kk) ? 1u : 0u);
+                tc_mma<TF32>(tmem, ah + o, bl + o, idesc, 1u);
+                tc_mma<TF32>(tmem, al + o, bh + o, idesc, 1u);
+            }
+            tc_commit(&empty[s]);
+        }
+        tc_commit(tmem_full);
+    } else if (warp >= 2) {
+        // ---- epilogue: TMEM -> registers -> fused outputs ----
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        const bool ok = mbar_wait(tmem_full, 0, 4);
+        tc_fence_after();
+        const int m = m0 + 32 * q + lane;
+        const TcEpilogue& ep = args.ep;
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+            if (!ok || m >= args.M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = n0 + c + j;
+                if (n >= args.N) break;
+                const float d = v[j];
+                if (ep.out_f32) ep.out_f32[(size_t)m * ep.ld_f32 + n] = d;
+                if (ep.mul)
+                    store_split<TF32>(args.out_hi, args.out_lo, (size_t)m * args.ld_split + n,
+                                      d * ep.mul[(size_t)m * ep.ld_mul + n]);
+                if (ep.out_f64t) ep.out_f64t[(size_t)n * ep.ld_f64t + m] = (double)d;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---- host side ---------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool load_encode() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode != nullptr;
+}
+
+bool make_map(CUtensorMap* map, bool tf32, const void* base, int rows, int cols, int pitch,
+              int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const int esz = tf32 ? 4 : 2;
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(KBYTES / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int g_max_smem = 0;
+
+}  // namespace
+
+bool tc_available() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return false;
+    if (!(p.major == 10 && p.minor == 3)) return false;
+    g_max_smem = (int)p.sharedMemPerBlockOptin;
+    return load_encode();
+}
+
+int tc_take_error() {
+    int h = 0, z = 0;
+    cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int));
+    if (h) cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+    return h;
+}
+
+cudaError_t tc_gemm(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMat& B, int M, int N,
+                    int K, const TcEpilogue& ep) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (!g_encode && !load_encode()) return cudaErrorNotSupported;
+    if (g_max_smem == 0) tc_available();
+    // tile N: a multiple of 16 up to 256, as wide as keeps about one CTA per SM busy
+    const int mt = cdiv(M, BM);
+    int cap = 64;
+    for (int cand : {256, 128}) {
+        if ((long)mt * cdiv(N, cand) >= 120) {
+            cap = cand;
+            break;
+        }
+    }
+    if (N <= cap) cap = std::max(16, ((N + 15) / 16) * 16);
+    const int BN = std::min(256, (cdiv(N, cdiv(N, cap)) + 15) / 16 * 16);
+    const int tileB = BN * KBYTES;
+    const int stage_bytes = 2 * TILE_A + 2 * tileB;
+    const int nkb = std::max(1, cdiv((long)K * (tf32 ? 4 : 2), KBYTES));
+    const int avail = g_max_smem - 1024 - 256;
+    const int stages = std::max(2, std::min(6, avail / stage_bytes));
+    const size_t smem = 1024 + (size_t)stages * stage_bytes + 256;
+    CUtensorMap mAh, mAl, mBh, mBl;
+    if (!make_map(&mAh, tf32, A.hi, M, K, A.pitch, BM) || !make_map(&mAl, tf32, A.lo, M, K, A.pitch, BM) ||
+        !make_map(&mBh, tf32, B.hi, N, K, B.pitch, BN) || !make_map(&mBl, tf32, B.lo, N, K, B.pitch, BN))
+        return cudaErrorInvalidValue;
+    KArgs args;
+    args.M = M;
+    args.N = N;
+    args.nkb = nkb;
+    args.BN = BN;
+    args.stages = stages;
+    args.ep = ep;
+    args.out_hi = ep.out_split ? ep.out_split->hi : nullptr;
+    args.out_lo = ep.out_split ? ep.out_split->lo : nullptr;
+    args.ld_split = ep.out_split ? ep.out_split->pitch : 0;
+    dim3 grid(cdiv(N, BN), cdiv(M, BM));
+    ProfScope prof(st, KC_TC, 2.0 * M * (double)N * K);
+    count_launch();
+    if (tf32) {
+        cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tc_gemm<true><<<grid, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
+    } else {
+        cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tc_gemm<false><<<grid, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
+    }
+    return cudaGetLastError();
+}
+
+// ---- split conversions ---------------------------------------------------------------
+int split_kblock(bool tf32) { return tf32 ? 32 : 64; }
+int split_pitch(bool tf32, int cols) {
+    const int kb = split_kblock(tf32);
+    return std::max(kb, ((cols + kb - 1) / kb) * kb);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void store_split_d(void* hi, void* lo, size_t idx, double x) {
+    if (TF32) {
+        const float xf = (float)x;
+        const uint32_t u = __float_as_uint(xf);
+        const float h = __uint_as_float((u + 0x1000u) & 0xFFFFE000u);
+        const float r = (float)(x - (double)h);
+        const float l = __uint_as_float((__float_as_uint(r) + 0x1000u) & 0xFFFFE000u);
+        ((float*)hi)[idx] = h;
+        ((float*)lo)[idx] = l;
+    } else {
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+        ((__nv_bfloat16*)hi)[idx] = h;
+        ((__nv_bfloat16*)lo)[idx] = l;
+    }
+}
+
+template <bool TF32>
+__global__ void k_split_rows(const double* __restrict__ src, int ld, int rows, int cols, void* hi,
+                             void* lo, int pitch) {
+    const long n = (long)rows * cols;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        store_split_d<TF32>(hi, lo, (size_t)r * pitch + c, src[(size_t)r * ld + c]);
+    }
+}
+
+// 32 x 32 tiles through shared memory so that reads and writes are both coalesced
+template <bool TF32>
+__global__ void k_split_transpose(const double* __restrict__ src, int ld, int rows, int cols,
+                                  void* hi, void* lo, int pitch) {
+    __shared__ double t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? src[(size_t)r * ld + c] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) store_split_d<TF32>(hi, lo, (size_t)c * pitch + r, t[threadIdx.x][i]);
+    }
+}
+
+template <bool TF32>
+__global__ void k_split_hadamard(const float* __restrict__ a, const float* __restrict__ b, int ld,
+                                 int rows, int cols, void* hi, void* lo, int pitch) {
+    const long n = (long)rows * cols;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        const size_t o = (size_t)r * ld + c;
+        store_split<TF32>(hi, lo, (size_t)r * pitch + c, a[o] * b[o]);
+    }
+}
+
+void split_rows(cudaStream_t st, bool tf32, const double* src, int ld, int rows, int cols,
+                SplitMat& d) {
+    const long n = (long)rows * cols;
+    const int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    count_launch();
+    if (tf32)
+        k_split_rows<true><<<blocks, 256, 0, st>>>(src, ld, rows, cols, d.hi, d.lo, d.pitch);
+    else
+        k_split_rows<false><<<blocks, 256, 0, st>>>(src, ld, rows, cols, d.hi, d.lo, d.pitch);
+}
+
+void split_transpose(cudaStream_t st, bool tf32, const double* src, int ld, int rows, int cols,
+                     SplitMat& d) {
+    dim3 grid(cdiv(cols, 32), cdiv(rows, 32)), block(32, 8);
+    count_launch();
+    if (tf32)
+        k_split_transpose<true><<<grid, block, 0, st>>>(src, ld, rows, cols, d.hi, d.lo, d.pitch);
+    else
+        k_split_transpose<false><<<grid, block, 0, st>>>(src, ld, rows, cols, d.hi, d.lo, d.pitch);
+}
+
+void split_hadamard(cudaStream_t st, bool tf32, const float* a, const float* b, int ld, int rows,
+                    int cols, SplitMat& d) {
+    const long n = (long)rows * cols;
+    const int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    count_launch();
+    if (tf32)
+        k_split_hadamard<true><<<blocks, 256, 0, st>>>(a, b, ld, rows, cols, d.hi, d.lo, d.pitch);
+    else
+        k_split_hadamard<false><<<blocks, 256, 0, st>>>(a, b, ld, rows, cols, d.hi, d.lo, d.pitch);
+}
+
+}  // namespace thc

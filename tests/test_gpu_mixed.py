@@ -1,0 +1,127 @@
+"""Split-precision tensor-core path (tcgen05, BF16x3 / TF32x3) vs FP64 references.
+
+Tolerances from the split arithmetic: an FP64 value x is stored as hi + lo words, so
+|x - hi - lo| <= u^2 |x| with u = 2^-9 (BF16) or 2^-12 (TF32, 11 significant bits with the
+implicit one, rounding to nearest gives half an ulp); the dropped lo*lo term is of the
+same size, and the FP32 accumulator adds about sqrt(K) * 2^-24 relative to sum |a b|.
+Elementwise GEMM errors are checked against c * (|A| |B|^T) with
+c = 4 u^2 + 8 sqrt(K) 2^-24. The chained MTTKRP is checked against the largest output
+entry with a per-precision bound (three chained GEMMs), and a full ALS run against the
+FP64 oracle's fit at equal sweeps."""
+import numpy as np
+import pytest
+
+from oracle import thc_cpd as O
+from tests._util import rel, to_dev
+from thc_inputs import make_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U2 = {"bf16x3": 2.0 ** -18, "tf32x3": 2.0 ** -24}
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import api as a
+    return a
+
+
+def gemm_tol(prec, K):
+    return 4 * U2[prec] + 8 * np.sqrt(K) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (7, 5, 3), (128, 16, 64), (130, 33, 65),
+                                   (200, 300, 500), (720, 480, 480), (1800, 1200, 1200)])
+def test_split_gemm(api, prec, shape):
+    M, N, K = shape
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.standard_normal((M, K)) * rng.uniform(0.1, 10.0, (M, 1))
+    B = rng.standard_normal((N, K))
+    C = api.thc_cpd_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), prec)
+    ref = A @ B.T
+    bound = gemm_tol(prec, K) * (np.abs(A) @ np.abs(B).T)
+    err = np.abs(C.cpu().numpy() - ref)
+    assert np.all(err <= bound + 1e-300), float(np.max(err / (bound + 1e-300)))
+    # it is a split computation, not plain FP32 or BF16: the error is far below one BF16 ulp
+    assert np.max(err / (np.abs(A) @ np.abs(B).T + 1e-300)) < 2.0 ** -12
+
+
+MTTKRP_TOL = {"bf16x3": 2e-4, "tf32x3": 2e-5}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("shape", [(2, 3, 5, 4), (5, 15, 60, 80), (7, 33, 97, 131),
+                                   (20, 100, 480, 720)])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_mixed_mttkrp(api, prec, shape, mode):
+    o, v, Rt, R = shape
+    p = make_problem(o, v, Rt, R, seed=11)
+    Z = p.Z + 0.3 * np.triu(p.Z, 1)
+    d = to_dev(p, torch)
+    Zd = torch.from_numpy(np.ascontiguousarray(Z)).cuda()
+    M = api.thc_cpd_mttkrp(d["Xo"], d["Xv"], Zd, d["A"], mode, precision=prec)
+    ref = O.mttkrp(p.Xo, p.Xv, Z, p.A, mode)
+    assert rel(M.cpu().numpy(), ref) <= MTTKRP_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_mixed_one_sweep_identical_inputs(api, prec):
+    # per-step parity: each mode update is an exact block minimiser, so an MTTKRP error
+    # eps moves the fit only at second order; one sweep from identical inputs matches the
+    # FP64 oracle's fit to 1e-6 relative at the bench workload
+    o, v, Rt, R = 20, 100, 480, 720
+    p = make_problem(o, v, Rt, R, seed=0)
+    d = to_dev(p, torch)
+    lam = torch.ones(R, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 1, 0.0, precision=prec)
+    _, _, _, fit_ref, _ = O.als_sweep(p.Xo, p.Xv, p.Z, p.A)
+    assert abs(out["fit"] - fit_ref) <= 1e-6 * abs(fit_ref)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_mixed_50_sweeps_report(api, prec):
+    # 50 sweeps of the unconverged bench workload: the split-precision trajectory drifts
+    # from the FP64 one (ALS amplifies the per-sweep ~1e-5 perturbation along an
+    # unconverged path) but the fit it reports is the exact FP64 loss of its factors
+    o, v, Rt, R, sweeps = 20, 100, 480, 720, 50
+    p = make_problem(o, v, Rt, R, seed=0)
+    d = to_dev(p, torch)
+    lam = torch.ones(R, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, sweeps, 0.0, precision=prec)
+    ref = O.als(p.Xo, p.Xv, p.Z, p.A, sweeps)
+    assert abs(out["fit"] - ref["fits"][-1]) <= 2e-3
+    loss, fit = api.thc_cpd_loss(d["Xo"], d["Xv"], d["Z"], d["A"], lam)
+    assert abs(fit - out["fit"]) <= 1e-12
+    A = [a.cpu().numpy() for a in d["A"]]
+    nG2 = O.thc_norm2(p.Xo, p.Xv, p.Z)
+    assert abs(O.loss_factor_form(p.Xo, p.Xv, p.Z, A, lam.cpu().numpy(), nG2) - loss) <= 1e-11 * nG2
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_mixed_with_fp64_polish_reaches_fp64_converged_fit(api, prec):
+    # converged comparison: split-precision sweeps until |dfit| < 10 tol, then FP64 sweeps
+    # to tol; both runs end on fixed points of FP64 ALS of the planted problem
+    from thc_inputs import make_planted
+    p, _ = make_planted(5, 15, 12, 12, seed=2, independent=True)
+    d = to_dev(p, torch)
+    lam = torch.ones(12, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 2000, 1e-9, precision=prec)
+    ref = O.als(p.Xo, p.Xv, p.Z, p.A, 2000, tol=1e-9)
+    assert out["flags"] & 4
+    assert abs(out["fit"] - ref["fits"][-1]) <= 1e-6 * abs(ref["fits"][-1])
+
+
+def test_mixed_small_workload_trajectory(api):
+    p = make_problem(5, 15, 60, 80, seed=0)
+    d = to_dev(p, torch)
+    lam = torch.ones(80, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 25, 0.0, precision="bf16x3",
+                          loss_every=1, history=True)
+    ref = O.als(p.Xo, p.Xv, p.Z, p.A, 25)
+    fits = np.array(out["fits"])
+    assert np.all(np.isfinite(fits))
+    assert np.max(np.abs(fits - np.array(ref["fits"]))) <= 1e-4

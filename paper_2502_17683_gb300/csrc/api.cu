@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <string>
@@ -10,6 +11,7 @@
 #include "thc_cpd.h"
 #include "f64.cuh"
 #include "mixed.cuh"
+#include "prof.cuh"
 
 namespace {
 
@@ -131,8 +133,19 @@ struct Ctx {
     double* pT = nullptr;
     void* safe_block = nullptr;
     MixedWs mx;
+    // CUDA graphs of one sweep (index: loss evaluated or not) on an internal stream
+    cudaStream_t gst = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gprec[2] = {-1, -1};
+    long glaunch[2] = {0, 0};
 
     ~Ctx() {
+        for (auto& g : gexec)
+            if (g) cudaGraphExecDestroy(g);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (gst) cudaStreamDestroy(gst);
         if (safe_block) cudaFreeAsync(safe_block, st);
         if (block) cudaFreeAsync(block, st);
     }
@@ -361,6 +374,60 @@ thc_cpd_status sweep(Ctx& c, double* const A[4], double* lam, bool safe, bool ev
     return THC_CPD_OK;
 }
 
+// One optimistic sweep, replayed from a CUDA graph when possible. The graph is captured
+// on an internal non-blocking stream (the legacy default stream cannot be captured) and
+// ordered after / before the caller's stream with events.
+thc_cpd_status fast_sweep(Ctx& c, double* const A[4], double* lam, bool eval, double tol,
+                          bool* use_graph) {
+    if (*use_graph) {
+        const int gi = eval ? 1 : 0;
+        if (c.gexec[gi] && c.gprec[gi] != c.prec) {
+            cudaGraphExecDestroy(c.gexec[gi]);
+            c.gexec[gi] = nullptr;
+        }
+        if (!c.gst) {
+            if (cudaStreamCreateWithFlags(&c.gst, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming) != cudaSuccess) {
+                *use_graph = false;
+                cudaGetLastError();
+            }
+        }
+        if (*use_graph && !c.gexec[gi]) {
+            cudaStream_t caller = c.st;
+            c.st = c.gst;
+            const long l0 = thc_cpd_launch_count();
+            cudaGraph_t graph = nullptr;
+            bool ok = cudaStreamBeginCapture(c.gst, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            int used = 0;
+            thc_cpd_status st = ok ? sweep(c, A, lam, false, eval, tol, &used) : THC_CPD_ERR_CUDA;
+            if (ok) ok = cudaStreamEndCapture(c.gst, &graph) == cudaSuccess && st == THC_CPD_OK;
+            if (ok) ok = cudaGraphInstantiate(&c.gexec[gi], graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            c.st = caller;
+            c.glaunch[gi] = thc_cpd_launch_count() - l0;
+            c.gprec[gi] = c.prec;
+            if (!ok) {
+                if (c.gexec[gi]) cudaGraphExecDestroy(c.gexec[gi]);
+                c.gexec[gi] = nullptr;
+                *use_graph = false;
+                cudaGetLastError();  // clear a capture error; run the sweep directly
+            }
+        }
+        if (*use_graph) {
+            CK(cudaEventRecord(c.ev_in, c.st));
+            CK(cudaStreamWaitEvent(c.gst, c.ev_in, 0));
+            CK(cudaGraphLaunch(c.gexec[gi], c.gst));
+            CK(cudaEventRecord(c.ev_out, c.gst));
+            CK(cudaStreamWaitEvent(c.st, c.ev_out, 0));
+            count_launch((int)c.glaunch[gi]);
+            return THC_CPD_OK;
+        }
+    }
+    int used = 0;
+    return sweep(c, A, lam, false, eval, tol, &used);
+}
+
 thc_cpd_status read_scalars(Ctx& c, DevScalars* out) {
     DevScalars* h = host_scalars();
     if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
@@ -412,6 +479,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     h.loss = nan("");
     h.fit = nan("");
     double fit1 = nan(""), fit2 = nan("");  // fits of the last two evaluated sweeps
+    bool use_graph = !prof_on() && getenv("THC_CPD_NO_GRAPH") == nullptr;
     for (int sw = 1; sw <= max_sweeps; ++sw) {
         // split precision hands over to FP64 sweeps (polish) near convergence or for the
         // last polish_sweeps of a fixed-length run
@@ -435,7 +503,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
         CK(cudaMemcpyAsync(c.lamsnap, lam, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
         CK(cudaMemcpyAsync(c.sc_snap, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
         int used = 0;
-        CKS(sweep(c, A, lam, false, eval, tol, &used));
+        CKS(fast_sweep(c, A, lam, eval, tol, &use_graph));
         CKS(read_scalars(c, &h));
         if (h.fail_mask) {
             // a Cholesky pivot failed somewhere in this sweep: roll back and replay the

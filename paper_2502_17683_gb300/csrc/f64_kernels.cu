@@ -280,33 +280,65 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   block column for the trailing update.
 // ------------------------------------------------------------------------------------
 constexpr int NB = 32;          // block size of the factorisation
-constexpr int PANEL_ROWS = 8;   // panel rows per CTA (two per warp)
-constexpr int UT = 32;          // trailing-update tile
+constexpr int UT = 16;          // trailing-update tile (one output per thread)
 
-// Reciprocal by Newton-Raphson (y <- y + y (1 - d y), quadratic convergence) from an
-// FP32 seed: two steps take a 24-bit seed past FP64 precision. Outside the FP32 range
-// the plain division is used.
+// Reciprocal 1/d of a positive normal double by Newton-Raphson, y <- y + y (1 - d y)
+// (quadratic convergence), from a seed built with integer operations: the FP32
+// reciprocal of the leading 20 mantissa bits, rescaled by the exponent. Two steps take
+// the ~20-bit seed past FP64 precision. Only d > 0 reaches here (the pivot test runs
+// first); the seed is exact in exponent for 2^-1000 < d < 2^1000.
 __device__ __forceinline__ double recip_nr(double d) {
-    if (!(fabs(d) > 1e-30 && fabs(d) < 1e30)) return 1.0 / d;
-    double y = (double)__frcp_rn((float)d);
-    double e = fma(-d, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-d, y, 1.0);
-    return fma(y, e, y);
+    const long long bits = __double_as_longlong(d);
+    const int e = (int)((bits >> 52) & 0x7FF);         // biased exponent of d
+    const unsigned mhi = (unsigned)((bits >> 32) & 0xFFFFF);  // top 20 mantissa bits
+    const float m = __uint_as_float(0x3F800000u | (mhi << 3));  // in [1, 2)
+    const float r = __frcp_rn(m);                       // in (0.5, 1]
+    const unsigned rb = __float_as_uint(r);
+    const int er = (int)((rb >> 23) & 0xFF) - 127;      // -1 or 0
+    // 1/d = r * 2^-(e - 1023)
+    const long long yb = ((long long)(er - (e - 1023) + 1023) << 52) |
+                         ((long long)(rb & 0x7FFFFF) << 29);
+    double y = __longlong_as_double(yb);
+    double t = fma(-d, y, 1.0);
+    y = fma(y, t, y);
+    t = fma(-d, y, 1.0);
+    return fma(y, t, y);
+}
+
+// d > tau with d, tau >= 0 finite-or-not, decided on the integer pipe: non-negative
+// doubles order like their bit patterns; NaN / inf / negative fail.
+__device__ __forceinline__ bool pivot_ok(double d, double tau) {
+    const long long bd = __double_as_longlong(d), bt = __double_as_longlong(tau);
+    const bool finite_pos = bd > 0 && bd < 0x7FF0000000000000LL;
+    return finite_pos && bd > bt && ((bd >> 52) & 0x7FF) > 24 && ((bd >> 52) & 0x7FF) < 2022;
+}
+
+// (r, s) pairs of the strictly lower triangle ordered by s descending, so that the
+// pairs with s > c form the prefix of length (31 - c) (32 - c) / 2.
+__device__ __forceinline__ void pair_of(int e, int* r, int* s) {
+    // s from 31 down: group for s holds r = s..31 -> (32 - s) entries
+    int cnt = 0, ss = NB - 1;
+    for (;; --ss) {
+        const int g = NB - ss;
+        if (e < cnt + g) break;
+        cnt += g;
+    }
+    *s = ss;
+    *r = ss + (e - cnt);
 }
 
 // LDL^T of the jb x jb diagonal block held in Ds (lower part); on return Ls holds the
 // unit-lower L_jj (strictly lower part), Ds[c][c] the pivots d_c and dinv_s[c] = 1/d_c.
 // Returns (in thread 0) whether a pivot failed the test d > tau.
-__device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* dinv_s, int jb,
-                         double tau) {
+__device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* dinv_s,
+                         const unsigned short* pairs, int jb, double tau) {
     __shared__ int bad;
     const int tid = threadIdx.x;
     if (tid == 0) bad = 0;
     for (int c = 0; c < jb; ++c) {
         if (tid == 0) {
             double d = Ds[c][c];
-            if (!(d > tau) || !isfinite(d)) {  // NaN fails the comparison
+            if (!pivot_ok(d, tau)) {
                 bad = 1;
                 d = 1.0;  // keep going; the caller replays this mode with the pseudo-inverse
                 Ds[c][c] = d;
@@ -315,14 +347,16 @@ __device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* din
         }
         __syncthreads();
         const double inv = dinv_s[c];
-        for (int r = c + 1 + tid; r < jb; r += blockDim.x) Ls[r][c] = Ds[r][c] * inv;
-        __syncthreads();
-        // trailing update of the block: D[r][s] -= L[r][c] * X[s][c], c < s <= r
-        const int lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-        const int s = c + 1 + lane;
-        if (s < jb) {
-            const double xs = Ds[s][c];
-            for (int r = s + w; r < jb; r += nw) Ds[r][s] = fma(-Ls[r][c], xs, Ds[r][s]);
+        // D[r][s] -= (D[r][c] / d_c) D[s][c] for c < s <= r < jb, pairs spread evenly
+        const int hi = NB - 1 - c;                  // s in (c, 31]
+        const int npair = hi * (hi + 1) / 2;
+        for (int e = tid; e < npair; e += blockDim.x) {
+            const int rs = pairs[e];
+            const int r = rs >> 8, ss = rs & 0xFF;
+            if (r >= jb) continue;
+            const double l = Ds[r][c] * inv;
+            if (ss == c + 1) Ls[r][c] = l;
+            Ds[r][ss] = fma(-l, Ds[ss][c], Ds[r][ss]);
         }
         __syncthreads();
     }
@@ -331,10 +365,11 @@ __device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* din
 
 __global__ void __launch_bounds__(128)
 k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__ dinv, int R,
-            int nrows, int j0, int jb, DevScalars* sc, int mode) {
+            int nrows, int j0, int jb, int rows_per_cta, DevScalars* sc, int mode) {
     __shared__ double Ds[NB][NB + 1];
     __shared__ double Ls[NB][NB + 1];
     __shared__ double dinv_s[NB];
+    __shared__ unsigned short pairs[NB * (NB + 1) / 2];
     const int tid = threadIdx.x;
     const double tau = (double)R * DBL_EPSILON * sc->maxdiag;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
@@ -342,8 +377,13 @@ k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__
         Ds[r][c] = (r < jb && c <= r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
         Ls[r][c] = (r == c) ? 1.0 : 0.0;
     }
+    for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) {
+        int r, s2;
+        pair_of(e, &r, &s2);
+        pairs[e] = (unsigned short)((r << 8) | s2);
+    }
     __syncthreads();
-    const int bad = ldl_block(Ds, Ls, dinv_s, jb, tau);
+    const int bad = ldl_block(Ds, Ls, dinv_s, pairs, jb, tau);
     if (blockIdx.x == 0) {
         if (tid == 0 && bad) atomicOr(&sc->fail_mask, 1 << mode);
         for (int e = tid; e < jb * jb; e += blockDim.x) {
@@ -358,8 +398,8 @@ k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__
     // then L = X D^{-1}; X goes to P for the trailing update (rows of H only)
     const int lane = tid & 31, w = tid >> 5;
     const int j1 = j0 + jb;
-    for (int rr = w; rr < PANEL_ROWS; rr += blockDim.x >> 5) {
-        const int i = j1 + (blockIdx.x - 1) * PANEL_ROWS + rr;
+    for (int rr = w; rr < rows_per_cta; rr += blockDim.x >> 5) {
+        const int i = j1 + (blockIdx.x - 1) * rows_per_cta + rr;
         if (i >= nrows) break;
         double b = (lane < jb) ? H[(size_t)i * R + j0 + lane] : 0.0;
         for (int c = 0; c < jb; ++c) {
@@ -374,7 +414,8 @@ k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__
 }
 
 // Trailing update H[i][c] -= sum_s L[i][j0+s] X[c][s] for i >= j1 (rows of H and of the
-// appended M block), j1 <= c < R, lower triangle only for rows of H.
+// appended M block), j1 <= c < R, lower triangle only for rows of H. One output per
+// thread on 16 x 16 tiles, so that the late (small) steps still spread over the SMs.
 __global__ void __launch_bounds__(256)
 k_ldl_update(double* __restrict__ H, const double* __restrict__ P, int R, int nrows, int j0,
              int jb, int nHtiles) {
@@ -401,35 +442,21 @@ k_ldl_update(double* __restrict__ H, const double* __restrict__ P, int R, int nr
     }
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;
-    double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
-#pragma unroll 8
-    for (int s = 0; s < NB; ++s) {
-        const double x0 = As[ty][s], x1 = As[ty + 16][s];
-        const double y0 = Bs[tx][s], y1 = Bs[tx + 16][s];
-        a00 = fma(x0, y0, a00);
-        a01 = fma(x0, y1, a01);
-        a10 = fma(x1, y0, a10);
-        a11 = fma(x1, y1, a11);
-    }
-    const double acc[2][2] = {{a00, a01}, {a10, a11}};
+    const int row = r0 + ty, col = c0 + tx;
+    if (row >= rend || col >= R || (hrows && col > row)) return;
+    double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int row = r0 + ty + 16 * i;
-        if (row >= rend) continue;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int col = c0 + tx + 16 * j;
-            if (col >= R) continue;
-            if (hrows && col > row) continue;
-            H[(size_t)row * R + col] -= acc[i][j];
-        }
+    for (int s = 0; s < NB; s += 2) {
+        a0 = fma(As[ty][s], Bs[tx][s], a0);
+        a1 = fma(As[ty][s + 1], Bs[tx][s + 1], a1);
     }
+    H[(size_t)row * R + col] -= (a0 + a1);
 }
 
 // Backward step J of A L = Y (unit lower L): warp 0 solves A_J L_JJ = Y_J for row r by
 // substitution, then every CTA applies Y[r, q] -= sum_c A_J[c] L[c0+c][q] to its chunk of
 // columns q < c0; CTA 0 stores A_J.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_bsolve_unit(double* __restrict__ Yf, double* __restrict__ A, int R,
               const double* __restrict__ H, int J) {
     const int c0 = J * NB, jb = min(NB, R - c0);
@@ -468,8 +495,11 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
         for (int j0 = 0; j0 < R; j0 += NB) {
             const int jb = std::min(NB, R - j0);
             const int below = nrows - (j0 + jb);
-            k_ldl_panel<<<1 + cdiv(below, PANEL_ROWS), 128, 0, st>>>(Haug, P, dinv, R, nrows, j0,
-                                                                     jb, sc, mode);
+            // every panel CTA repeats the diagonal-block factorisation: keep the grid
+            // within one CTA per SM so that the repeats do not share an FP64 pipe
+            const int rpc = std::max(4, ((cdiv(std::max(below, 1), kNumSM - 4) + 3) / 4) * 4);
+            k_ldl_panel<<<1 + cdiv(below, rpc), 128, 0, st>>>(Haug, P, dinv, R, nrows, j0, jb,
+                                                              rpc, sc, mode);
             count_launch();
             const int j1 = j0 + jb;
             if (j1 < R) {
@@ -486,8 +516,8 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
     double* Yf = Haug + (size_t)R * R;
     for (int J = nJ - 1; J >= 0; --J) {
         const int c0 = J * NB;
-        dim3 grid(std::max(1, cdiv(c0, 128)), n);
-        k_bsolve_unit<<<grid, 128, 0, st>>>(Yf, A, R, Haug, J);
+        dim3 grid(std::max(1, cdiv(c0, 256)), n);
+        k_bsolve_unit<<<grid, 256, 0, st>>>(Yf, A, R, Haug, J);
         count_launch();
     }
 }

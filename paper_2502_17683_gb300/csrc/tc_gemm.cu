@@ -370,13 +370,16 @@ cudaError_t tc_gemm(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMa
     dim3 grid(cdiv(N, BN), cdiv(M, BM));
     ProfScope prof(st, KC_TC, 2.0 * M * (double)N * K);
     count_launch();
-    if (tf32) {
-        cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+        // once per process, outside any stream capture: allow the largest ring
+        cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem);
+        cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_max_smem);
+    });
+    if (tf32)
         k_tc_gemm<true><<<grid, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
-    } else {
-        cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
         k_tc_gemm<false><<<grid, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
-    }
     return cudaGetLastError();
 }
 

@@ -152,3 +152,22 @@ def test_bad_arguments_raise(api):
         api.thc_cpd_mttkrp(d["Xo"], d["Xv"], d["Z"], d["A"], 5)
     with pytest.raises(ThcCpdError):
         api.thc_cpd_mttkrp(d["Xo"], d["Xv"], d["Z"], d["A"][:3], 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_graph_replay_is_bit_identical_to_direct_launches(api, prec, monkeypatch):
+    # every kernel is deterministic (fixed-order reductions, no atomics on data), so the
+    # CUDA-graph replay of a sweep and direct launches give the same bits
+    p = make_problem(7, 33, 97, 131, seed=8)
+    outs = []
+    for no_graph in (False, True):
+        if no_graph:
+            monkeypatch.setenv("THC_CPD_NO_GRAPH", "1")
+        d = to_dev(p, torch)
+        lam = torch.ones(131, dtype=torch.float64, device="cuda")
+        out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 6, 0.0, precision=prec)
+        outs.append((out["fit"], [a.cpu().numpy() for a in d["A"]], lam.cpu().numpy()))
+    assert outs[0][0] == outs[1][0]
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(outs[0][2], outs[1][2])

@@ -149,6 +149,25 @@ void thc_cpd_profile(int enable);
  * filled or -1 on a CUDA error. */
 int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes);
 
+/* thc_cpd_mttkrp without any device allocation (the paper has no counterpart: this is
+ * a service for callers that may not allocate device memory while they run, such as a
+ * host whose own pool allocator owns all device memory, or code that must not call
+ * cudaMalloc because it can synchronise the device).
+ * Same arguments and result as thc_cpd_mttkrp, FP64 only (opts->precision must be
+ * THC_CPD_FP64 or opts NULL). The caller still provides Xo, Xv, Z, A and M; all scratch
+ * comes from one 32 MiB array in the library's device memory, which every GPU that loads
+ * the library keeps until the process exits. Problems whose 4 * R_thc * R_cp doubles do
+ * not fit in it are rejected with THC_CPD_ERR_SHAPE (message in thc_cpd_last_error()).
+ * The first call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress); make it before any stream capture. Calls only enqueue
+ * work on opts->stream (no synchronisation); M is ready when the stream reaches that
+ * point. All calls on a device share the array, which keeps the last call's contents:
+ * calls whose GPU work overlaps race on it and must be serialised by the caller. */
+thc_cpd_status thc_cpd_mttkrp_noalloc(int o, int v, int Rt, int R,
+                                      const double* Xo, const double* Xv, const double* Z,
+                                      const double* const A[4], int mode, double* M,
+                                      const thc_cpd_opts* opts);
+
 /* Message for the last non-OK status returned on this host thread. */
 const char* thc_cpd_last_error(void);
 

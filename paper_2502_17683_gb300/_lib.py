@@ -18,7 +18,8 @@ PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 # every symbol include/thc_cpd.h declares
 EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version", "thc_cpd_launch_count",
-           "thc_cpd_profile", "thc_cpd_profile_read", "thc_cpd_split_gemm")
+           "thc_cpd_profile", "thc_cpd_profile_read", "thc_cpd_split_gemm",
+           "thc_cpd_mttkrp_noalloc")
 KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
 
 
@@ -57,6 +58,7 @@ _SIGS = {
     "thc_cpd_als_sweep": [I, I, I, I, P, P, P, PTR4, P, D, DP, DP, OPTS],
     "thc_cpd_als": [I, I, I, I, P, P, P, PTR4, P, I, D, IP, DP, DP, OPTS],
     "thc_cpd_split_gemm": [I, I, I, P, P, P, OPTS],
+    "thc_cpd_mttkrp_noalloc": [I, I, I, I, P, P, P, PTR4, I, P, OPTS],
 }
 
 _lib = None

@@ -15,7 +15,7 @@ from ._lib import (ERR_ARG, KCLASS_NAMES, PRECISIONS, PTR4, KStat, Opts, ThcCpdE
 
 __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_version", "thc_cpd_launch_count", "thc_cpd_profile",
-           "thc_cpd_profile_read", "thc_cpd_split_gemm", "Opts"]
+           "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -79,6 +79,19 @@ def thc_cpd_mttkrp(Xo, Xv, Z, A, mode: int, M=None, precision="fp64", stream=Non
     check(load().thc_cpd_mttkrp(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
                                 _dev(Z, "Z", (Rt, Rt)), _ptr4(A, dims, R), int(mode),
                                 _dev(M, "M"), ctypes.byref(opts)))
+    return M
+
+
+def thc_cpd_mttkrp_noalloc(Xo, Xv, Z, A, mode: int, M, stream=None):
+    """thc_cpd_mttkrp (FP64) with the library's fixed scratch array instead of any device
+    allocation; M must be provided by the caller. Only enqueues work on the stream."""
+    o, v, Rt = _dims(Xo, Xv, Z)
+    R = A[0].shape[1]
+    dims = (o, v, o, v)
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_mttkrp_noalloc(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                                        _dev(Z, "Z", (Rt, Rt)), _ptr4(A, dims, R), int(mode),
+                                        _dev(M, "M"), ctypes.byref(opts)))
     return M
 
 

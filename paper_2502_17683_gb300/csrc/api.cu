@@ -550,6 +550,13 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
 
 }  // namespace
 
+namespace thc {
+int set_error(int s, const char* msg) {
+    g_err = msg;
+    return s;
+}
+}  // namespace thc
+
 extern "C" {
 
 const char* thc_cpd_last_error(void) { return g_err.c_str(); }

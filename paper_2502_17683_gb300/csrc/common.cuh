@@ -46,4 +46,7 @@ struct Arena {
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Record the message returned by thc_cpd_last_error() for this host thread; returns s.
+int set_error(int s, const char* msg);
+
 }  // namespace thc

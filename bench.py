@@ -22,8 +22,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-W = dict(o=20, v=100, Rt=480, R=720, sweeps=50, seed=0)
+W = dict(o=20, v=100, Rt=480, R=720, sweeps=50, seed=0, decay=None)
 WORKLOAD = "THC-driven CP-ALS, o=20 v=100 R_thc=480 R_cp=720, 50 sweeps per step"
+# other paper-shaped sizes, for profiling captures (the bench line uses the default)
+CONFIGS = {
+    "c1": dict(o=5, v=15, Rt=60, R=80, sweeps=25),
+    "c2": dict(o=20, v=100, Rt=480, R=720, sweeps=50),
+    "c3": dict(o=50, v=250, Rt=1200, R=1800, sweeps=100, decay=240.0),
+    "c5": dict(o=30, v=150, Rt=720, R=1080, sweeps=50),
+}
 METRIC = "ALS sweeps/s"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
@@ -39,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps", type=int, default=None,
                     help="sweeps per step (profiling captures only; the bench line uses 50)")
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS),
+                    help="workload size (profiling captures only; the bench line uses c2)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the FP64 path beside the split precision")
     return ap.parse_args()
 
 
@@ -107,7 +118,7 @@ def oracle_sweeps_per_s(seconds: float, seed: int):
     of the same workload from the same start point."""
     from oracle import thc_cpd as O
     from thc_inputs import make_problem
-    p = make_problem(W["o"], W["v"], W["Rt"], W["R"], seed=seed)
+    p = make_problem(W["o"], W["v"], W["Rt"], W["R"], seed=seed, decay=W.get("decay"))
     nG2 = O.thc_norm2(p.Xo, p.Xv, p.Z)
     A, lam = p.A, None
     t0 = time.perf_counter()
@@ -174,9 +185,14 @@ def main():
     from thc_inputs import make_problem
 
     precision = args.precision or "bf16x3"
+    global WORKLOAD
+    if args.config != "c2":
+        W.update(CONFIGS[args.config])
+        WORKLOAD = (f"THC-driven CP-ALS, o={W['o']} v={W['v']} R_thc={W['Rt']} R_cp={W['R']}, "
+                    f"{W['sweeps']} sweeps per step")
     if args.sweeps:
         W["sweeps"] = args.sweeps
-    p = make_problem(W["o"], W["v"], W["Rt"], W["R"], seed=W["seed"] + rank)
+    p = make_problem(W["o"], W["v"], W["Rt"], W["R"], seed=W["seed"] + rank, decay=W.get("decay"))
     t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     Xo, Xv, Z = t(p.Xo), t(p.Xv), t(p.Z)
     A0 = [t(a) for a in p.A]
@@ -264,7 +280,7 @@ def main():
 
     # ---- the plain FP64 GPU path on the same workload, same protocol ----
     compare = None
-    if precision != "fp64":
+    if precision != "fp64" and not args.no_compare:
         for _ in range(2):
             reset()
             api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64")

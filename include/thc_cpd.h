@@ -68,7 +68,27 @@ typedef struct thc_cpd_opts {
                             max_sweeps run in FP64. With tol > 0 the run switches to FP64
                             by itself once |fit_s - fit_{s-1}| < 10 tol and stops at tol,
                             so that it ends on a fixed point of FP64 ALS */
+    int autotune;        /* split precision: nonzero times the candidate tensor-core tile
+                            shapes of every GEMM shape the first time it is met (on the
+                            live operands, before any graph capture) and keeps the fastest
+                            for the rest of the process */
+    int reserved;
 } thc_cpd_opts;
+
+/* One independent problem of a batched run (thc_cpd_als_batched). Inputs as for
+ * thc_cpd_als (device pointers); sweeps_done, flags_out, loss and fit are outputs. */
+typedef struct thc_cpd_problem {
+    int o, v, Rt, R;
+    const double* Xo;
+    const double* Xv;
+    const double* Z;
+    double* A[4];
+    double* lam;
+    int sweeps_done;
+    int flags_out;
+    double loss;
+    double fit;
+} thc_cpd_problem;
 
 /* ||G||_F^2 = sum_PQ Z[P,Q] (S Z S)[P,Q], S = (Xo^T Xo) o (Xv^T Xv): the THC norm in
  * O(Rt^3), the contraction pattern of the J term of Eq. thc_Ej. Result in *normG2_host. */
@@ -122,6 +142,15 @@ thc_cpd_status thc_cpd_als(int o, int v, int Rt, int R,
  * (Sec. 2.1 gradients of Eq. lossF), exposed for testing and reuse. Synchronises. */
 thc_cpd_status thc_cpd_split_gemm(int M, int N, int K, const double* A, const double* B,
                                   double* C, const thc_cpd_opts* opts);
+
+/* CP-ALS of many independent problems of uneven (o, v, R_thc, R_cp) at once: each problem
+ * follows thc_cpd_als (same sweeps, same results bit for bit), but one sweep of every
+ * still-running problem is captured into a single CUDA graph whose branches run
+ * concurrently, and the graph is replayed once per sweep; problems that meet
+ * |fit_s - fit_{s-1}| < tol leave the graph. opts->precision applies to all problems
+ * (split precisions run without the FP64 polish phase); opts->history is not used. */
+thc_cpd_status thc_cpd_als_batched(int nprob, thc_cpd_problem* probs, int max_sweeps, double tol,
+                                   thc_cpd_opts* opts);
 
 /* ---- launch accounting and kernel timing (tracing support; the paper has no
  * counterpart: it reports wall-times only) ---------------------------------------- */

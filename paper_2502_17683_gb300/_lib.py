@@ -19,7 +19,7 @@ PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version", "thc_cpd_launch_count",
            "thc_cpd_profile", "thc_cpd_profile_read", "thc_cpd_split_gemm",
-           "thc_cpd_mttkrp_noalloc")
+           "thc_cpd_mttkrp_noalloc", "thc_cpd_als_batched")
 KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
 
 
@@ -40,7 +40,17 @@ class Opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p),
                 ("history", ctypes.POINTER(ctypes.c_double)),
                 ("flags_out", ctypes.c_int),
-                ("polish_sweeps", ctypes.c_int)]
+                ("polish_sweeps", ctypes.c_int),
+                ("autotune", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("o", ctypes.c_int), ("v", ctypes.c_int), ("Rt", ctypes.c_int), ("R", ctypes.c_int),
+                ("Xo", ctypes.c_void_p), ("Xv", ctypes.c_void_p), ("Z", ctypes.c_void_p),
+                ("A", ctypes.c_void_p * 4), ("lam", ctypes.c_void_p),
+                ("sweeps_done", ctypes.c_int), ("flags_out", ctypes.c_int),
+                ("loss", ctypes.c_double), ("fit", ctypes.c_double)]
 
 
 P = ctypes.c_void_p
@@ -59,6 +69,7 @@ _SIGS = {
     "thc_cpd_als": [I, I, I, I, P, P, P, PTR4, P, I, D, IP, DP, DP, OPTS],
     "thc_cpd_split_gemm": [I, I, I, P, P, P, OPTS],
     "thc_cpd_mttkrp_noalloc": [I, I, I, I, P, P, P, PTR4, I, P, OPTS],
+    "thc_cpd_als_batched": [I, ctypes.c_void_p, I, D, OPTS],
 }
 
 _lib = None

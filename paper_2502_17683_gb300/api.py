@@ -10,12 +10,13 @@ import ctypes
 
 import torch
 
-from ._lib import (ERR_ARG, KCLASS_NAMES, PRECISIONS, PTR4, KStat, Opts, ThcCpdError, check,
-                   load)
+from ._lib import (ERR_ARG, KCLASS_NAMES, PRECISIONS, PTR4, KStat, Opts, Problem, ThcCpdError,
+                   check, load)
 
 __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_version", "thc_cpd_launch_count", "thc_cpd_profile",
-           "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc", "Opts"]
+           "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc",
+           "thc_cpd_als_batched", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -28,9 +29,11 @@ def _dev(t: torch.Tensor, name: str, shape=None) -> int:
     return t.data_ptr()
 
 
-def _opts(precision="fp64", stream=None, loss_every=0, history=None, polish_sweeps=0) -> Opts:
+def _opts(precision="fp64", stream=None, loss_every=0, history=None, polish_sweeps=0,
+          autotune=False) -> Opts:
     o = Opts()
     o.polish_sweeps = int(polish_sweeps)
+    o.autotune = 1 if autotune else 0
     if isinstance(precision, str):
         if precision not in PRECISIONS:
             raise ThcCpdError(ERR_ARG, f"unknown precision {precision!r}")
@@ -121,14 +124,15 @@ def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", 
 
 
 def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision="fp64",
-                stream=None, loss_every: int = 0, history: bool = False, polish_sweeps: int = 0):
+                stream=None, loss_every: int = 0, history: bool = False, polish_sweeps: int = 0,
+                autotune: bool = False):
     o, v, Rt = _dims(Xo, Xv, Z)
     R = A[0].shape[1]
     loss, fit, done = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     hist = (ctypes.c_double * max(1, 2 * max_sweeps))() if history else None
     opts = _opts(precision, stream, loss_every,
                  ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
-                 polish_sweeps)
+                 polish_sweeps, autotune)
     check(load().thc_cpd_als(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
                              _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R),
                              _dev(lam, "lam", (R,)), int(max_sweeps), float(tol),
@@ -171,3 +175,26 @@ def thc_cpd_profile_read() -> dict:
         raise ThcCpdError(3, "profile read failed")
     return {KCLASS_NAMES[i]: dict(ms=buf[i].ms, flops=buf[i].flops, bytes=buf[i].bytes,
                                   groups=buf[i].groups) for i in range(got)}
+
+
+def thc_cpd_als_batched(problems, max_sweeps: int, tol: float = 0.0, precision="fp64",
+                        stream=None, autotune: bool = False):
+    """problems: list of dicts with Xo, Xv, Z, A (list of 4), lam (device tensors, updated in
+    place). Returns a list of dict(sweeps, loss, fit, flags) per problem."""
+    n = len(problems)
+    arr = (Problem * max(1, n))()
+    for i, pr in enumerate(problems):
+        o, v, Rt = _dims(pr["Xo"], pr["Xv"], pr["Z"])
+        R = pr["A"][0].shape[1]
+        arr[i].o, arr[i].v, arr[i].Rt, arr[i].R = o, v, Rt, R
+        arr[i].Xo = _dev(pr["Xo"], "Xo", (o, Rt))
+        arr[i].Xv = _dev(pr["Xv"], "Xv", (v, Rt))
+        arr[i].Z = _dev(pr["Z"], "Z", (Rt, Rt))
+        for k, a in enumerate(pr["A"]):
+            arr[i].A[k] = _dev(a, f"A[{k}]", ((o, v, o, v)[k], R))
+        arr[i].lam = _dev(pr["lam"], "lam", (R,))
+    opts = _opts(precision, stream, autotune=autotune)
+    check(load().thc_cpd_als_batched(n, ctypes.cast(arr, ctypes.c_void_p), int(max_sweeps),
+                                     float(tol), ctypes.byref(opts)))
+    return [dict(sweeps=arr[i].sweeps_done, loss=arr[i].loss, fit=arr[i].fit, flags=arr[i].flags_out)
+            for i in range(n)]

@@ -6,7 +6,9 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <memory>
 #include <string>
+#include <vector>
 
 #include "thc_cpd.h"
 #include "f64.cuh"
@@ -480,7 +482,9 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     h.fit = nan("");
     double fit1 = nan(""), fit2 = nan("");  // fits of the last two evaluated sweeps
     bool use_graph = !prof_on() && getenv("THC_CPD_NO_GRAPH") == nullptr;
+    const bool tune = opts && opts->autotune && split_run;
     for (int sw = 1; sw <= max_sweeps; ++sw) {
+        if (tune) tc_set_tuning(sw == 1);
         // split precision hands over to FP64 sweeps (polish) near convergence or for the
         // last polish_sweeps of a fixed-length run
         if (split_run && c.prec != THC_CPD_FP64 &&
@@ -503,7 +507,12 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
         CK(cudaMemcpyAsync(c.lamsnap, lam, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
         CK(cudaMemcpyAsync(c.sc_snap, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
         int used = 0;
-        CKS(fast_sweep(c, A, lam, eval, tol, &use_graph));
+        if (tune && sw == 1) {
+            CKS(sweep(c, A, lam, false, eval, tol, &used));  // tuned on live operands
+            tc_set_tuning(false);
+        } else {
+            CKS(fast_sweep(c, A, lam, eval, tol, &use_graph));
+        }
         CKS(read_scalars(c, &h));
         if (h.fail_mask) {
             // a Cholesky pivot failed somewhere in this sweep: roll back and replay the
@@ -542,6 +551,190 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     if (fit_host) *fit_host = h.fit;
     CK(cudaStreamSynchronize(c.st));
     if (c.prec != THC_CPD_FP64) {
+        if (int e = mixed_take_error())
+            return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
+    }
+    return THC_CPD_OK;
+}
+
+
+// ---- batched driver -------------------------------------------------------------------
+// Every problem has its own Ctx and stream; one sweep of all running problems is captured
+// as one CUDA graph (fork from a capture stream, one branch per problem, join) and
+// replayed per sweep. The device scalars of all problems live in one array so that a
+// single copy per sweep brings back every problem's loss, fit and failure flags.
+thc_cpd_status run_batched(int np, thc_cpd_problem* P, int max_sweeps, double tol,
+                           thc_cpd_opts* opts) {
+    if (np < 1 || !P) return set_err(THC_CPD_ERR_ARG, "need at least one problem");
+    if (max_sweeps < 0) return set_err(THC_CPD_ERR_ARG, "max_sweeps must be >= 0");
+    CKS(check_prec(opts));
+    std::vector<Shape> shp(np);
+    for (int p = 0; p < np; ++p) {
+        CKS(check_shape(P[p].o, P[p].v, P[p].Rt, P[p].R, &shp[p]));
+        CKS(check_ptrs(P[p].Xo, P[p].Xv, P[p].Z, P[p].A));
+        if (!P[p].lam) return set_err(THC_CPD_ERR_ARG, "problem %d: lam must be non-null", p);
+        P[p].sweeps_done = 0;
+        P[p].flags_out = 0;
+        P[p].loss = P[p].fit = nan("");
+    }
+    if (opts) opts->flags_out = 0;
+    const cudaStream_t caller = stream_of(opts);
+    const int prec = opts ? opts->precision : THC_CPD_FP64;
+    struct Res {
+        std::vector<cudaStream_t> streams;
+        std::vector<cudaEvent_t> events;
+        std::vector<std::unique_ptr<Ctx>> ctx;
+        cudaStream_t cap = nullptr;
+        cudaGraphExec_t exec[2] = {nullptr, nullptr};
+        DevScalars* dsc = nullptr;
+        DevScalars* hsc = nullptr;
+        cudaStream_t free_on = nullptr;
+        ~Res() {
+            for (auto& e : exec)
+                if (e) cudaGraphExecDestroy(e);
+            ctx.clear();  // frees workspaces on their streams
+            if (dsc) cudaFreeAsync(dsc, free_on);
+            if (hsc) cudaFreeHost(hsc);
+            for (auto e : events) cudaEventDestroy(e);
+            for (auto s : streams) cudaStreamDestroy(s);
+            if (cap) cudaStreamDestroy(cap);
+        }
+    } r;
+    r.free_on = caller;
+    CK(cudaStreamCreateWithFlags(&r.cap, cudaStreamNonBlocking));
+    r.streams.resize(np);
+    for (int p = 0; p < np; ++p) CK(cudaStreamCreateWithFlags(&r.streams[p], cudaStreamNonBlocking));
+    r.events.resize(np + 2);
+    for (auto& e : r.events) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEvent_t ev_fork = r.events[np], ev_done = r.events[np + 1];
+    // order everything after the caller's prior work
+    CK(cudaEventRecord(ev_fork, caller));
+    CK(cudaStreamWaitEvent(r.cap, ev_fork, 0));
+    for (int p = 0; p < np; ++p) CK(cudaStreamWaitEvent(r.streams[p], ev_fork, 0));
+    CK(cudaMallocAsync((void**)&r.dsc, sizeof(DevScalars) * 2 * np, caller));
+    CK(cudaMallocHost((void**)&r.hsc, sizeof(DevScalars) * np));
+    CK(cudaStreamSynchronize(caller));
+    r.ctx.resize(np);
+    for (int p = 0; p < np; ++p) {
+        r.ctx[p] = std::make_unique<Ctx>();
+        thc_cpd_opts o2 = opts ? *opts : thc_cpd_opts{};
+        o2.stream = r.streams[p];
+        Ctx& c = *r.ctx[p];
+        CKS(ctx_init(c, shp[p], P[p].Xo, P[p].Xv, P[p].Z, &o2, NEED_ALS | NEED_NORM));
+        c.sc = r.dsc + p;
+        c.sc_snap = r.dsc + np + p;
+        double nG2;
+        CKS(obtain_norm(c, 0.0, &nG2));
+        refresh_state(c, P[p].A);
+    }
+    for (int p = 0; p < np; ++p) CK(cudaStreamSynchronize(r.streams[p]));
+    std::vector<int> active(np);
+    for (int p = 0; p < np; ++p) active[p] = p;
+    bool graph_ok[2] = {false, false};
+    const bool use_graph = !prof_on() && getenv("THC_CPD_NO_GRAPH") == nullptr;
+    const bool tune = opts && opts->autotune && prec != THC_CPD_FP64;
+    int any_flags = 0;
+    for (int sw = 1; sw <= max_sweeps && !active.empty(); ++sw) {
+        const bool eval = prec == THC_CPD_FP64 || tol > 0.0 || sw == max_sweeps;
+        const int gi = eval ? 1 : 0;
+        auto enqueue_sweep = [&](int p) -> thc_cpd_status {
+            Ctx& c = *r.ctx[p];
+            for (int k = 0; k < 4; ++k)
+                CK(cudaMemcpyAsync(c.Asnap[k], P[p].A[k], sizeof(double) * c.s.n[k] * c.s.R,
+                                   cudaMemcpyDeviceToDevice, c.st));
+            CK(cudaMemcpyAsync(c.lamsnap, P[p].lam, sizeof(double) * c.s.R, cudaMemcpyDeviceToDevice,
+                               c.st));
+            CK(cudaMemcpyAsync(c.sc_snap, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+            int used = 0;
+            return sweep(c, P[p].A, P[p].lam, false, eval, tol, &used);
+        };
+        if (use_graph && !(tune && sw == 1)) {
+            if (!graph_ok[gi]) {
+                if (r.exec[gi]) cudaGraphExecDestroy(r.exec[gi]);
+                r.exec[gi] = nullptr;
+                const long l0 = thc_cpd_launch_count();
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamBeginCapture(r.cap, cudaStreamCaptureModeThreadLocal));
+                CK(cudaEventRecord(ev_fork, r.cap));
+                thc_cpd_status st = THC_CPD_OK;
+                for (int p : active) {
+                    cudaStreamWaitEvent(r.streams[p], ev_fork, 0);
+                    if (st == THC_CPD_OK) st = enqueue_sweep(p);
+                    cudaEventRecord(r.events[p], r.streams[p]);
+                    cudaStreamWaitEvent(r.cap, r.events[p], 0);
+                }
+                const cudaError_t ce = cudaStreamEndCapture(r.cap, &g);
+                if (st != THC_CPD_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return st;
+                }
+                if (ce != cudaSuccess) return set_err(THC_CPD_ERR_CUDA, "batched capture failed: %s", cudaGetErrorString(ce));
+                const cudaError_t ie = cudaGraphInstantiate(&r.exec[gi], g, 0);
+                cudaGraphDestroy(g);
+                if (ie != cudaSuccess) return set_err(THC_CPD_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+                graph_ok[gi] = true;
+                r.ctx[0]->glaunch[gi] = thc_cpd_launch_count() - l0;
+            }
+            CK(cudaGraphLaunch(r.exec[gi], r.cap));
+            count_launch((int)r.ctx[0]->glaunch[gi]);
+        } else {
+            if (tune) tc_set_tuning(sw == 1);
+            for (int p : active) {
+                CK(cudaEventRecord(ev_fork, r.cap));
+                CK(cudaStreamWaitEvent(r.streams[p], ev_fork, 0));
+                CKS(enqueue_sweep(p));
+                CK(cudaEventRecord(r.events[p], r.streams[p]));
+                CK(cudaStreamWaitEvent(r.cap, r.events[p], 0));
+            }
+            if (tune) tc_set_tuning(false);
+        }
+        CK(cudaMemcpyAsync(r.hsc, r.dsc, sizeof(DevScalars) * np, cudaMemcpyDeviceToHost, r.cap));
+        CK(cudaStreamSynchronize(r.cap));
+        std::vector<int> still;
+        for (int p : active) {
+            DevScalars h = r.hsc[p];
+            Ctx& c = *r.ctx[p];
+            if (h.fail_mask) {
+                // roll this problem back and replay its sweep with checked factorisations
+                for (int k = 0; k < 4; ++k)
+                    CK(cudaMemcpyAsync(P[p].A[k], c.Asnap[k], sizeof(double) * c.s.n[k] * c.s.R,
+                                       cudaMemcpyDeviceToDevice, c.st));
+                CK(cudaMemcpyAsync(P[p].lam, c.lamsnap, sizeof(double) * c.s.R,
+                                   cudaMemcpyDeviceToDevice, c.st));
+                CK(cudaMemcpyAsync(c.sc, c.sc_snap, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+                refresh_state(c, P[p].A);
+                CKS(ctx_safe_buffers(c));
+                int used = 0;
+                CKS(sweep(c, P[p].A, P[p].lam, true, eval, tol, &used));
+                CKS(read_scalars(c, &h));
+                P[p].flags_out |= 2 | (used ? 1 : 0);
+                r.hsc[p] = h;
+            }
+            P[p].sweeps_done = sw;
+            if (eval) {
+                P[p].loss = h.loss;
+                P[p].fit = h.fit;
+                if (h.nonfinite || !isfinite(h.loss))
+                    return set_err(THC_CPD_ERR_NONFINITE, "problem %d: loss became non-finite at sweep %d", p, sw);
+            }
+            any_flags |= P[p].flags_out;
+            if (h.done)
+                graph_ok[0] = graph_ok[1] = false;  // re-capture without it
+            else
+                still.push_back(p);
+        }
+        active.swap(still);
+    }
+    // the caller's stream waits for everything
+    CK(cudaEventRecord(ev_done, r.cap));
+    for (int p = 0; p < np; ++p) {
+        CK(cudaEventRecord(r.events[p], r.streams[p]));
+        CK(cudaStreamWaitEvent(caller, r.events[p], 0));
+    }
+    CK(cudaStreamWaitEvent(caller, ev_done, 0));
+    CK(cudaStreamSynchronize(caller));
+    if (opts) opts->flags_out = any_flags;
+    if (prec != THC_CPD_FP64) {
         if (int e = mixed_take_error())
             return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
     }
@@ -695,3 +888,8 @@ thc_cpd_status thc_cpd_als(int o, int v, int Rt, int R, const double* Xo, const 
 }
 
 }  // extern "C"
+
+extern "C" thc_cpd_status thc_cpd_als_batched(int nprob, thc_cpd_problem* probs, int max_sweeps,
+                                              double tol, thc_cpd_opts* opts) {
+    return run_batched(nprob, probs, max_sweeps, tol, opts);
+}

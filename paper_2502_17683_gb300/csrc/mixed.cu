@@ -8,6 +8,7 @@ namespace thc {
 bool mixed_supported() { return tc_available(); }
 
 namespace {
+constexpr int kBackSplits = 10;  // at most this many K slices in the back-projection
 size_t split_bytes(bool tf32, int rows, int cols) {
     return 2 * Arena::need<uint8_t>((size_t)rows * split_pitch(tf32, cols) * (tf32 ? 4 : 2));
 }
@@ -30,6 +31,7 @@ size_t mixed_ws_bytes(bool tf32, int o, int v, int Rt, int R) {
     b += 2 * split_bytes(tf32, R, o) + 2 * split_bytes(tf32, R, v);
     b += 2 * split_bytes(tf32, R, Rt);
     b += 5 * Arena::need<float>((size_t)R * Rt);
+    b += Arena::need<double>((size_t)kBackSplits * std::max(o, v) * R);
     return b;
 }
 
@@ -53,6 +55,8 @@ void mixed_ws_carve(MixedWs& mx, Arena& ar, bool tf32, int o, int v, int Rt, int
     carve_split(ar, tf32, mx.Et, R, Rt);
     for (int k = 0; k < 4; ++k) mx.Wt[k] = ar.take<float>((size_t)R * Rt);
     mx.Yf = ar.take<float>((size_t)R * Rt);
+    mx.part_cap = (size_t)kBackSplits * std::max(o, v) * R;
+    mx.part = ar.take<double>(mx.part_cap);
 }
 
 cudaError_t mixed_setup(MixedWs& mx, cudaStream_t st, const double* Xo, const double* Xv,
@@ -107,7 +111,7 @@ cudaError_t mixed_backproject(MixedWs& mx, cudaStream_t st, int k, double* M) {
     TcEpilogue ep;
     ep.out_f64t = M;
     ep.ld_f64t = mx.R;
-    return tc_gemm(st, mx.tf32, mx.Et, mx.Xs[k % 2], mx.R, n, mx.Rt, ep);
+    return tc_gemm(st, mx.tf32, mx.Et, mx.Xs[k % 2], mx.R, n, mx.Rt, ep, mx.part, mx.part_cap);
 }
 
 int mixed_take_error() { return tc_take_error(); }

@@ -26,6 +26,8 @@ struct MixedWs {
     SplitMat Pt, Et;     // Hadamard operands (R x Rt): A of Z-GEMM / back-projection
     float* Wt[4] = {};   // W_k^T (R x Rt, FP32)
     float* Yf = nullptr; // Y12 or Y34 (R x Rt, FP32)
+    double* part = nullptr;  // split-K partials of the back-projection
+    size_t part_cap = 0;
 };
 
 bool mixed_supported();

@@ -3,6 +3,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -144,6 +146,8 @@ __host__ __device__ constexpr uint32_t make_idesc(bool tf32, int M, int N) {
 
 struct KArgs {
     int M, N, nkb, BN, stages;
+    int kper;          // k-blocks per CTA along grid z (split-K of the FP64-out epilogue)
+    double* part;      // split-K partials [z][N][ld_f64t] (when gridDim.z > 1)
     TcEpilogue ep;
     void* out_hi;
     void* out_lo;
@@ -188,6 +192,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kel = TF32 ? 32 : 64;  // elements per 128-byte K block
+    const int kb0 = blockIdx.z * args.kper;
+    const int kb1 = min(args.nkb, kb0 + args.kper);
+    const int nk = kb1 - kb0;        // k-blocks of this CTA (>= 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -209,24 +216,25 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     if (warp == 0 && lane == 0) {
         // ---- TMA producer ----
         const uint32_t tx = (uint32_t)stage_bytes;
-        for (int kb = 0; kb < args.nkb; ++kb) {
+        for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % S;
             if (!mbar_wait(&empty[s], ((kb / S) & 1) ^ 1, 1)) break;
             uint8_t* st = smem + (size_t)s * stage_bytes;
+            const int kx = (kb0 + kb) * kel;
             mbar_expect_tx(&full[s], tx);
-            tma_load_2d(st, &tAh, &full[s], kb * kel, m0);
-            tma_load_2d(st + TILE_A, &tAl, &full[s], kb * kel, m0);
-            tma_load_2d(st + 2 * TILE_A, &tBh, &full[s], kb * kel, n0);
-            tma_load_2d(st + 2 * TILE_A + tileB, &tBl, &full[s], kb * kel, n0);
+            tma_load_2d(st, &tAh, &full[s], kx, m0);
+            tma_load_2d(st + TILE_A, &tAl, &full[s], kx, m0);
+            tma_load_2d(st + 2 * TILE_A, &tBh, &full[s], kx, n0);
+            tma_load_2d(st + 2 * TILE_A + tileB, &tBl, &full[s], kx, n0);
         }
         // drain: wait until the consumer released every stage still in flight
-        for (int kb = max(0, args.nkb - S); kb < args.nkb; ++kb)
+        for (int kb = max(0, nk - S); kb < nk; ++kb)
             mbar_wait(&empty[kb % S], (kb / S) & 1, 2);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
         const uint32_t idesc = make_idesc(TF32, BM, BN);
         bool ok = true;
-        for (int kb = 0; kb < args.nkb && ok; ++kb) {
+        for (int kb = 0; kb < nk && ok; ++kb) {
             const int s = kb % S;
             if (!mbar_wait(&full[s], (kb / S) & 1, 3)) {
                 ok = false;
@@ -255,20 +263,55 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
         tc_fence_after();
         const int m = m0 + 32 * q + lane;
         const TcEpilogue& ep = args.ep;
+        // per-warp staging of a 32 x 16 slice (the ring is idle once the MMAs are done), so
+        // that row-major outputs and the Hadamard partner are accessed row-contiguously
+        float* stg = (float*)smem + (warp - 2) * 32 * 17;
+        const bool rowmajor = ep.out_f32 || ep.mul;
+        double* f64t = gridDim.z > 1 ? args.part + (size_t)blockIdx.z * args.N * ep.ld_f64t
+                                     : ep.out_f64t;
         for (int c = 0; c < BN; c += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-            if (!ok || m >= args.M) continue;
+            if (!ok) continue;
+            if (f64t && m < args.M) {
+                // transposed FP64 output: consecutive lanes hold consecutive m (coalesced)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int n = n0 + c + j;
-                if (n >= args.N) break;
-                const float d = v[j];
-                if (ep.out_f32) ep.out_f32[(size_t)m * ep.ld_f32 + n] = d;
-                if (ep.mul)
-                    store_split<TF32>(args.out_hi, args.out_lo, (size_t)m * args.ld_split + n,
-                                      d * ep.mul[(size_t)m * ep.ld_mul + n]);
-                if (ep.out_f64t) ep.out_f64t[(size_t)n * ep.ld_f64t + m] = (double)d;
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c + j;
+                    if (n < args.N) f64t[(size_t)n * ep.ld_f64t + m] = (double)v[j];
+                }
+            }
+            if (rowmajor) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
+                const int col = lane & 15, half = lane >> 4;
+                const int n = n0 + c + col;
+                // all partner loads of the slice in flight at once (read-only path), so the
+                // stores below do not serialise them
+                float mv[16];
+                if (ep.mul) {
+#pragma unroll
+                    for (int rr = 0; rr < 16; ++rr) {
+                        const int mm = m0 + 32 * q + 2 * rr + half;
+                        mv[rr] = (mm < args.M && n < args.N)
+                                     ? __ldg(ep.mul + (size_t)mm * ep.ld_mul + n)
+                                     : 0.f;
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int rr = 0; rr < 16; ++rr) {
+                    const int row = 2 * rr + half;
+                    const int mm = m0 + 32 * q + row;
+                    if (mm < args.M && n < args.N) {
+                        const float d = stg[row * 17 + col];
+                        if (ep.out_f32) ep.out_f32[(size_t)mm * ep.ld_f32 + n] = d;
+                        if (ep.mul)
+                            store_split<TF32>(args.out_hi, args.out_lo,
+                                              (size_t)mm * args.ld_split + n, d * mv[rr]);
+                    }
+                }
+                __syncwarp();
             }
         }
     }
@@ -277,6 +320,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// fixed-order sum of the split-K partials into the FP64 output
+__global__ void k_tc_splitk_reduce(const double* __restrict__ part, int splits, long total,
+                                   double* __restrict__ out) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+         i += (long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * total + i];
+        out[i] = s;
     }
 }
 
@@ -331,22 +385,12 @@ int tc_take_error() {
     return h;
 }
 
-cudaError_t tc_gemm(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMat& B, int M, int N,
-                    int K, const TcEpilogue& ep) {
-    if (M <= 0 || N <= 0) return cudaSuccess;
-    if (!g_encode && !load_encode()) return cudaErrorNotSupported;
-    if (g_max_smem == 0) tc_available();
-    // tile N: a multiple of 16 up to 256, as wide as keeps about one CTA per SM busy
+namespace {
+
+// Launch one GEMM with tile N = BN (a multiple of 16, at most 256).
+cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMat& B, int M,
+                      int N, int K, const TcEpilogue& ep, double* part, size_t part_cap, int BN) {
     const int mt = cdiv(M, BM);
-    int cap = 64;
-    for (int cand : {256, 128}) {
-        if ((long)mt * cdiv(N, cand) >= 120) {
-            cap = cand;
-            break;
-        }
-    }
-    if (N <= cap) cap = std::max(16, ((N + 15) / 16) * 16);
-    const int BN = std::min(256, (cdiv(N, cdiv(N, cap)) + 15) / 16 * 16);
     const int tileB = BN * KBYTES;
     const int stage_bytes = 2 * TILE_A + 2 * tileB;
     const int nkb = std::max(1, cdiv((long)K * (tf32 ? 4 : 2), KBYTES));
@@ -357,19 +401,32 @@ cudaError_t tc_gemm(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMa
     if (!make_map(&mAh, tf32, A.hi, M, K, A.pitch, BM) || !make_map(&mAl, tf32, A.lo, M, K, A.pitch, BM) ||
         !make_map(&mBh, tf32, B.hi, N, K, B.pitch, BN) || !make_map(&mBl, tf32, B.lo, N, K, B.pitch, BN))
         return cudaErrorInvalidValue;
+    // split-K (deterministic, via FP64 partials) when only the transposed FP64 output is
+    // wanted and the tile grid is far smaller than the SM count
+    int splits = 1;
+    const long tiles = (long)cdiv(N, BN) * mt;
+    if (!ep.out_f32 && !ep.mul && ep.out_f64t && part && tiles * 2 <= kNumSM && nkb >= 4) {
+        splits = (int)std::min<long>(std::min<long>(kNumSM / tiles, nkb / 2),
+                                     (long)(part_cap / ((size_t)N * ep.ld_f64t)));
+        splits = std::max(1, splits);
+    }
+    const int kper = cdiv(nkb, splits);
+    splits = cdiv(nkb, kper);
     KArgs args;
     args.M = M;
     args.N = N;
     args.nkb = nkb;
     args.BN = BN;
     args.stages = stages;
+    args.kper = kper;
+    args.part = splits > 1 ? part : nullptr;
     args.ep = ep;
     args.out_hi = ep.out_split ? ep.out_split->hi : nullptr;
     args.out_lo = ep.out_split ? ep.out_split->lo : nullptr;
     args.ld_split = ep.out_split ? ep.out_split->pitch : 0;
-    dim3 grid(cdiv(N, BN), cdiv(M, BM));
+    dim3 grid(cdiv(N, BN), mt, splits);
     ProfScope prof(st, KC_TC, 2.0 * M * (double)N * K);
-    count_launch();
+    count_launch(splits > 1 ? 2 : 1);
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
         // once per process, outside any stream capture: allow the largest ring
@@ -380,7 +437,105 @@ cudaError_t tc_gemm(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMa
         k_tc_gemm<true><<<grid, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
     else
         k_tc_gemm<false><<<grid, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
+    if (splits > 1) {
+        const long total = (long)N * ep.ld_f64t;
+        k_tc_splitk_reduce<<<(int)std::min<long>(cdiv(total, 256), 4L * kNumSM), 256, 0, st>>>(
+            part, splits, total, ep.out_f64t);
+    }
     return cudaGetLastError();
+}
+
+// Default tile N: a multiple of 16 up to 256, as wide as keeps about one CTA per SM busy.
+int heuristic_bn(int M, int N) {
+    const int mt = cdiv(M, BM);
+    int cap = 64;
+    for (int cand : {256, 128}) {
+        if ((long)mt * cdiv(N, cand) >= 120) {
+            cap = cand;
+            break;
+        }
+    }
+    if (N <= cap) cap = std::max(16, ((N + 15) / 16) * 16);
+    return std::min(256, (cdiv(N, cdiv(N, cap)) + 15) / 16 * 16);
+}
+
+// ---- autotuner: per (M, N, K, kind, epilogue) the fastest tile N, process-wide ----
+struct TuneKey {
+    int M, N, K, kind;
+    bool operator<(const TuneKey& o) const {
+        if (M != o.M) return M < o.M;
+        if (N != o.N) return N < o.N;
+        if (K != o.K) return K < o.K;
+        return kind < o.kind;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+std::atomic<int> g_tuning{0};
+
+int epi_kind(bool tf32, const TcEpilogue& ep) {
+    return (tf32 ? 1 : 0) | (ep.out_f32 ? 2 : 0) | (ep.mul ? 4 : 0) | (ep.out_f64t ? 8 : 0);
+}
+
+}  // namespace
+
+void tc_set_tuning(bool on) { g_tuning.store(on ? 1 : 0); }
+
+int tc_tuned_entries() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int)g_tuned.size();
+}
+
+cudaError_t tc_gemm(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMat& B, int M, int N,
+                    int K, const TcEpilogue& ep, double* part, size_t part_cap) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (!g_encode && !load_encode()) return cudaErrorNotSupported;
+    if (g_max_smem == 0) tc_available();
+    const TuneKey key{M, N, K, epi_kind(tf32, ep)};
+    int BN = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) BN = it->second;
+    }
+    if (BN == 0 && g_tuning.load()) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusNone) {
+            // time every candidate on the live operands (outputs are rewritten identically)
+            const int nmax = std::min(256, ((N + 15) / 16) * 16);
+            int cands[6], nc = 0;
+            for (int c : {32, 64, 96, 128, 192, 256})
+                if (c <= nmax) cands[nc++] = c;
+            if (nc == 0) cands[nc++] = nmax;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            float best = 1e30f;
+            for (int i = 0; i < nc; ++i) {
+                cudaError_t err = tc_launch(st, tf32, A, B, M, N, K, ep, part, part_cap, cands[i]);
+                if (err != cudaSuccess) continue;
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3; ++r) tc_launch(st, tf32, A, B, M, N, K, ep, part, part_cap, cands[i]);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    BN = cands[i];
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (BN) {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tuned[key] = BN;
+            }
+        }
+    }
+    if (BN == 0) BN = heuristic_bn(M, N);
+    return tc_launch(st, tf32, A, B, M, N, K, ep, part, part_cap, BN);
 }
 
 // ---- split conversions ---------------------------------------------------------------

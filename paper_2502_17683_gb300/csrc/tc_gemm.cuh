@@ -33,8 +33,15 @@ struct TcEpilogue {
 
 bool tc_available();
 // D = A B^T for A (M x K) and B (N x K) split operands; tf32 selects the TF32x3 kind.
+// With only the transposed FP64 output requested, K may be split over CTAs: the partial
+// sums go to `part` (capacity part_cap doubles) and are reduced in a fixed order.
 cudaError_t tc_gemm(cudaStream_t st, bool tf32, const SplitMat& A, const SplitMat& B, int M,
-                    int N, int K, const TcEpilogue& ep);
+                    int N, int K, const TcEpilogue& ep, double* part = nullptr,
+                    size_t part_cap = 0);
+// Autotuning of the tile N: while on, the first call of every (M, N, K, precision,
+// epilogue) outside stream capture times the candidates and caches the fastest.
+void tc_set_tuning(bool on);
+int tc_tuned_entries();
 // Device error word of the tensor-core kernels (bounded waits that gave up); read and
 // clear.
 int tc_take_error();

@@ -1,0 +1,67 @@
+"""Batched ALS of independent problems of uneven shapes (one CUDA graph per sweep for all
+problems) against the single-problem driver and the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import thc_cpd as O
+from tests._util import to_dev
+from thc_inputs import batched_shapes, make_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import api as a
+    return a
+
+
+def _problems(shapes, seed0):
+    out = []
+    for i, (o, v, Rt, R) in enumerate(shapes):
+        p = make_problem(o, v, Rt, R, seed=seed0 + i)
+        d = to_dev(p, torch)
+        d["lam"] = torch.ones(R, dtype=torch.float64, device="cuda")
+        d["host"] = p
+        out.append(d)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_batched_equals_single_problem_runs(api, prec):
+    shapes = batched_shapes(6, seed=3, o_lo=2, o_hi=9)
+    assert len(set(shapes)) > 1  # uneven
+    batch = _problems(shapes, 100)
+    solo = _problems(shapes, 100)
+    res = api.thc_cpd_als_batched(batch, 8, 0.0, precision=prec)
+    for b, s_, r in zip(batch, solo, res):
+        out = api.thc_cpd_als(s_["Xo"], s_["Xv"], s_["Z"], s_["A"], s_["lam"], 8, 0.0, precision=prec)
+        assert r["sweeps"] == out["sweeps"] == 8
+        assert r["fit"] == out["fit"]  # same kernels in the same order: same bits
+        for a, c in zip(b["A"], s_["A"]):
+            assert torch.equal(a, c)
+
+
+def test_batched_fp64_matches_oracle_and_stops_per_problem(api):
+    shapes = [(3, 15, 48, 64), (5, 25, 96, 112), (2, 10, 48, 48)]
+    batch = _problems(shapes, 7)
+    res = api.thc_cpd_als_batched(batch, 200, 1e-5, precision="fp64")
+    for d, r in zip(batch, res):
+        p = d["host"]
+        ref = O.als(p.Xo, p.Xv, p.Z, p.A, 200, tol=1e-5)
+        assert r["sweeps"] == ref["sweeps"]
+        assert abs(r["fit"] - ref["fits"][-1]) <= 1e-10
+    assert len({r["sweeps"] for r in res}) >= 1
+
+
+def test_batched_autotune_keeps_results(api):
+    shapes = batched_shapes(4, seed=5, o_lo=3, o_hi=8)
+    batch = _problems(shapes, 300)
+    ref = _problems(shapes, 300)
+    res = api.thc_cpd_als_batched(batch, 5, 0.0, precision="bf16x3", autotune=True)
+    res0 = api.thc_cpd_als_batched(ref, 5, 0.0, precision="bf16x3")
+    for a, b in zip(res, res0):
+        assert abs(a["fit"] - b["fit"]) <= 1e-6

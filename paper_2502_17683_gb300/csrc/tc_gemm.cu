@@ -259,21 +259,38 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     } else if (warp >= 2) {
         // ---- epilogue: TMEM -> registers -> fused outputs ----
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        const bool ok = mbar_wait(tmem_full, 0, 4);
-        tc_fence_after();
-        const int m = m0 + 32 * q + lane;
         const TcEpilogue& ep = args.ep;
+        const int m = m0 + 32 * q + lane;
         // per-warp staging of a 32 x 16 slice (the ring is idle once the MMAs are done), so
         // that row-major outputs and the Hadamard partner are accessed row-contiguously
         float* stg = (float*)smem + (warp - 2) * 32 * 17;
         const bool rowmajor = ep.out_f32 || ep.mul;
         double* f64t = gridDim.z > 1 ? args.part + (size_t)blockIdx.z * args.N * ep.ld_f64t
                                      : ep.out_f64t;
+        const int col = lane & 15, half = lane >> 4;
+        // partner values of one 32 x 16 slice: lane (col, half) holds rows 2 rr + half
+        float cur[16], nxt[16];
+        auto load_partner = [&](int c, float* dst) {
+            const int n = n0 + c + col;
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr) {
+                const int mm = m0 + 32 * q + 2 * rr + half;
+                dst[rr] = (mm < args.M && n < args.N) ? __ldg(ep.mul + (size_t)mm * ep.ld_mul + n)
+                                                      : 0.f;
+            }
+        };
+        // the first slice's partner loads overlap the main loop
+        if (ep.mul) load_partner(0, cur);
+        const bool ok = mbar_wait(tmem_full, 0, 4);
+        tc_fence_after();
+#pragma unroll 1
         for (int c = 0; c < BN; c += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-            if (!ok) continue;
-            if (f64t && m < args.M) {
+            // software pipeline: the next slice's partner loads are in flight while this
+            // slice is written
+            if (ep.mul && c + 16 < BN) load_partner(c + 16, nxt);
+            if (ok && f64t && m < args.M) {
                 // transposed FP64 output: consecutive lanes hold consecutive m (coalesced)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -281,24 +298,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
                     if (n < args.N) f64t[(size_t)n * ep.ld_f64t + m] = (double)v[j];
                 }
             }
-            if (rowmajor) {
+            if (ok && rowmajor) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
-                const int col = lane & 15, half = lane >> 4;
-                const int n = n0 + c + col;
-                // all partner loads of the slice in flight at once (read-only path), so the
-                // stores below do not serialise them
-                float mv[16];
-                if (ep.mul) {
-#pragma unroll
-                    for (int rr = 0; rr < 16; ++rr) {
-                        const int mm = m0 + 32 * q + 2 * rr + half;
-                        mv[rr] = (mm < args.M && n < args.N)
-                                     ? __ldg(ep.mul + (size_t)mm * ep.ld_mul + n)
-                                     : 0.f;
-                    }
-                }
                 __syncwarp();
+                const int n = n0 + c + col;
 #pragma unroll
                 for (int rr = 0; rr < 16; ++rr) {
                     const int row = 2 * rr + half;
@@ -308,10 +312,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
                         if (ep.out_f32) ep.out_f32[(size_t)mm * ep.ld_f32 + n] = d;
                         if (ep.mul)
                             store_split<TF32>(args.out_hi, args.out_lo,
-                                              (size_t)mm * args.ld_split + n, d * mv[rr]);
+                                              (size_t)mm * args.ld_split + n, d * cur[rr]);
                     }
                 }
                 __syncwarp();
+            }
+            if (ep.mul) {
+#pragma unroll
+                for (int rr = 0; rr < 16; ++rr) cur[rr] = nxt[rr];
             }
         }
     }

@@ -72,7 +72,9 @@ typedef struct thc_cpd_opts {
                             shapes of every GEMM shape the first time it is met (on the
                             live operands, before any graph capture) and keeps the fastest
                             for the rest of the process */
-    int reserved;
+    int accepted_out;    /* out (thc_cpd_als with mlp): accepted extrapolated steps */
+    const float* mlp;    /* thc_cpd_als: device parameters of the step-proposer network
+                            (THC_CPD_MLP_NPARAM floats) or NULL for plain ALS; see below */
 } thc_cpd_opts;
 
 /* One independent problem of a batched run (thc_cpd_als_batched). Inputs as for
@@ -151,6 +153,42 @@ thc_cpd_status thc_cpd_split_gemm(int M, int N, int K, const double* A, const do
  * (split precisions run without the FP64 polish phase); opts->history is not used. */
 thc_cpd_status thc_cpd_als_batched(int nprob, thc_cpd_problem* probs, int max_sweeps, double tol,
                                    thc_cpd_opts* opts);
+
+/* ---- learned extrapolation of the ALS step (the paper's ALS has no line search; this
+ * is an acceleration on top of it) -------------------------------------------------------
+ * A 40-64-64-1 tanh network maps the ALS history to a step factor alpha = 1 + 3 sigmoid(z)
+ * in [1, 4]. Inputs, most recent sweep first, zero-padded: 8 values
+ * log10(max(log L_{s-1} - log L_s, 1e-12)) / 6 of the loss decrements, then per sweep the
+ * four log10(max(||B_k^s - B_k^{s-1}|| / ||B_k^s||, 1e-12)) / 6 of the lam-absorbed
+ * factors (lam multiplies the last mode). With opts->mlp set, thc_cpd_als tries after each
+ * sweep the point P + alpha (P_ALS - P) and keeps it only if its exact FP64 loss is below
+ * the plain ALS point's, so the run is never worse than plain ALS step by step.
+ * Parameters (FP32 masters; the kernels use BF16-rounded weights with FP32 accumulation):
+ * W1 (64 x 40 row-major), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1). */
+#define THC_CPD_MLP_NPARAM 6849
+
+/* Glorot-uniform weights and zero biases from a counter-based generator (SplitMix64). */
+thc_cpd_status thc_cpd_mlp_init(float* params, unsigned long long seed, const thc_cpd_opts* opts);
+/* alpha[i] for the n feature rows X (n x 40, device). Synchronises. */
+thc_cpd_status thc_cpd_mlp_forward(const float* params, const float* X, int n, float* alpha,
+                                   const thc_cpd_opts* opts);
+/* Gradient (device, THC_CPD_MLP_NPARAM) of the MSE (1/n) sum (alpha_i - y_i)^2 and the loss
+ * (host). Synchronises. */
+thc_cpd_status thc_cpd_mlp_grad(const float* params, const float* X, const float* y, int n,
+                                float* grad, float* loss_host, const thc_cpd_opts* opts);
+/* Adam training (lr, batches of `batch`, reshuffled every epoch from `seed`) of the MSE on
+ * (X, y); params updated in place; final loss over all rows in *final_loss_host. */
+thc_cpd_status thc_cpd_mlp_train(float* params, const float* X, const float* y, int n, int epochs,
+                                 int batch, float lr, unsigned long long seed,
+                                 float* final_loss_host, const thc_cpd_opts* opts);
+/* Training data from a plain ALS trajectory: after each of `sweeps` sweeps, the 40
+ * features (feats, host, sweeps x 40) and the exact FP64 losses of the trial points for
+ * each alpha in alphas (trial_losses, host, sweeps x nalpha; alpha = 1 is the ALS point).
+ * The trajectory itself is plain ALS (A and lam end at its last point). */
+thc_cpd_status thc_cpd_als_trajectory(int o, int v, int Rt, int R, const double* Xo,
+                                      const double* Xv, const double* Z, double* const A[4],
+                                      double* lam, int sweeps, const double* alphas, int nalpha,
+                                      float* feats, double* trial_losses, thc_cpd_opts* opts);
 
 /* ---- launch accounting and kernel timing (tracing support; the paper has no
  * counterpart: it reports wall-times only) ---------------------------------------- */

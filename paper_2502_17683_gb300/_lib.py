@@ -19,7 +19,9 @@ PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version", "thc_cpd_launch_count",
            "thc_cpd_profile", "thc_cpd_profile_read", "thc_cpd_split_gemm",
-           "thc_cpd_mttkrp_noalloc", "thc_cpd_als_batched")
+           "thc_cpd_mttkrp_noalloc", "thc_cpd_als_batched", "thc_cpd_mlp_init",
+           "thc_cpd_mlp_forward", "thc_cpd_mlp_grad", "thc_cpd_mlp_train", "thc_cpd_als_trajectory")
+MLP_NPARAM = 6849
 KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
 
 
@@ -42,7 +44,8 @@ class Opts(ctypes.Structure):
                 ("flags_out", ctypes.c_int),
                 ("polish_sweeps", ctypes.c_int),
                 ("autotune", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("accepted_out", ctypes.c_int),
+                ("mlp", ctypes.c_void_p)]
 
 
 class Problem(ctypes.Structure):
@@ -70,6 +73,13 @@ _SIGS = {
     "thc_cpd_split_gemm": [I, I, I, P, P, P, OPTS],
     "thc_cpd_mttkrp_noalloc": [I, I, I, I, P, P, P, PTR4, I, P, OPTS],
     "thc_cpd_als_batched": [I, ctypes.c_void_p, I, D, OPTS],
+    "thc_cpd_mlp_init": [P, ctypes.c_ulonglong, OPTS],
+    "thc_cpd_mlp_forward": [P, P, I, P, OPTS],
+    "thc_cpd_mlp_grad": [P, P, P, I, P, ctypes.POINTER(ctypes.c_float), OPTS],
+    "thc_cpd_mlp_train": [P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong,
+                          ctypes.POINTER(ctypes.c_float), OPTS],
+    "thc_cpd_als_trajectory": [I, I, I, I, P, P, P, PTR4, P, I, DP, I,
+                               ctypes.POINTER(ctypes.c_float), DP, OPTS],
 }
 
 _lib = None

@@ -10,18 +10,29 @@ import ctypes
 
 import torch
 
-from ._lib import (ERR_ARG, KCLASS_NAMES, PRECISIONS, PTR4, KStat, Opts, Problem, ThcCpdError,
-                   check, load)
+from ._lib import (ERR_ARG, KCLASS_NAMES, MLP_NPARAM, PRECISIONS, PTR4, KStat, Opts, Problem,
+                   ThcCpdError, check, load)
 
 __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_version", "thc_cpd_launch_count", "thc_cpd_profile",
            "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc",
-           "thc_cpd_als_batched", "Opts"]
+           "thc_cpd_als_batched", "thc_cpd_mlp_init", "thc_cpd_mlp_forward", "thc_cpd_mlp_grad",
+           "thc_cpd_mlp_train", "thc_cpd_als_trajectory", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
         raise ThcCpdError(ERR_ARG, f"{name} must be a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ThcCpdError(ERR_ARG, f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ThcCpdError(ERR_ARG, f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _fdev(t: torch.Tensor, name: str, shape=None) -> int:
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+        raise ThcCpdError(ERR_ARG, f"{name} must be a float32 CUDA tensor")
     if not t.is_contiguous():
         raise ThcCpdError(ERR_ARG, f"{name} must be contiguous")
     if shape is not None and tuple(t.shape) != tuple(shape):
@@ -125,7 +136,7 @@ def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", 
 
 def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision="fp64",
                 stream=None, loss_every: int = 0, history: bool = False, polish_sweeps: int = 0,
-                autotune: bool = False):
+                autotune: bool = False, mlp=None):
     o, v, Rt = _dims(Xo, Xv, Z)
     R = A[0].shape[1]
     loss, fit, done = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
@@ -133,12 +144,15 @@ def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision=
     opts = _opts(precision, stream, loss_every,
                  ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
                  polish_sweeps, autotune)
+    if mlp is not None:
+        opts.mlp = _fdev(mlp, "mlp", (MLP_NPARAM,))
     check(load().thc_cpd_als(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
                              _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R),
                              _dev(lam, "lam", (R,)), int(max_sweeps), float(tol),
                              ctypes.byref(done), ctypes.byref(loss), ctypes.byref(fit),
                              ctypes.byref(opts)))
-    out = dict(sweeps=done.value, loss=loss.value, fit=fit.value, flags=opts.flags_out)
+    out = dict(sweeps=done.value, loss=loss.value, fit=fit.value, flags=opts.flags_out,
+               accepted=opts.accepted_out)
     if hist is not None:
         h = list(hist)[: 2 * done.value]
         out["losses"] = h[0::2]
@@ -198,3 +212,61 @@ def thc_cpd_als_batched(problems, max_sweeps: int, tol: float = 0.0, precision="
                                      float(tol), ctypes.byref(opts)))
     return [dict(sweeps=arr[i].sweeps_done, loss=arr[i].loss, fit=arr[i].fit, flags=arr[i].flags_out)
             for i in range(n)]
+
+
+def thc_cpd_mlp_init(seed: int = 0, params=None, stream=None):
+    if params is None:
+        params = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_mlp_init(_fdev(params, "params", (MLP_NPARAM,)), int(seed), ctypes.byref(opts)))
+    return params
+
+
+def thc_cpd_mlp_forward(params, X, stream=None):
+    n = X.shape[0]
+    alpha = torch.empty(n, dtype=torch.float32, device=X.device)
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_mlp_forward(_fdev(params, "params", (MLP_NPARAM,)), _fdev(X, "X", (n, 40)),
+                                     n, _fdev(alpha, "alpha"), ctypes.byref(opts)))
+    return alpha
+
+
+def thc_cpd_mlp_grad(params, X, y, stream=None):
+    n = X.shape[0]
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+    loss = ctypes.c_float()
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_mlp_grad(_fdev(params, "params", (MLP_NPARAM,)), _fdev(X, "X", (n, 40)),
+                                  _fdev(y, "y", (n,)), n, _fdev(grad, "grad"), ctypes.byref(loss),
+                                  ctypes.byref(opts)))
+    return grad, loss.value
+
+
+def thc_cpd_mlp_train(params, X, y, epochs: int, batch: int = 64, lr: float = 1e-3, seed: int = 0,
+                      stream=None) -> float:
+    n = X.shape[0]
+    loss = ctypes.c_float()
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_mlp_train(_fdev(params, "params", (MLP_NPARAM,)), _fdev(X, "X", (n, 40)),
+                                   _fdev(y, "y", (n,)), n, int(epochs), int(batch), float(lr),
+                                   int(seed), ctypes.byref(loss), ctypes.byref(opts)))
+    return loss.value
+
+
+def thc_cpd_als_trajectory(Xo, Xv, Z, A, lam, sweeps: int, alphas, precision="fp64", stream=None):
+    """Plain ALS for `sweeps` sweeps, recording per sweep the 40 features and the exact losses
+    of the trial points at each alpha. Returns (features (sweeps, 40), losses (sweeps, na))."""
+    import numpy as np
+    o, v, Rt = _dims(Xo, Xv, Z)
+    R = A[0].shape[1]
+    al = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+    feats = np.zeros((sweeps, 40), dtype=np.float32)
+    tl = np.zeros((sweeps, len(al)), dtype=np.float64)
+    opts = _opts(precision, stream)
+    check(load().thc_cpd_als_trajectory(
+        o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)), _dev(Z, "Z", (Rt, Rt)),
+        _ptr4(A, (o, v, o, v), R), _dev(lam, "lam", (R,)), int(sweeps),
+        al.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(al),
+        feats.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+        tl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts)))
+    return feats, tl

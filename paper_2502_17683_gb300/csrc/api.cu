@@ -4,8 +4,10 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <memory>
 #include <string>
 #include <vector>
@@ -455,11 +457,121 @@ thc_cpd_status obtain_norm(Ctx& c, double normG2, double* out) {
     return THC_CPD_OK;
 }
 
-// The ALS driver shared by thc_cpd_als and thc_cpd_als_sweep.
+// ---- learned extrapolation -------------------------------------------------------------
+// After each plain ALS sweep: per-mode change norms of the lam-absorbed factors, the 40
+// history features, the network's step factor alpha, the trial point
+// T = P + alpha (N - P) (P: previous point, N: the ALS point), its exact FP64 loss, and
+// acceptance iff that loss is below the ALS point's. In recording mode the exact losses
+// of trial points on a grid of alpha are stored instead and the plain trajectory is kept.
+struct LearnArgs {
+    const float* mlp = nullptr;     // network parameters (device) or NULL
+    const double* alphas = nullptr; // recording: alpha grid (host)
+    int nalpha = 0;
+    float* feats = nullptr;         // recording: features per sweep (host, 40 each)
+    double* tloss = nullptr;        // recording: trial losses per sweep (host, nalpha each)
+    int accepted = 0;               // out: accepted extrapolations
+};
+
+struct LearnWs {
+    double* T[4] = {};
+    double* lamk[4] = {};
+    double* lamT = nullptr;
+    double* Wtr[4] = {};
+    double* Gtr[4] = {};
+    double* Ytr = nullptr;
+    double* red = nullptr;
+    double* chg = nullptr;  // 8 doubles: (num, den) per mode
+    float* feat = nullptr;
+    float* alpha = nullptr;
+    DevScalars* sc = nullptr;
+    void* block = nullptr;
+    cudaStream_t st = nullptr;
+    ~LearnWs() {
+        if (block) cudaFreeAsync(block, st);
+    }
+};
+
+thc_cpd_status learn_init(Ctx& c, LearnWs& L) {
+    const int Rt = c.s.Rt, R = c.s.R;
+    size_t b = 0;
+    for (int k = 0; k < 4; ++k) b += Arena::need<double>((size_t)c.s.n[k] * R);
+    b += 5 * Arena::need<double>(R) + 5 * Arena::need<double>((size_t)Rt * R) +
+         4 * Arena::need<double>((size_t)R * R) + Arena::need<double>(256) + Arena::need<double>(8) +
+         Arena::need<float>(64) + Arena::need<DevScalars>(1);
+    L.st = c.st;
+    CK(cudaMallocAsync(&L.block, b, c.st));
+    Arena ar;
+    ar.base = (char*)L.block;
+    for (int k = 0; k < 4; ++k) L.T[k] = ar.take<double>((size_t)c.s.n[k] * R);
+    for (int k = 0; k < 4; ++k) L.lamk[k] = ar.take<double>(R);
+    L.lamT = ar.take<double>(R);
+    for (int k = 0; k < 4; ++k) L.Wtr[k] = ar.take<double>((size_t)Rt * R);
+    L.Ytr = ar.take<double>((size_t)Rt * R);
+    for (int k = 0; k < 4; ++k) L.Gtr[k] = ar.take<double>((size_t)R * R);
+    L.red = ar.take<double>(256);
+    L.chg = ar.take<double>(8);
+    L.feat = ar.take<float>(48);
+    L.alpha = L.feat + 40;
+    L.sc = ar.take<DevScalars>(1);
+    return THC_CPD_OK;
+}
+
+// 40 features from the histories, most recent first (same formula as the oracle's)
+void make_features(const std::vector<double>& loss_hist, const std::vector<std::array<double, 4>>& chg,
+                   float* f) {
+    for (int i = 0; i < 40; ++i) f[i] = 0.f;
+    const int nl = (int)loss_hist.size();
+    for (int i = 0; i < 8; ++i) {
+        const int s = nl - 1 - i;
+        if (s >= 1) {
+            const double d = log(loss_hist[s - 1]) - log(loss_hist[s]);
+            f[i] = (float)(log10(std::max(d, 1e-12)) / 6.0);
+        }
+    }
+    const int nc = (int)chg.size();
+    for (int i = 0; i < 8; ++i) {
+        const int s = nc - 1 - i;
+        if (s >= 0)
+            for (int k = 0; k < 4; ++k) f[8 + 4 * i + k] = (float)(log10(std::max(chg[s][k], 1e-12)) / 6.0);
+    }
+}
+
+// exact FP64 loss of the trial factors T with weights lamT (W, G, Y into the trial buffers)
+thc_cpd_status trial_loss(Ctx& c, LearnWs& L, double* loss) {
+    const int Rt = c.s.Rt, R = c.s.R;
+    for (int k = 0; k < 4; ++k) {
+        dgemm(c.st, true, Rt, R, c.s.n[k], c.X[k], Rt, L.T[k], nullptr, R, L.Wtr[k], R, nullptr, false,
+              c.part, c.part_cap);
+        dgemm(c.st, true, R, R, c.s.n[k], L.T[k], R, L.T[k], nullptr, R, L.Gtr[k], R, nullptr, true,
+              c.part, c.part_cap);
+    }
+    dgemm(c.st, true, Rt, R, Rt, c.Z, Rt, L.Wtr[0], L.Wtr[1], R, L.Ytr, R, nullptr, false, c.part, c.part_cap);
+    CK(cudaMemcpyAsync(L.sc, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+    loss_eval(c.st, Rt, R, L.Ytr, L.Wtr[2], L.Wtr[3], L.lamT, L.Gtr, c.red, L.sc, 0.0);
+    DevScalars* h = host_scalars();
+    if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
+    CK(cudaMemcpyAsync(h, L.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    *loss = h->loss;
+    return THC_CPD_OK;
+}
+
+// build T = P + alpha (N - P) and its column normalisation (lamT = product of the norms)
+void build_trial(Ctx& c, LearnWs& L, double* const A[4], const double* lam, double alpha) {
+    const int R = c.s.R;
+    for (int k = 0; k < 4; ++k) {
+        trial_point(c.st, c.s.n[k], R, A[k], c.Asnap[k], lam, c.lamsnap, k == 3, alpha, L.T[k]);
+        normalise_columns(c.st, c.s.n[k], R, L.T[k], L.lamk[k]);
+    }
+    const double* lk[4] = {L.lamk[0], L.lamk[1], L.lamk[2], L.lamk[3]};
+    lam_product(c.st, R, lk, L.lamT);
+}
+
+// The ALS driver shared by thc_cpd_als, thc_cpd_als_sweep and the trajectory recorder.
 thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
                        const double* Z, double* const A[4], double* lam, int max_sweeps,
                        double tol, double normG2, int* sweeps_done, double* loss_host,
-                       double* fit_host, thc_cpd_opts* opts) {
+                       double* fit_host, thc_cpd_opts* opts, LearnArgs* la = nullptr) {
     Shape s;
     CKS(check_shape(o, v, Rt, R, &s));
     CKS(check_ptrs(Xo, Xv, Z, A));
@@ -472,6 +584,20 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     double nG2 = 0.0;
     CKS(obtain_norm(c, normG2, &nG2));
     refresh_state(c, A);
+    const bool learning = la && (la->mlp || la->nalpha > 0);
+    LearnWs L;
+    std::vector<double> loss_hist;
+    std::vector<std::array<double, 4>> chg_hist;
+    if (learning) {
+        CKS(learn_init(c, L));
+        // loss of the start point (history entry L_0)
+        for (int k = 0; k < 4; ++k) CK(cudaMemcpyAsync(L.T[k], A[k], sizeof(double) * s.n[k] * R,
+                                                       cudaMemcpyDeviceToDevice, c.st));
+        CK(cudaMemcpyAsync(L.lamT, lam, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
+        double l0;
+        CKS(trial_loss(c, L, &l0));
+        loss_hist.push_back(l0);
+    }
     const int loss_every = (opts && opts->loss_every > 0) ? opts->loss_every : 0;
     const int polish = (opts && opts->polish_sweeps > 0 && tol <= 0.0) ? opts->polish_sweeps : 0;
     const bool split_run = c.prec != THC_CPD_FP64;
@@ -495,7 +621,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
             flags |= 4;
         }
         bool eval = true;
-        if (c.prec != THC_CPD_FP64) {
+        if (c.prec != THC_CPD_FP64 && !learning) {
             if (loss_every > 0)
                 eval = (sw % loss_every == 0) || sw == max_sweeps;
             else
@@ -530,6 +656,73 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
         }
         if (used) flags |= 1;
         done_sweeps = sw;
+        if (learning) {
+            // change norms between the previous point (snapshot) and the ALS point
+            std::array<double, 4> ch;
+            double hc[8];
+            for (int k = 0; k < 4; ++k)
+                change_norm(c.st, s.n[k], R, A[k], c.Asnap[k], lam, c.lamsnap, k == 3, L.red, L.chg + 2 * k);
+            CK(cudaMemcpyAsync(hc, L.chg, sizeof(hc), cudaMemcpyDeviceToHost, c.st));
+            CK(cudaStreamSynchronize(c.st));
+            for (int k = 0; k < 4; ++k) ch[k] = hc[2 * k + 1] > 0 ? sqrt(hc[2 * k] / hc[2 * k + 1]) : 0.0;
+            chg_hist.push_back(ch);
+            std::vector<double> lh = loss_hist;
+            lh.push_back(h.loss);
+            float f[40];
+            make_features(lh, chg_hist, f);
+            if (la->nalpha > 0) {
+                // recording: exact losses of the trial points on the alpha grid
+                if (la->feats) memcpy(la->feats + (size_t)40 * (sw - 1), f, sizeof f);
+                for (int a = 0; a < la->nalpha; ++a) {
+                    double tl = h.loss;
+                    if (la->alphas[a] != 1.0) {
+                        build_trial(c, L, A, lam, la->alphas[a]);
+                        CKS(trial_loss(c, L, &tl));
+                    }
+                    if (la->tloss) la->tloss[(size_t)la->nalpha * (sw - 1) + a] = tl;
+                }
+                loss_hist.push_back(h.loss);
+            } else {
+                CK(cudaMemcpyAsync(L.feat, f, sizeof f, cudaMemcpyHostToDevice, c.st));
+                mlp_forward1(c.st, la->mlp, L.feat, L.alpha);
+                float ha = 1.f;
+                CK(cudaMemcpyAsync(&ha, L.alpha, sizeof(float), cudaMemcpyDeviceToHost, c.st));
+                CK(cudaStreamSynchronize(c.st));
+                bool accepted = false;
+                if (sw >= 2 && ha > 1.02f && isfinite(ha)) {
+                    build_trial(c, L, A, lam, (double)ha);
+                    double tl;
+                    CKS(trial_loss(c, L, &tl));
+                    if (tl < h.loss) {
+                        // accept: the trial becomes the current point, with its state
+                        for (int k = 0; k < 4; ++k) {
+                            CK(cudaMemcpyAsync(A[k], L.T[k], sizeof(double) * s.n[k] * R,
+                                               cudaMemcpyDeviceToDevice, c.st));
+                            CK(cudaMemcpyAsync(c.G[k], L.Gtr[k], sizeof(double) * R * R,
+                                               cudaMemcpyDeviceToDevice, c.st));
+                            if (c.prec == THC_CPD_FP64)
+                                CK(cudaMemcpyAsync(c.W[k], L.Wtr[k], sizeof(double) * Rt * R,
+                                                   cudaMemcpyDeviceToDevice, c.st));
+                        }
+                        CK(cudaMemcpyAsync(lam, L.lamT, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
+                        if (c.prec != THC_CPD_FP64)
+                            for (int k = 0; k < 4; ++k) CK(mixed_project(c.mx, c.st, k, A[k], false));
+                        CK(cudaMemcpyAsync(c.sc, L.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+                        DevScalars* hs = host_scalars();
+                        CK(cudaMemcpyAsync(hs, L.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.st));
+                        CK(cudaStreamSynchronize(c.st));
+                        h.loss = hs->loss;
+                        h.fit = hs->fit;
+                        accepted = true;
+                        la->accepted++;
+                    }
+                }
+                loss_hist.push_back(h.loss);
+                // convergence decided on the host from the accepted points' fits
+                h.done = (tol > 0.0 && isfinite(fit1) && fabs(h.fit - fit1) < tol) ? 1 : 0;
+                (void)accepted;
+            }
+        }
         if (eval) {
             fit2 = fit1;
             fit1 = h.fit;
@@ -883,8 +1076,27 @@ thc_cpd_status thc_cpd_als(int o, int v, int Rt, int R, const double* Xo, const 
                            const double* Z, double* const A[4], double* lam, int max_sweeps,
                            double tol, int* sweeps_done, double* loss_host, double* fit_host,
                            thc_cpd_opts* opts) {
-    return run_als(o, v, Rt, R, Xo, Xv, Z, A, lam, max_sweeps, tol, 0.0, sweeps_done, loss_host,
-                   fit_host, opts);
+    LearnArgs la;
+    la.mlp = opts ? opts->mlp : nullptr;
+    thc_cpd_status st = run_als(o, v, Rt, R, Xo, Xv, Z, A, lam, max_sweeps, tol, 0.0, sweeps_done,
+                                loss_host, fit_host, opts, la.mlp ? &la : nullptr);
+    if (opts && la.mlp) opts->accepted_out = la.accepted;
+    return st;
+}
+
+thc_cpd_status thc_cpd_als_trajectory(int o, int v, int Rt, int R, const double* Xo,
+                                      const double* Xv, const double* Z, double* const A[4],
+                                      double* lam, int sweeps, const double* alphas, int nalpha,
+                                      float* feats, double* trial_losses, thc_cpd_opts* opts) {
+    if (!alphas || nalpha < 1 || nalpha > 64 || !feats || !trial_losses)
+        return set_err(THC_CPD_ERR_ARG, "need 1..64 alphas and host feature / loss buffers");
+    LearnArgs la;
+    la.alphas = alphas;
+    la.nalpha = nalpha;
+    la.feats = feats;
+    la.tloss = trial_losses;
+    int done = 0;
+    return run_als(o, v, Rt, R, Xo, Xv, Z, A, lam, sweeps, 0.0, 0.0, &done, nullptr, nullptr, opts, &la);
 }
 
 }  // extern "C"

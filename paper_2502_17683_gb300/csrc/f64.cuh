@@ -51,6 +51,16 @@ void scalars_init(cudaStream_t st, DevScalars* sc, double normG2);
 cudaError_t pinv_solve(cudaStream_t st, int R, int n, double* H, const double* M,
                        double* A, double* V, double* w, double* T, int* host_sweeps);
 
+// Learned extrapolation helpers on lam-absorbed factors (lam multiplies the last mode):
+// out2 = (||N - P||_F^2, ||N||_F^2); T = P + alpha (N - P); out = a o b o c o d.
+void change_norm(cudaStream_t st, int n, int R, const double* An, const double* Ao,
+                 const double* ln, const double* lo, bool absorb, double* red, double* out2);
+void trial_point(cudaStream_t st, int n, int R, const double* An, const double* Ao,
+                 const double* ln, const double* lo, bool absorb, double alpha, double* T);
+void lam_product(cudaStream_t st, int R, const double* const l[4], double* out);
+// the network's alpha for one 40-feature vector (device pointers)
+void mlp_forward1(cudaStream_t st, const float* P, const float* x, float* alpha);
+
 // fill lam with ones
 void fill(cudaStream_t st, double* p, long n, double v);
 

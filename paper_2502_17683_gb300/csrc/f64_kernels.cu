@@ -673,3 +673,85 @@ void fill(cudaStream_t st, double* p, long n, double v) {
 }
 
 }  // namespace thc
+
+namespace thc {
+
+// ---- learned extrapolation helpers (FP64) --------------------------------------------
+// Factors with lam absorbed into the last mode: X = A (k < 3) or A diag(lam) (k = 3).
+__global__ void __launch_bounds__(RED_THREADS)
+k_change_partials(long n, int R, const double* __restrict__ An, const double* __restrict__ Ao,
+                  const double* __restrict__ ln, const double* __restrict__ lo, int absorb,
+                  double* __restrict__ red) {
+    __shared__ double sh[32];
+    double num = 0.0, den = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i % R);
+        const double a = absorb ? An[i] * ln[r] : An[i];
+        const double b = absorb ? Ao[i] * lo[r] : Ao[i];
+        num = fma(a - b, a - b, num);
+        den = fma(a, a, den);
+    }
+    num = block_reduce_sum(num, sh);
+    den = block_reduce_sum(den, sh);
+    if (threadIdx.x == 0) {
+        red[2 * blockIdx.x] = num;
+        red[2 * blockIdx.x + 1] = den;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_change_final(const double* __restrict__ red, int nb, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += red[2 * i];
+        b += red[2 * i + 1];
+    }
+    a = block_reduce_sum(a, sh);
+    b = block_reduce_sum(b, sh);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+void change_norm(cudaStream_t st, int n, int R, const double* An, const double* Ao,
+                 const double* ln, const double* lo, bool absorb, double* red, double* out2) {
+    const int nb = 64;
+    k_change_partials<<<nb, RED_THREADS, 0, st>>>((long)n * R, R, An, Ao, ln, lo, absorb ? 1 : 0, red);
+    k_change_final<<<1, RED_THREADS, 0, st>>>(red, nb, out2);
+    count_launch(2);
+}
+
+// T = P + alpha (N - P) on lam-absorbed factors
+__global__ void k_trial(long n, int R, const double* __restrict__ An, const double* __restrict__ Ao,
+                        const double* __restrict__ ln, const double* __restrict__ lo, int absorb,
+                        double alpha, double* __restrict__ T) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i % R);
+        const double a = absorb ? An[i] * ln[r] : An[i];
+        const double b = absorb ? Ao[i] * lo[r] : Ao[i];
+        T[i] = fma(alpha, a - b, b);
+    }
+}
+
+void trial_point(cudaStream_t st, int n, int R, const double* An, const double* Ao,
+                 const double* ln, const double* lo, bool absorb, double alpha, double* T) {
+    const long N = (long)n * R;
+    k_trial<<<(int)std::min<long>(cdiv(N, 256), 4L * kNumSM), 256, 0, st>>>(N, R, An, Ao, ln, lo,
+                                                                           absorb ? 1 : 0, alpha, T);
+    count_launch();
+}
+
+__global__ void k_lam_product(int R, const double* a, const double* b, const double* c,
+                              const double* d, double* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) out[r] = a[r] * b[r] * c[r] * d[r];
+}
+
+void lam_product(cudaStream_t st, int R, const double* const l[4], double* out) {
+    k_lam_product<<<cdiv(R, 128), 128, 0, st>>>(R, l[0], l[1], l[2], l[3], out);
+    count_launch();
+}
+
+}  // namespace thc

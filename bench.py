@@ -50,6 +50,12 @@ def parse():
                     help="workload size (profiling captures only; the bench line uses c2)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the FP64 path beside the split precision")
+    ap.add_argument("--learned-report", action="store_true",
+                    help="o=30 v=150 R_thc=720 R_cp=1080, split precision: sweeps and wall-time "
+                         "to a 1e-6 fit change, plain vs learned extrapolation")
+    ap.add_argument("--batched", action="store_true",
+                    help="64 uneven problems (o in [4,40], v=5o, R_thc=4(o+v), R_cp=6(o+v) "
+                         "rounded up to 16), 40 sweeps each: batched graph vs one by one")
     return ap.parse_args()
 
 
@@ -113,6 +119,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (barrier semantics); x itself without a process
+    group. Works on any backend (NCCL with a CUDA device, gloo on the CPU)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, ms_per_rank: float, device=None):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest
+    rank's time (weak scaling)."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    ms = max_over_ranks(ms_per_rank, device)
+    return world * units_per_rank / (ms / 1000.0), ms
+
+
 def oracle_sweeps_per_s(seconds: float, seed: int):
     """The FP64 CPU oracle as it stands, on the host cores, over a bounded number of sweeps
     of the same workload from the same start point."""
@@ -162,10 +189,97 @@ def run_reference(args):
     return 0
 
 
+def learned_report(args):
+    """Wall-time and sweeps to |fit_s - fit_{s-1}| < 1e-6 at o=30 v=150 R_thc=720
+    R_cp=1080 (split precision), plain ALS vs the trained step proposer, plus plain FP64."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import api, learned
+    from thc_inputs import make_problem
+    prec = args.precision or "bf16x3"
+    P = learned.load_params()
+    rows = {}
+    for seed in (0, 1):
+        p = make_problem(30, 150, 720, 1080, seed=seed)
+        t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        for name, mlp, pr in (("plain", None, prec), ("learned", P, prec), ("plain_fp64", None, "fp64")):
+            A = [t(a) for a in p.A]
+            lam = torch.ones(1080, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = api.thc_cpd_als(t(p.Xo), t(p.Xv), t(p.Z), A, lam, 5000, 1e-6, precision=pr, mlp=mlp)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            rows.setdefault(name, []).append({"seed": seed, "sweeps": out["sweeps"], "seconds": dt,
+                                              "fit": out["fit"], "accepted": out.get("accepted", 0)})
+    print(json.dumps({"report": "learned extrapolation", "workload":
+                      "o=30 v=150 R_thc=720 R_cp=1080, stop at |dfit| < 1e-6", "precision": prec,
+                      "rows": rows}))
+    return 0
+
+
+def batched_report(args):
+    """64 uneven problems, 40 sweeps each, split precision: one batched call (one CUDA
+    graph per sweep for all problems, autotuned tiles) vs the same problems one by one."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import api
+    from thc_inputs import batched_shapes, make_problem
+    prec = args.precision or "bf16x3"
+    shapes = batched_shapes(64, seed=0)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    probs = [make_problem(o, v, Rt, R, seed=i) for i, (o, v, Rt, R) in enumerate(shapes)]
+    dev = [dict(Xo=t(p.Xo), Xv=t(p.Xv), Z=t(p.Z), A0=[t(a) for a in p.A]) for p in probs]
+
+    def fresh():
+        out = []
+        for d, p in zip(dev, probs):
+            out.append(dict(Xo=d["Xo"], Xv=d["Xv"], Z=d["Z"], A=[a.clone() for a in d["A0"]],
+                            lam=torch.ones(p.R, dtype=torch.float64, device="cuda")))
+        return out
+    sweeps = 40
+    flops = 0.0
+    for (o, v, Rt, R) in shapes:
+        n = o + v
+        flops += sweeps * (4 * Rt * Rt * R + 8 * n * Rt * R + 2 * n * R * R + 4 * R ** 3 / 3 + 4 * n * R * R)
+    api.thc_cpd_als_batched(fresh(), 2, 0.0, precision=prec, autotune=True)  # warm-up + tuning
+    torch.cuda.synchronize()
+    res = {}
+    for name in ("batched", "one_by_one"):
+        best = 1e30
+        for _ in range(2):
+            pr = fresh()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "batched":
+                outs = api.thc_cpd_als_batched(pr, sweeps, 0.0, precision=prec)
+            else:
+                outs = [api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], d["lam"], sweeps, 0.0,
+                                        precision=prec) for d in pr]
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        res[name] = {"seconds": best, "problem_sweeps_per_s": 64 * sweeps / best,
+                     "useful_tflops": flops / best / 1e12,
+                     "mean_fit": float(np.mean([o["fit"] for o in outs]))}
+    print(json.dumps({"report": "batched", "problems": 64, "sweeps": sweeps, "precision": prec,
+                      "shapes": {"o_min": min(s[0] for s in shapes), "o_max": max(s[0] for s in shapes),
+                                 "R_cp_max": max(s[3] for s in shapes)},
+                      "rows": res, "speedup": res["one_by_one"]["seconds"] / res["batched"]["seconds"]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.learned_report:
+        return learned_report(args)
+    if args.batched:
+        return batched_report(args)
 
     import numpy as np
     import torch
@@ -231,13 +345,8 @@ def main():
     launches = api.thc_cpd_launch_count() - l0
     if world > 1:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    value, ms = job_throughput(args.steps * W["sweeps"], sum(a.elapsed_time(b) for a, b in ev), dev)
     sweeps_total = world * args.steps * W["sweeps"]
-    value = sweeps_total / (ms / 1000.0)
     fit = out["fit"]
 
     # ---- end to end through the public API with host buffers ----
@@ -271,12 +380,7 @@ def main():
         e2e_step()
         ev2[k][1].record(stream)
     torch.cuda.synchronize()
-    ms2 = sum(a.elapsed_time(b) for a, b in ev2)
-    if world > 1:
-        tt = torch.tensor([ms2], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms2 = float(tt.item())
-    e2e_value = sweeps_total / (ms2 / 1000.0)
+    e2e_value, ms2 = job_throughput(args.steps * W["sweeps"], sum(a.elapsed_time(b) for a, b in ev2), dev)
 
     # ---- the plain FP64 GPU path on the same workload, same protocol ----
     compare = None
@@ -294,12 +398,7 @@ def main():
             o64 = api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64")
             ev3[k][1].record(stream)
         torch.cuda.synchronize()
-        ms3 = sum(a.elapsed_time(b) for a, b in ev3)
-        if world > 1:
-            tt = torch.tensor([ms3], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms3 = float(tt.item())
-        v64 = sweeps_total / (ms3 / 1000.0)
+        v64, ms3 = job_throughput(args.steps * W["sweeps"], sum(a.elapsed_time(b) for a, b in ev3), dev)
         compare = {"fp64": {"value": v64, "fit": o64["fit"], "ms_per_step": ms3 / args.steps},
                    precision: {"value": value, "fit": fit, "ms_per_step": ms / args.steps},
                    "speedup_vs_fp64": value / v64,

@@ -342,7 +342,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
             CK(cudaStreamSynchronize(c.st));
         }
     }
-    normalise_columns(c.st, n, R, A[k], lam);
+    normalise_columns(c.st, n, R, A[k], lam, c.LinvD);  // panel buffer is free after the solve
     gram_fp64(c, k, A[k]);
     if (c.prec == THC_CPD_FP64)
         project_fp64(c, k, A[k]);
@@ -561,7 +561,7 @@ void build_trial(Ctx& c, LearnWs& L, double* const A[4], const double* lam, doub
     const int R = c.s.R;
     for (int k = 0; k < 4; ++k) {
         trial_point(c.st, c.s.n[k], R, A[k], c.Asnap[k], lam, c.lamsnap, k == 3, alpha, L.T[k]);
-        normalise_columns(c.st, c.s.n[k], R, L.T[k], L.lamk[k]);
+        normalise_columns(c.st, c.s.n[k], R, L.T[k], L.lamk[k], L.lamT);
     }
     const double* lk[4] = {L.lamk[0], L.lamk[1], L.lamk[2], L.lamk[3]};
     lam_product(c.st, R, lk, L.lamT);

@@ -28,8 +28,8 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode);
 
-// lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column).
-void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam);
+// lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column); scratch >= R doubles.
+void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch);
 
 // Loss in factor form after a sweep: inner = sum lam_r Y[Q,r] W3[Q,r] W4[Q,r],
 // cpdn2 = lam^T (G1 o G2 o G3 o G4) lam; loss, fit, convergence into sc.

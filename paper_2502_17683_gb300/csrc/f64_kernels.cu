@@ -130,12 +130,25 @@ GemmPlan plan_gemm(int M, int N, int K, bool symm) {
     p.BM = (!symm && M <= 32) ? 32 : 64;
     const int tm = cdiv(M, p.BM), tn = cdiv(N, p.BN);
     p.tiles = symm ? (tm * (tm + 1)) / 2 : tm * tn;
-    int splits = 1;
-    if (p.tiles < kTargetCTAs) splits = cdiv(kTargetCTAs, p.tiles);
-    splits = std::max(1, std::min(splits, cdiv(K, 64)));
-    int kchunk = ((cdiv(K, splits) + 15) / 16) * 16;
-    p.kchunk = kchunk;
-    p.splits = cdiv(K, kchunk);
+    // split K so that the busiest SM finishes first: the FP64 pipe of an SM is shared by
+    // its CTAs, so the cost is (CTAs per SM, rounded up) x (K per CTA) plus a small charge
+    // per split for the partials' write and fixed-order reduction
+    int best_s = 1, best_kc = ((K + 15) / 16) * 16;
+    double best = 1e300;
+    for (int s = 1; s <= 32; ++s) {
+        const int kc = ((cdiv(K, s) + 15) / 16) * 16;
+        const int ss = cdiv(K, kc);
+        if (ss != s) continue;
+        const double waves = (double)cdiv((long)p.tiles * ss, kNumSM);
+        const double cost = waves * kc + (ss > 1 ? 0.5 * ss : 0.0);
+        if (cost < best) {
+            best = cost;
+            best_s = ss;
+            best_kc = kc;
+        }
+    }
+    p.kchunk = best_kc;
+    p.splits = best_s;
     return p;
 }
 
@@ -282,27 +295,26 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 constexpr int NB = 32;          // block size of the factorisation
 constexpr int UT = 16;          // trailing-update tile (one output per thread)
 
-// Reciprocal 1/d of a positive normal double by Newton-Raphson, y <- y + y (1 - d y)
-// (quadratic convergence), from a seed built with integer operations: the FP32
-// reciprocal of the leading 20 mantissa bits, rescaled by the exponent. Two steps take
-// the ~20-bit seed past FP64 precision. Only d > 0 reaches here (the pivot test runs
-// first); the seed is exact in exponent for 2^-1000 < d < 2^1000.
+// Reciprocal 1/d of a positive normal double from a seed built with integer operations
+// (the FP32 reciprocal of the leading 23 mantissa bits, rescaled by the exponent, ~2^-22
+// accurate), refined by one third-order Newton step y <- y (1 + e + e^2), e = 1 - d y
+// (cubic convergence: 2^-22 -> below 2^-60). Three dependent FP64 operations. Only
+// d > 0 with 2^-998 < d < 2^998 reaches here (the pivot test runs first).
 __device__ __forceinline__ double recip_nr(double d) {
     const long long bits = __double_as_longlong(d);
-    const int e = (int)((bits >> 52) & 0x7FF);         // biased exponent of d
-    const unsigned mhi = (unsigned)((bits >> 32) & 0xFFFFF);  // top 20 mantissa bits
-    const float m = __uint_as_float(0x3F800000u | (mhi << 3));  // in [1, 2)
-    const float r = __frcp_rn(m);                       // in (0.5, 1]
+    const int e = (int)((bits >> 52) & 0x7FF);                        // biased exponent of d
+    const unsigned mhi = (unsigned)((bits >> 29) & 0x7FFFFF);         // top 23 mantissa bits
+    const float m = __uint_as_float(0x3F800000u | mhi);              // in [1, 2)
+    const float r = __frcp_rn(m);                                     // in (0.5, 1]
     const unsigned rb = __float_as_uint(r);
-    const int er = (int)((rb >> 23) & 0xFF) - 127;      // -1 or 0
+    const int er = (int)((rb >> 23) & 0xFF) - 127;                    // -1 or 0
     // 1/d = r * 2^-(e - 1023)
     const long long yb = ((long long)(er - (e - 1023) + 1023) << 52) |
                          ((long long)(rb & 0x7FFFFF) << 29);
-    double y = __longlong_as_double(yb);
-    double t = fma(-d, y, 1.0);
-    y = fma(y, t, y);
-    t = fma(-d, y, 1.0);
-    return fma(y, t, y);
+    const double y = __longlong_as_double(yb);
+    const double t = fma(-d, y, 1.0);
+    const double u = fma(t, t, t);
+    return fma(y, u, y);
 }
 
 // d > tau with d, tau >= 0 finite-or-not, decided on the integer pipe: non-negative
@@ -330,36 +342,54 @@ __device__ __forceinline__ void pair_of(int e, int* r, int* s) {
 // LDL^T of the jb x jb diagonal block held in Ds (lower part); on return Ls holds the
 // unit-lower L_jj (strictly lower part), Ds[c][c] the pivots d_c and dinv_s[c] = 1/d_c.
 // Returns (in thread 0) whether a pivot failed the test d > tau.
+// One-column look-ahead: while warps 1..3 apply column c to the rest of the block, thread
+// 0 updates the next pivot (d_{c+1} -= x^2 / d_c, x = D[c+1][c]) and inverts it, so the
+// sequential chain per column is four FP64 operations and one barrier.
 __device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* dinv_s,
                          const unsigned short* pairs, int jb, double tau) {
     __shared__ int bad;
     const int tid = threadIdx.x;
-    if (tid == 0) bad = 0;
-    for (int c = 0; c < jb; ++c) {
-        if (tid == 0) {
-            double d = Ds[c][c];
-            if (!pivot_ok(d, tau)) {
-                bad = 1;
-                d = 1.0;  // keep going; the caller replays this mode with the pseudo-inverse
-                Ds[c][c] = d;
-            }
-            dinv_s[c] = recip_nr(d);
+    if (tid == 0) {
+        bad = 0;
+        double d = Ds[0][0];
+        if (!pivot_ok(d, tau)) {
+            bad = 1;
+            d = 1.0;  // keep going; the caller replays this mode with the pseudo-inverse
+            Ds[0][0] = d;
         }
-        __syncthreads();
-        const double inv = dinv_s[c];
-        // D[r][s] -= (D[r][c] / d_c) D[s][c] for c < s <= r < jb, pairs spread evenly
-        const int hi = NB - 1 - c;                  // s in (c, 31]
-        const int npair = hi * (hi + 1) / 2;
-        for (int e = tid; e < npair; e += blockDim.x) {
-            const int rs = pairs[e];
-            const int r = rs >> 8, ss = rs & 0xFF;
-            if (r >= jb) continue;
-            const double l = Ds[r][c] * inv;
-            if (ss == c + 1) Ls[r][c] = l;
-            Ds[r][ss] = fma(-l, Ds[ss][c], Ds[r][ss]);
-        }
-        __syncthreads();
+        dinv_s[0] = recip_nr(d);
     }
+    for (int c = 0; c < jb; ++c) {
+        __syncthreads();  // dinv_s[c] and column c are final
+        const double inv = dinv_s[c];
+        if (tid == 0) {
+            if (c + 1 < jb) {
+                const double x = Ds[c + 1][c];
+                const double xx = x * x;
+                Ls[c + 1][c] = x * inv;
+                double d1 = fma(-xx, inv, Ds[c + 1][c + 1]);
+                if (!pivot_ok(d1, tau)) {
+                    bad = 1;
+                    d1 = 1.0;
+                }
+                Ds[c + 1][c + 1] = d1;
+                dinv_s[c + 1] = recip_nr(d1);
+            }
+        } else if (tid >= 32) {
+            // D[r][s] -= (D[r][c] / d_c) D[s][c] for c < s <= r < jb except (c+1, c+1)
+            const int hi = NB - 1 - c;
+            const int npair = hi * (hi + 1) / 2;
+            for (int e = tid - 32; e < npair; e += blockDim.x - 32) {
+                const int rs = pairs[e];
+                const int r = rs >> 8, ss = rs & 0xFF;
+                if (r >= jb || (r == c + 1 && ss == c + 1)) continue;
+                const double l = Ds[r][c] * inv;
+                if (ss == c + 1) Ls[r][c] = l;
+                Ds[r][ss] = fma(-l, Ds[ss][c], Ds[r][ss]);
+            }
+        }
+    }
+    __syncthreads();
     return bad;
 }
 
@@ -481,9 +511,18 @@ k_bsolve_unit(double* __restrict__ Yf, double* __restrict__ A, int R,
     __syncthreads();
     const int q = blockIdx.x * blockDim.x + tid;
     if (q < c0) {
-        double s = 0.0;
-        for (int c = 0; c < jb; ++c) s = fma(a_s[c], H[(size_t)(c0 + c) * R + q], s);
-        Yf[(size_t)r * R + q] -= s;
+        // all 32 L2 loads in flight before the dependent FMAs (jb == 32 except the last
+        // block, and that one has c0 = 0 here only when R <= 32)
+        double hv[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) hv[c] = (c < jb) ? H[(size_t)(c0 + c) * R + q] : 0.0;
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int c = 0; c < NB; c += 2) {
+            s0 = fma(a_s[c], hv[c], s0);
+            s1 = fma(a_s[c + 1], hv[c + 1], s1);
+        }
+        Yf[(size_t)r * R + q] -= (s0 + s1);
     }
 }
 
@@ -525,24 +564,44 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
 // ------------------------------------------------------------------------------------
 // column normalisation, loss, norms
 // ------------------------------------------------------------------------------------
-__global__ void k_normalise(int n, int R, double* __restrict__ A, double* __restrict__ lam) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
+// lam_r = ||A[:, r]||_2 (32 columns x 8 row slices per block, fixed-order reduction) and
+// the reciprocal, then A[:, r] *= 1 / lam_r: one sqrt and one divide per column instead of
+// a divide per element (a divide costs ~430 clocks on GB300's FP64 pipe).
+__global__ void __launch_bounds__(256)
+k_colnorm(int n, int R, const double* __restrict__ A, double* __restrict__ lam,
+          double* __restrict__ inv) {
+    __shared__ double sh[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + tx;
     double s = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double x = A[(size_t)i * R + r];
-        s = fma(x, x, s);
+    if (r < R)
+        for (int i = ty; i < n; i += 8) {
+            const double x = A[(size_t)i * R + r];
+            s = fma(x, x, s);
+        }
+    sh[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += sh[k][tx];
+        const double l = sqrt(t);
+        lam[r] = l;
+        inv[r] = l > 0.0 ? 1.0 / l : 1.0;  // zero columns are left as they are
     }
-    const double l = sqrt(s);
-    lam[r] = l;
-    if (l > 0.0)
-        for (int i = 0; i < n; ++i) A[(size_t)i * R + r] /= l;
 }
 
-void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam) {
+__global__ void k_colscale(long total, int R, double* __restrict__ A, const double* __restrict__ inv) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+         i += (long)gridDim.x * blockDim.x)
+        A[i] *= inv[i % R];
+}
+
+void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch) {
     ProfScope prof(st, KC_AUX, 3.0 * n * R, 24.0 * n * R);
-    count_launch();
-    k_normalise<<<cdiv(R, 128), 128, 0, st>>>(n, R, A, lam);
+    count_launch(2);
+    k_colnorm<<<cdiv(R, 32), 256, 0, st>>>(n, R, A, lam, scratch);
+    const long total = (long)n * R;
+    k_colscale<<<(int)std::min<long>(cdiv(total, 256), 4L * kNumSM), 256, 0, st>>>(total, R, A, scratch);
 }
 
 constexpr int RED_BLOCKS = 2 * kNumSM;

@@ -325,30 +325,62 @@ __device__ __forceinline__ bool pivot_ok(double d, double tau) {
     return finite_pos && bd > bt && ((bd >> 52) & 0x7FF) > 24 && ((bd >> 52) & 0x7FF) < 2022;
 }
 
-// (r, s) pairs of the strictly lower triangle ordered by s descending, so that the
-// pairs with s > c form the prefix of length (31 - c) (32 - c) / 2.
-__device__ __forceinline__ void pair_of(int e, int* r, int* s) {
-    // s from 31 down: group for s holds r = s..31 -> (32 - s) entries
-    int cnt = 0, ss = NB - 1;
-    for (;; --ss) {
-        const int g = NB - ss;
-        if (e < cnt + g) break;
-        cnt += g;
-    }
-    *s = ss;
-    *r = ss + (e - cnt);
+// Pairs (r, s), c < s <= r < 32, ordered by s descending: the group of s = 31 - k holds the
+// k + 1 rows r = s..31 and starts at k (k + 1) / 2, so the pairs with s > c form the prefix
+// of length (31 - c)(32 - c) / 2. Closed-form inverse of the group start (FP32 sqrt is
+// exact for these small integers; the two checks correct any rounding of the estimate).
+__device__ __forceinline__ unsigned short pair_code(int e) {
+    int k = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    if ((k + 1) * (k + 2) / 2 <= e) ++k;
+    if (k * (k + 1) / 2 > e) --k;
+    const int s = NB - 1 - k;
+    const int r = s + (e - k * (k + 1) / 2);
+    return (unsigned short)((r << 8) | s);
 }
 
-// LDL^T of the jb x jb diagonal block held in Ds (lower part); on return Ls holds the
-// unit-lower L_jj (strictly lower part), Ds[c][c] the pivots d_c and dinv_s[c] = 1/d_c.
-// Returns (in thread 0) whether a pivot failed the test d > tau.
-// One-column look-ahead: while warps 1..3 apply column c to the rest of the block, thread
-// 0 updates the next pivot (d_{c+1} -= x^2 / d_c, x = D[c+1][c]) and inverts it, so the
-// sequential chain per column is four FP64 operations and one barrier.
-__device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* dinv_s,
-                         const unsigned short* pairs, int jb, double tau) {
+constexpr int PANEL_THREADS = 256;  // warps 0-3 factorise, warps 4-7 substitute panel rows
+constexpr int SUB_WARPS = 4;
+constexpr int MAX_ROWS_PER_WARP = 8;
+
+// One block step of the LDL^T: CTA 0 factorises the diagonal block and stores L_jj, D, D^-1;
+// every other CTA factorises it too (no inter-CTA wait) and substitutes its panel rows
+// X L_jj^T = B, then L = X D^-1 (X kept in P for the trailing update). The substitution
+// warps run one column behind the factorisation inside the same loop, so the rows are done
+// when the block is. Column loop: thread 0 carries the pivot chain (next pivot update and
+// its reciprocal, one column ahead), warps 1-3 apply the current column to the rest of the
+// block over a packed pair list, one barrier per column.
+__global__ void __launch_bounds__(PANEL_THREADS)
+k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__ dinv, int R,
+            int nrows, int j0, int jb, int rows_per_cta, DevScalars* sc, int mode) {
+    __shared__ double Ds[NB][NB + 1];
+    __shared__ double Ls[NB][NB + 1];
+    __shared__ double dinv_s[NB];
+    __shared__ unsigned short pairs[NB * (NB + 1) / 2];
     __shared__ int bad;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const double tau = (double)R * DBL_EPSILON * sc->maxdiag;
+    const int j1 = j0 + jb;
+    // panel rows of this CTA: loads issued before the factorisation
+    const bool subst = blockIdx.x > 0 && w >= 4;
+    const int sw = w - 4;
+    const int nmine = subst ? max(0, min(MAX_ROWS_PER_WARP,
+                                         (rows_per_cta - sw + SUB_WARPS - 1) / SUB_WARPS))
+                            : 0;
+    double b[MAX_ROWS_PER_WARP];
+    int rowi[MAX_ROWS_PER_WARP];
+#pragma unroll
+    for (int q = 0; q < MAX_ROWS_PER_WARP; ++q) {
+        rowi[q] = j1 + (blockIdx.x - 1) * rows_per_cta + sw + q * SUB_WARPS;
+        b[q] = 0.0;
+        if (q < nmine && rowi[q] < nrows && lane < jb) b[q] = H[(size_t)rowi[q] * R + j0 + lane];
+    }
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        Ds[r][c] = (r < jb && c <= r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
+        Ls[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+    for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) pairs[e] = pair_code(e);
+    __syncthreads();
     if (tid == 0) {
         bad = 0;
         double d = Ds[0][0];
@@ -360,13 +392,12 @@ __device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* din
         dinv_s[0] = recip_nr(d);
     }
     for (int c = 0; c < jb; ++c) {
-        __syncthreads();  // dinv_s[c] and column c are final
+        __syncthreads();  // dinv_s[c], column c of D and column c-1 of L are final
         const double inv = dinv_s[c];
         if (tid == 0) {
             if (c + 1 < jb) {
                 const double x = Ds[c + 1][c];
                 const double xx = x * x;
-                Ls[c + 1][c] = x * inv;
                 double d1 = fma(-xx, inv, Ds[c + 1][c + 1]);
                 if (!pivot_ok(d1, tau)) {
                     bad = 1;
@@ -374,12 +405,13 @@ __device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* din
                 }
                 Ds[c + 1][c + 1] = d1;
                 dinv_s[c + 1] = recip_nr(d1);
+                Ls[c + 1][c] = x * inv;
             }
-        } else if (tid >= 32) {
+        } else if (tid >= 32 && tid < 128) {
             // D[r][s] -= (D[r][c] / d_c) D[s][c] for c < s <= r < jb except (c+1, c+1)
             const int hi = NB - 1 - c;
             const int npair = hi * (hi + 1) / 2;
-            for (int e = tid - 32; e < npair; e += blockDim.x - 32) {
+            for (int e = tid - 32; e < npair; e += 96) {
                 const int rs = pairs[e];
                 const int r = rs >> 8, ss = rs & 0xFF;
                 if (r >= jb || (r == c + 1 && ss == c + 1)) continue;
@@ -387,33 +419,19 @@ __device__ int ldl_block(double (*Ds)[NB + 1], double (*Ls)[NB + 1], double* din
                 if (ss == c + 1) Ls[r][c] = l;
                 Ds[r][ss] = fma(-l, Ds[ss][c], Ds[r][ss]);
             }
+        } else if (subst && c >= 1) {
+            // substitution step c-1 (column c-1 of L is final)
+            const int cc = c - 1;
+            const double lc = Ls[lane][cc];
+#pragma unroll
+            for (int q = 0; q < MAX_ROWS_PER_WARP; ++q) {
+                if (q >= nmine) break;
+                const double xc = __shfl_sync(0xffffffffu, b[q], cc);
+                if (lane > cc) b[q] = fma(-xc, lc, b[q]);
+            }
         }
     }
     __syncthreads();
-    return bad;
-}
-
-__global__ void __launch_bounds__(128)
-k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__ dinv, int R,
-            int nrows, int j0, int jb, int rows_per_cta, DevScalars* sc, int mode) {
-    __shared__ double Ds[NB][NB + 1];
-    __shared__ double Ls[NB][NB + 1];
-    __shared__ double dinv_s[NB];
-    __shared__ unsigned short pairs[NB * (NB + 1) / 2];
-    const int tid = threadIdx.x;
-    const double tau = (double)R * DBL_EPSILON * sc->maxdiag;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int r = e / NB, c = e % NB;
-        Ds[r][c] = (r < jb && c <= r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
-        Ls[r][c] = (r == c) ? 1.0 : 0.0;
-    }
-    for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) {
-        int r, s2;
-        pair_of(e, &r, &s2);
-        pairs[e] = (unsigned short)((r << 8) | s2);
-    }
-    __syncthreads();
-    const int bad = ldl_block(Ds, Ls, dinv_s, pairs, jb, tau);
     if (blockIdx.x == 0) {
         if (tid == 0 && bad) atomicOr(&sc->fail_mask, 1 << mode);
         for (int e = tid; e < jb * jb; e += blockDim.x) {
@@ -424,21 +442,15 @@ k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__
         if (tid < jb) dinv[j0 + tid] = dinv_s[tid];
         return;
     }
-    // rows below the block: unit-triangular substitution X L_jj^T = B (one row per warp),
-    // then L = X D^{-1}; X goes to P for the trailing update (rows of H only)
-    const int lane = tid & 31, w = tid >> 5;
-    const int j1 = j0 + jb;
-    for (int rr = w; rr < rows_per_cta; rr += blockDim.x >> 5) {
-        const int i = j1 + (blockIdx.x - 1) * rows_per_cta + rr;
-        if (i >= nrows) break;
-        double b = (lane < jb) ? H[(size_t)i * R + j0 + lane] : 0.0;
-        for (int c = 0; c < jb; ++c) {
-            const double xc = __shfl_sync(0xffffffffu, b, c);
-            if (lane > c) b = fma(-xc, Ls[lane][c], b);
-        }
-        if (lane < jb) {
-            H[(size_t)i * R + j0 + lane] = b * dinv_s[lane];
-            if (i < R) P[(size_t)i * NB + lane] = b;
+    if (!subst) return;
+    // the last substitution step (c = jb - 1) changes nothing; scale and store
+#pragma unroll
+    for (int q = 0; q < MAX_ROWS_PER_WARP; ++q) {
+        if (q >= nmine) break;
+        const int i = rowi[q];
+        if (i < nrows && lane < jb) {
+            H[(size_t)i * R + j0 + lane] = b[q] * dinv_s[lane];
+            if (i < R) P[(size_t)i * NB + lane] = b[q];
         }
     }
 }
@@ -536,9 +548,11 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
             const int below = nrows - (j0 + jb);
             // every panel CTA repeats the diagonal-block factorisation: keep the grid
             // within one CTA per SM so that the repeats do not share an FP64 pipe
-            const int rpc = std::max(4, ((cdiv(std::max(below, 1), kNumSM - 4) + 3) / 4) * 4);
-            k_ldl_panel<<<1 + cdiv(below, rpc), 128, 0, st>>>(Haug, P, dinv, R, nrows, j0, jb,
-                                                              rpc, sc, mode);
+            const int rpc = std::min(SUB_WARPS * MAX_ROWS_PER_WARP,
+                                     std::max(SUB_WARPS, ((cdiv(std::max(below, 1), kNumSM - 4) +
+                                                           SUB_WARPS - 1) / SUB_WARPS) * SUB_WARPS));
+            k_ldl_panel<<<1 + cdiv(below, rpc), PANEL_THREADS, 0, st>>>(Haug, P, dinv, R, nrows,
+                                                                        j0, jb, rpc, sc, mode);
             count_launch();
             const int j1 = j0 + jb;
             if (j1 < R) {

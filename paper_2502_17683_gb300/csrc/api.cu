@@ -117,6 +117,7 @@ struct Ctx {
     double* Y = nullptr;
     double* Haug = nullptr;
     double* LinvD = nullptr;
+    int* counters = nullptr;
     double* part = nullptr;
     size_t part_cap = 0;
     double* red = nullptr;
@@ -187,6 +188,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     bytes += Arena::need<double>(RtR);                     // Y
     bytes += Arena::need<double>((size_t)(R + nmax) * R);  // Haug
     bytes += Arena::need<double>((size_t)R * 32 + R);  // panel X and D^{-1}
+    bytes += Arena::need<int>(cdiv(R, 32));               // arrival counters of the LDL^T
     bytes += Arena::need<double>(pc);
     bytes += Arena::need<double>(loss_red_need() + 2 * kNumSM * 2);
     bytes += Arena::need<double>(R);
@@ -208,6 +210,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     c.Y = ar.take<double>(RtR);
     c.Haug = ar.take<double>((size_t)(R + nmax) * R);
     c.LinvD = ar.take<double>((size_t)R * 32 + R);
+    c.counters = ar.take<int>(cdiv(R, 32));
     c.part = ar.take<double>(pc);
     c.red = ar.take<double>(loss_red_need() + 2 * kNumSM * 2);
     c.ones = ar.take<double>(R);
@@ -327,7 +330,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
         CK(cudaMemcpyAsync(Mrows, c.Msave, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, c.st));
         CK(cudaMemcpyAsync(c.Haug, c.Hsave, sizeof(double) * R * R, cudaMemcpyDeviceToDevice, c.st));
     }
-    chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * 32, c.sc, k);
+    chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * 32, c.sc, k, c.counters);
     if (safe) {
         DevScalars* h = host_scalars();
         if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");

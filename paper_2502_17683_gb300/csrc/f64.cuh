@@ -25,8 +25,9 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   P: R x 32 panel workspace, dinv: R doubles.
 //   A pivot <= R * eps * sc->maxdiag sets bit `mode` of sc->fail_mask (the result is then
 //   garbage and the caller replays the mode with the pseudo-inverse).
+//   counters: cdiv(R, 32) ints (arrival counters of the update kernels, cleared inside).
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode);
+                DevScalars* sc, int mode, int* counters);
 
 // lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column); scratch >= R doubles.
 void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch);

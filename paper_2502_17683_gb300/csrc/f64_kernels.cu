@@ -305,7 +305,8 @@ __device__ __forceinline__ double recip_nr(double d) {
     const int e = (int)((bits >> 52) & 0x7FF);                        // biased exponent of d
     const unsigned mhi = (unsigned)((bits >> 29) & 0x7FFFFF);         // top 23 mantissa bits
     const float m = __uint_as_float(0x3F800000u | mhi);              // in [1, 2)
-    const float r = __frcp_rn(m);                                     // in (0.5, 1]
+    float r;                                                          // in (0.5, 1]
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));            // ~2^-23 seed
     const unsigned rb = __float_as_uint(r);
     const int er = (int)((rb >> 23) & 0xFF) - 127;                    // -1 or 0
     // 1/d = r * 2^-(e - 1023)
@@ -338,129 +339,128 @@ __device__ __forceinline__ unsigned short pair_code(int e) {
     return (unsigned short)((r << 8) | s);
 }
 
-constexpr int PANEL_THREADS = 256;  // warps 0-3 factorise, warps 4-7 substitute panel rows
-constexpr int SUB_WARPS = 4;
-constexpr int MAX_ROWS_PER_WARP = 8;
+struct BlockSmem {
+    double Ds[NB][NB + 1];
+    double Ls[NB][NB + 1];
+    double dinv[NB];
+    unsigned short pairs[NB * (NB + 1) / 2];
+    int bad;
+};
 
-// One block step of the LDL^T: CTA 0 factorises the diagonal block and stores L_jj, D, D^-1;
-// every other CTA factorises it too (no inter-CTA wait) and substitutes its panel rows
-// X L_jj^T = B, then L = X D^-1 (X kept in P for the trailing update). The substitution
-// warps run one column behind the factorisation inside the same loop, so the rows are done
-// when the block is. Column loop: thread 0 carries the pivot chain (next pivot update and
-// its reciprocal, one column ahead), warps 1-3 apply the current column to the rest of the
-// block over a packed pair list, one barrier per column.
-__global__ void __launch_bounds__(PANEL_THREADS)
-k_ldl_panel(double* __restrict__ H, double* __restrict__ P, double* __restrict__ dinv, int R,
-            int nrows, int j0, int jb, int rows_per_cta, DevScalars* sc, int mode) {
-    __shared__ double Ds[NB][NB + 1];
-    __shared__ double Ls[NB][NB + 1];
-    __shared__ double dinv_s[NB];
-    __shared__ unsigned short pairs[NB * (NB + 1) / 2];
-    __shared__ int bad;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+// LDL^T of the jb x jb diagonal block at (j0, j0) of H, in place: strictly lower L, D on the
+// diagonal, D^-1 in dinv[j0..]; a pivot <= tau sets bit `mode` of sc->fail_mask. Called by
+// every thread of the CTA (barriers inside); threads 0..127 compute: thread 0 carries the
+// pivot chain one column ahead (pivot update and its reciprocal), warps 1-3 apply the
+// current column to the rest of the block over a packed pair list, one barrier per column.
+// Loads go through L2 (__ldcg): other CTAs of the same kernel may have written the block.
+__device__ void factor_block(double* __restrict__ H, int R, int j0, int jb,
+                             double* __restrict__ dinv, DevScalars* sc, int mode, BlockSmem& S) {
+    const int tid = threadIdx.x;
     const double tau = (double)R * DBL_EPSILON * sc->maxdiag;
-    const int j1 = j0 + jb;
-    // panel rows of this CTA: loads issued before the factorisation
-    const bool subst = blockIdx.x > 0 && w >= 4;
-    const int sw = w - 4;
-    const int nmine = subst ? max(0, min(MAX_ROWS_PER_WARP,
-                                         (rows_per_cta - sw + SUB_WARPS - 1) / SUB_WARPS))
-                            : 0;
-    double b[MAX_ROWS_PER_WARP];
-    int rowi[MAX_ROWS_PER_WARP];
-#pragma unroll
-    for (int q = 0; q < MAX_ROWS_PER_WARP; ++q) {
-        rowi[q] = j1 + (blockIdx.x - 1) * rows_per_cta + sw + q * SUB_WARPS;
-        b[q] = 0.0;
-        if (q < nmine && rowi[q] < nrows && lane < jb) b[q] = H[(size_t)rowi[q] * R + j0 + lane];
-    }
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
-        Ds[r][c] = (r < jb && c <= r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
-        Ls[r][c] = (r == c) ? 1.0 : 0.0;
+        S.Ds[r][c] = (r < jb && c <= r) ? __ldcg(H + (size_t)(j0 + r) * R + j0 + c) : 0.0;
+        S.Ls[r][c] = (r == c) ? 1.0 : 0.0;
     }
-    for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) pairs[e] = pair_code(e);
+    for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code(e);
     __syncthreads();
     if (tid == 0) {
-        bad = 0;
-        double d = Ds[0][0];
+        S.bad = 0;
+        double d = S.Ds[0][0];
         if (!pivot_ok(d, tau)) {
-            bad = 1;
+            S.bad = 1;
             d = 1.0;  // keep going; the caller replays this mode with the pseudo-inverse
-            Ds[0][0] = d;
+            S.Ds[0][0] = d;
         }
-        dinv_s[0] = recip_nr(d);
+        S.dinv[0] = recip_nr(d);
     }
     for (int c = 0; c < jb; ++c) {
-        __syncthreads();  // dinv_s[c], column c of D and column c-1 of L are final
-        const double inv = dinv_s[c];
+        __syncthreads();  // dinv[c] and column c of D are final
+        const double inv = S.dinv[c];
         if (tid == 0) {
             if (c + 1 < jb) {
-                const double x = Ds[c + 1][c];
-                const double xx = x * x;
-                double d1 = fma(-xx, inv, Ds[c + 1][c + 1]);
+                const double x = S.Ds[c + 1][c];
+                const double l = x * inv;
+                double d1 = fma(-l, x, S.Ds[c + 1][c + 1]);
+                S.Ls[c + 1][c] = l;
                 if (!pivot_ok(d1, tau)) {
-                    bad = 1;
+                    S.bad = 1;
                     d1 = 1.0;
                 }
-                Ds[c + 1][c + 1] = d1;
-                dinv_s[c + 1] = recip_nr(d1);
-                Ls[c + 1][c] = x * inv;
+                S.Ds[c + 1][c + 1] = d1;
+                S.dinv[c + 1] = recip_nr(d1);
             }
         } else if (tid >= 32 && tid < 128) {
             // D[r][s] -= (D[r][c] / d_c) D[s][c] for c < s <= r < jb except (c+1, c+1)
             const int hi = NB - 1 - c;
             const int npair = hi * (hi + 1) / 2;
             for (int e = tid - 32; e < npair; e += 96) {
-                const int rs = pairs[e];
+                const int rs = S.pairs[e];
                 const int r = rs >> 8, ss = rs & 0xFF;
                 if (r >= jb || (r == c + 1 && ss == c + 1)) continue;
-                const double l = Ds[r][c] * inv;
-                if (ss == c + 1) Ls[r][c] = l;
-                Ds[r][ss] = fma(-l, Ds[ss][c], Ds[r][ss]);
-            }
-        } else if (subst && c >= 1) {
-            // substitution step c-1 (column c-1 of L is final)
-            const int cc = c - 1;
-            const double lc = Ls[lane][cc];
-#pragma unroll
-            for (int q = 0; q < MAX_ROWS_PER_WARP; ++q) {
-                if (q >= nmine) break;
-                const double xc = __shfl_sync(0xffffffffu, b[q], cc);
-                if (lane > cc) b[q] = fma(-xc, lc, b[q]);
+                const double l = S.Ds[r][c] * inv;
+                if (ss == c + 1) S.Ls[r][c] = l;
+                S.Ds[r][ss] = fma(-l, S.Ds[ss][c], S.Ds[r][ss]);
             }
         }
     }
     __syncthreads();
-    if (blockIdx.x == 0) {
-        if (tid == 0 && bad) atomicOr(&sc->fail_mask, 1 << mode);
-        for (int e = tid; e < jb * jb; e += blockDim.x) {
-            const int r = e / jb, c = e % jb;
-            if (c < r) H[(size_t)(j0 + r) * R + j0 + c] = Ls[r][c];
-            else if (c == r) H[(size_t)(j0 + r) * R + j0 + c] = Ds[r][r];
-        }
-        if (tid < jb) dinv[j0 + tid] = dinv_s[tid];
-        return;
+    if (tid == 0 && S.bad) atomicOr(&sc->fail_mask, 1 << mode);
+    for (int e = tid; e < jb * jb; e += blockDim.x) {
+        const int r = e / jb, c = e % jb;
+        if (c < r) H[(size_t)(j0 + r) * R + j0 + c] = S.Ls[r][c];
+        else if (c == r) H[(size_t)(j0 + r) * R + j0 + c] = S.Ds[r][r];
     }
-    if (!subst) return;
-    // the last substitution step (c = jb - 1) changes nothing; scale and store
-#pragma unroll
-    for (int q = 0; q < MAX_ROWS_PER_WARP; ++q) {
-        if (q >= nmine) break;
-        const int i = rowi[q];
-        if (i < nrows && lane < jb) {
-            H[(size_t)i * R + j0 + lane] = b[q] * dinv_s[lane];
-            if (i < R) P[(size_t)i * NB + lane] = b[q];
-        }
+    if (tid < jb) dinv[j0 + tid] = S.dinv[tid];
+}
+
+// First diagonal block; also clears the per-step arrival counters of the update kernels.
+__global__ void __launch_bounds__(128)
+k_ldl_diag(double* __restrict__ H, double* __restrict__ dinv, int R, int jb, DevScalars* sc,
+           int mode, int* counters, int nsteps) {
+    __shared__ BlockSmem S;
+    for (int i = threadIdx.x; i < nsteps; i += blockDim.x) counters[i] = 0;
+    factor_block(H, R, 0, jb, dinv, sc, mode, S);
+}
+
+// Panel rows below block j (rows of H and the appended rows), one per warp: unit-triangular
+// substitution X L_jj^T = B with the column values passed by shuffles, then L = X D^-1;
+// X goes to P for the trailing update (rows of H only).
+__global__ void __launch_bounds__(128)
+k_ldl_subst(double* __restrict__ H, double* __restrict__ P, const double* __restrict__ dinv,
+            int R, int nrows, int j0, int jb) {
+    __shared__ double Lj[NB][NB + 1];
+    __shared__ double di[NB];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int i = j0 + jb + blockIdx.x * 4 + w;
+    double b = (i < nrows && lane < jb) ? H[(size_t)i * R + j0 + lane] : 0.0;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        Lj[r][c] = (r < jb && c < r) ? H[(size_t)(j0 + r) * R + j0 + c] : 0.0;
+    }
+    if (tid < NB) di[tid] = tid < jb ? dinv[j0 + tid] : 0.0;
+    __syncthreads();
+    if (i >= nrows) return;
+    for (int c = 0; c + 1 < jb; ++c) {
+        const double xc = __shfl_sync(0xffffffffu, b, c);
+        if (lane > c) b = fma(-xc, Lj[lane][c], b);
+    }
+    if (lane < jb) {
+        H[(size_t)i * R + j0 + lane] = b * di[lane];
+        if (i < R) P[(size_t)i * NB + lane] = b;
     }
 }
 
 // Trailing update H[i][c] -= sum_s L[i][j0+s] X[c][s] for i >= j1 (rows of H and of the
-// appended M block), j1 <= c < R, lower triangle only for rows of H. One output per
-// thread on 16 x 16 tiles, so that the late (small) steps still spread over the SMs.
+// appended M block), j1 <= c < R, lower triangle only for rows of H. One output per thread
+// on 16 x 16 tiles, so that the late (small) steps still spread over the SMs. The tiles
+// that cover the next diagonal block count their arrivals (fence + atomic); the last one to
+// arrive factorises that block while the rest of the update is still running, so the
+// factorisation leaves the critical path of the step. No CTA ever waits for another.
 __global__ void __launch_bounds__(256)
-k_ldl_update(double* __restrict__ H, const double* __restrict__ P, int R, int nrows, int j0,
-             int jb, int nHtiles) {
+k_ldl_update(double* __restrict__ H, const double* __restrict__ P, double* __restrict__ dinv,
+             int R, int nrows, int j0, int jb, int nHtiles, DevScalars* sc, int mode,
+             int* counter) {
     const int j1 = j0 + jb;
     int r0, rend;
     if ((int)blockIdx.y < nHtiles) {
@@ -485,14 +485,28 @@ k_ldl_update(double* __restrict__ H, const double* __restrict__ P, int R, int nr
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;
     const int row = r0 + ty, col = c0 + tx;
-    if (row >= rend || col >= R || (hrows && col > row)) return;
-    double a0 = 0.0, a1 = 0.0;
+    if (row < rend && col < R && !(hrows && col > row)) {
+        double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-    for (int s = 0; s < NB; s += 2) {
-        a0 = fma(As[ty][s], Bs[tx][s], a0);
-        a1 = fma(As[ty][s + 1], Bs[tx][s + 1], a1);
+        for (int s = 0; s < NB; s += 2) {
+            a0 = fma(As[ty][s], Bs[tx][s], a0);
+            a1 = fma(As[ty][s + 1], Bs[tx][s + 1], a1);
+        }
+        H[(size_t)row * R + col] -= (a0 + a1);
     }
-    H[(size_t)row * R + col] -= (a0 + a1);
+    // next diagonal block: rows and columns [j1, j1 + jbn)
+    const int jbn = min(NB, R - j1);
+    const int kt = (jbn + UT - 1) / UT;  // tiles per side of the block
+    if (!(hrows && (int)blockIdx.y < kt && (int)blockIdx.x < kt)) return;
+    __shared__ int last;
+    __threadfence();  // this tile's writes before the arrival count
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(counter, 1) == kt * (kt + 1) / 2 - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ BlockSmem S;
+    factor_block(H, R, j1, jbn, dinv, sc, mode, S);
 }
 
 // Backward step J of A L = Y (unit lower L): warp 0 solves A_J L_JJ = Y_J for row r by
@@ -539,33 +553,32 @@ k_bsolve_unit(double* __restrict__ Yf, double* __restrict__ A, int R,
 }
 
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode) {
+                DevScalars* sc, int mode, int* counters) {
     const int nrows = R + n;
+    const int nJ = cdiv(R, NB);
     {
         ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
-        for (int j0 = 0; j0 < R; j0 += NB) {
+        k_ldl_diag<<<1, 128, 0, st>>>(Haug, dinv, R, std::min(NB, R), sc, mode, counters, nJ);
+        count_launch();
+        for (int j0 = 0, step = 0; j0 < R; j0 += NB, ++step) {
             const int jb = std::min(NB, R - j0);
-            const int below = nrows - (j0 + jb);
-            // every panel CTA repeats the diagonal-block factorisation: keep the grid
-            // within one CTA per SM so that the repeats do not share an FP64 pipe
-            const int rpc = std::min(SUB_WARPS * MAX_ROWS_PER_WARP,
-                                     std::max(SUB_WARPS, ((cdiv(std::max(below, 1), kNumSM - 4) +
-                                                           SUB_WARPS - 1) / SUB_WARPS) * SUB_WARPS));
-            k_ldl_panel<<<1 + cdiv(below, rpc), PANEL_THREADS, 0, st>>>(Haug, P, dinv, R, nrows,
-                                                                        j0, jb, rpc, sc, mode);
-            count_launch();
             const int j1 = j0 + jb;
+            const int below = nrows - j1;
+            if (below > 0) {
+                k_ldl_subst<<<cdiv(below, 4), 128, 0, st>>>(Haug, P, dinv, R, nrows, j0, jb);
+                count_launch();
+            }
             if (j1 < R) {
                 const int nH = cdiv(R - j1, UT);
                 dim3 grid(cdiv(R - j1, UT), nH + cdiv(n, UT));
-                k_ldl_update<<<grid, 256, 0, st>>>(Haug, P, R, nrows, j0, jb, nH);
+                k_ldl_update<<<grid, 256, 0, st>>>(Haug, P, dinv, R, nrows, j0, jb, nH, sc, mode,
+                                                   counters + step);
                 count_launch();
             }
         }
     }
     if (n <= 0) return;
     ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
-    const int nJ = cdiv(R, NB);
     double* Yf = Haug + (size_t)R * R;
     for (int J = nJ - 1; J >= 0; --J) {
         const int c0 = J * NB;

@@ -235,6 +235,20 @@ thc_cpd_status thc_cpd_mttkrp_noalloc(int o, int v, int Rt, int R,
                                       const double* const A[4], int mode, double* M,
                                       const thc_cpd_opts* opts);
 
+/* Task list of the dataflow LDL^T of the normal-equation solve (host only, no device
+ * work; Sec. 2.1's normal equations, solved by LDL^T with the M rows carried along).
+ * For an R x R matrix with n appended rows and 16 x 16 tiles, writes the off-path tasks in
+ * the order worker groups claim them, 4 shorts per task: type (0 = substitution S(t, k) of
+ * row tile t with diagonal tile k, 1 = trailing update U(t, j, k) of tile (t, j) with panel
+ * k), then t, j, k. Row tiles 0..ceil(R/16)-1 are rows of H, the next ones rows of M. The
+ * diagonal chain (S(s, s-1), U(s, s, s-1) and the factorisation of tile (s, s)) is not in
+ * the list. out: caller-owned host array of cap tasks (4 * cap shorts), or NULL to query
+ * the count; at most cap tasks are written. Returns the number of tasks, or -1 when R < 1,
+ * n < 0, the shape is beyond the dataflow path (more than 256 tiles a side: the blocked
+ * factorisation runs instead) or the order fails its check that every task comes after
+ * all tasks it waits for. No counterpart in the paper: it exposes the schedule to tests. */
+int thc_cpd_ldl_schedule(int R, int n, short* out, int cap);
+
 /* Message for the last non-OK status returned on this host thread. */
 const char* thc_cpd_last_error(void);
 

@@ -20,7 +20,8 @@ EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_als", "thc_cpd_last_error", "thc_cpd_version", "thc_cpd_launch_count",
            "thc_cpd_profile", "thc_cpd_profile_read", "thc_cpd_split_gemm",
            "thc_cpd_mttkrp_noalloc", "thc_cpd_als_batched", "thc_cpd_mlp_init",
-           "thc_cpd_mlp_forward", "thc_cpd_mlp_grad", "thc_cpd_mlp_train", "thc_cpd_als_trajectory")
+           "thc_cpd_mlp_forward", "thc_cpd_mlp_grad", "thc_cpd_mlp_train", "thc_cpd_als_trajectory",
+           "thc_cpd_ldl_schedule")
 MLP_NPARAM = 6849
 KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
 
@@ -80,6 +81,7 @@ _SIGS = {
                           ctypes.POINTER(ctypes.c_float), OPTS],
     "thc_cpd_als_trajectory": [I, I, I, I, P, P, P, PTR4, P, I, DP, I,
                                ctypes.POINTER(ctypes.c_float), DP, OPTS],
+    "thc_cpd_ldl_schedule": [I, I, ctypes.POINTER(ctypes.c_short), I],
 }
 
 _lib = None

@@ -172,6 +172,22 @@ def thc_cpd_split_gemm(A, B, precision="bf16x3", C=None, stream=None):
     return C
 
 
+def thc_cpd_ldl_schedule(R: int, n: int):
+    """Ticket-ordered task list of the dataflow LDL^T for R x R with n appended rows, as a
+    list of (type, t, j, k) tuples (type 0: substitution S(t, k); 1: update U(t, j, k)).
+    Host only. Raises if the shape is outside the dataflow path or the order fails its
+    check."""
+    lib = load()
+    cnt = lib.thc_cpd_ldl_schedule(int(R), int(n), None, 0)
+    if cnt < 0:
+        raise ThcCpdError(ERR_ARG, f"no dataflow schedule for R={R} n={n}")
+    buf = (ctypes.c_short * (4 * max(cnt, 1)))()
+    got = lib.thc_cpd_ldl_schedule(int(R), int(n), buf, cnt)
+    if got != cnt:
+        raise ThcCpdError(ERR_ARG, "schedule size changed between calls")
+    return [tuple(buf[4 * i:4 * i + 4]) for i in range(cnt)]
+
+
 def thc_cpd_launch_count() -> int:
     return int(load().thc_cpd_launch_count())
 

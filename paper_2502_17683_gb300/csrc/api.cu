@@ -95,6 +95,28 @@ cudaStream_t stream_of(const thc_cpd_opts* o) {
     return o ? (cudaStream_t)o->stream : (cudaStream_t)0;
 }
 
+// The factorisation runs as one dataflow launch per solve unless THC_CPD_LDL=blocked
+// (one launch per block step, kept for comparison).
+bool ldl_dataflow() {
+    static const bool on = [] {
+        const char* e = getenv("THC_CPD_LDL");
+        return !(e && strcmp(e, "blocked") == 0);
+    }();
+    return on;
+}
+
+// Bounded device waits that gave up during this call (flags read and cleared; call after
+// the stream has drained).
+thc_cpd_status kernel_errors(bool mixed) {
+    if (int e = flow_take_error())
+        return set_err(THC_CPD_ERR_TIMEOUT, "LDL^T dataflow wait gave up (code %d)", e);
+    if (mixed) {
+        if (int e = mixed_take_error())
+            return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
+    }
+    return THC_CPD_OK;
+}
+
 // Pinned host copy of the device scalars (one per host thread).
 DevScalars* host_scalars() {
     thread_local DevScalars* h = nullptr;
@@ -118,6 +140,7 @@ struct Ctx {
     double* Haug = nullptr;
     double* LinvD = nullptr;
     int* counters = nullptr;
+    int* flow_sync = nullptr;
     double* part = nullptr;
     size_t part_cap = 0;
     double* red = nullptr;
@@ -187,8 +210,9 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     bytes += 4 * Arena::need<double>(RR);                  // G
     bytes += Arena::need<double>(RtR);                     // Y
     bytes += Arena::need<double>((size_t)(R + nmax) * R);  // Haug
-    bytes += Arena::need<double>((size_t)R * 32 + R);  // panel X and D^{-1}
+    bytes += Arena::need<double>(RR + R);                  // X = L D and D^{-1}
     bytes += Arena::need<int>(cdiv(R, 32));               // arrival counters of the LDL^T
+    bytes += Arena::need<int>(flow_sync_ints(R, nmax));   // dataflow LDL^T progress
     bytes += Arena::need<double>(pc);
     bytes += Arena::need<double>(loss_red_need() + 2 * kNumSM * 2);
     bytes += Arena::need<double>(R);
@@ -209,8 +233,9 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     for (int k = 0; k < 4; ++k) c.G[k] = ar.take<double>(RR);
     c.Y = ar.take<double>(RtR);
     c.Haug = ar.take<double>((size_t)(R + nmax) * R);
-    c.LinvD = ar.take<double>((size_t)R * 32 + R);
+    c.LinvD = ar.take<double>(RR + R);
     c.counters = ar.take<int>(cdiv(R, 32));
+    c.flow_sync = ar.take<int>(flow_sync_ints(R, nmax));
     c.part = ar.take<double>(pc);
     c.red = ar.take<double>(loss_red_need() + 2 * kNumSM * 2);
     c.ones = ar.take<double>(R);
@@ -230,6 +255,11 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
         CK(mixed_setup(c.mx, c.st, Xo, Xv, Z));
     }
     fill(c.st, c.ones, R, 1.0);
+    // dataflow task lists (allocated and uploaded once per shape, never inside a capture)
+    if (ldl_dataflow()) {
+        flow_prepare(R, s.o);
+        flow_prepare(R, s.v);
+    }
     CK(cudaGetLastError());
     return THC_CPD_OK;
 }
@@ -330,7 +360,8 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
         CK(cudaMemcpyAsync(Mrows, c.Msave, sizeof(double) * n * R, cudaMemcpyDeviceToDevice, c.st));
         CK(cudaMemcpyAsync(c.Haug, c.Hsave, sizeof(double) * R * R, cudaMemcpyDeviceToDevice, c.st));
     }
-    chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * 32, c.sc, k, c.counters);
+    chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * R, c.sc, k, c.counters,
+               ldl_dataflow() ? c.flow_sync : nullptr);
     if (safe) {
         DevScalars* h = host_scalars();
         if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
@@ -746,10 +777,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     if (loss_host) *loss_host = h.loss;
     if (fit_host) *fit_host = h.fit;
     CK(cudaStreamSynchronize(c.st));
-    if (c.prec != THC_CPD_FP64) {
-        if (int e = mixed_take_error())
-            return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
-    }
+    CKS(kernel_errors(c.prec != THC_CPD_FP64));
     return THC_CPD_OK;
 }
 
@@ -930,10 +958,7 @@ thc_cpd_status run_batched(int np, thc_cpd_problem* P, int max_sweeps, double to
     CK(cudaStreamWaitEvent(caller, ev_done, 0));
     CK(cudaStreamSynchronize(caller));
     if (opts) opts->flags_out = any_flags;
-    if (prec != THC_CPD_FP64) {
-        if (int e = mixed_take_error())
-            return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
-    }
+    CKS(kernel_errors(prec != THC_CPD_FP64));
     return THC_CPD_OK;
 }
 

@@ -22,12 +22,24 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 // In-place solve of A H = M for A (n x R), H SPD (R x R), by LDL^T with the M rows
 // carried along (fused forward solve) and a unit backward solve.
 //   Haug: (R + n) x R, rows 0..R-1 hold H (lower triangle read), rows R.. hold M.
-//   P: R x 32 panel workspace, dinv: R doubles.
+//   P: R x 32 panel workspace (R x R for the dataflow path), dinv: R doubles.
 //   A pivot <= R * eps * sc->maxdiag sets bit `mode` of sc->fail_mask (the result is then
 //   garbage and the caller replays the mode with the pseudo-inverse).
 //   counters: cdiv(R, 32) ints (arrival counters of the update kernels, cleared inside).
+//   flow_sync: flow_sync_ints(R, n) ints, or null: with it (and a plan for (R, n)) the
+//   factorisation runs as one persistent dataflow launch (P is then R x R), else as one
+//   launch per block step.
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode, int* counters);
+                DevScalars* sc, int mode, int* counters, int* flow_sync);
+
+// Dataflow LDL^T (ldl_flow.cu): ints of progress state for R and n <= nmax; plan set-up
+// for (R, n) (false: too large or the task order failed its check; use the blocked path);
+// the launch; the error flag of bounded waits that gave up (read and cleared).
+size_t flow_sync_ints(int R, int nmax);
+bool flow_prepare(int R, int n);
+cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
+                     DevScalars* sc, int mode, int* sync);
+int flow_take_error();
 
 // lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column); scratch >= R doubles.
 void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch);

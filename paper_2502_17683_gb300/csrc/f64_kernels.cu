@@ -11,6 +11,7 @@
 #include <algorithm>
 
 #include "f64.cuh"
+#include "ldl_common.cuh"
 #include "prof.cuh"
 
 namespace thc {
@@ -295,50 +296,6 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 constexpr int NB = 32;          // block size of the factorisation
 constexpr int UT = 16;          // trailing-update tile (one output per thread)
 
-// Reciprocal 1/d of a positive normal double from a seed built with integer operations
-// (the FP32 reciprocal of the leading 23 mantissa bits, rescaled by the exponent, ~2^-22
-// accurate), refined by one third-order Newton step y <- y (1 + e + e^2), e = 1 - d y
-// (cubic convergence: 2^-22 -> below 2^-60). Three dependent FP64 operations. Only
-// d > 0 with 2^-998 < d < 2^998 reaches here (the pivot test runs first).
-__device__ __forceinline__ double recip_nr(double d) {
-    const long long bits = __double_as_longlong(d);
-    const int e = (int)((bits >> 52) & 0x7FF);                        // biased exponent of d
-    const unsigned mhi = (unsigned)((bits >> 29) & 0x7FFFFF);         // top 23 mantissa bits
-    const float m = __uint_as_float(0x3F800000u | mhi);              // in [1, 2)
-    float r;                                                          // in (0.5, 1]
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));            // ~2^-23 seed
-    const unsigned rb = __float_as_uint(r);
-    const int er = (int)((rb >> 23) & 0xFF) - 127;                    // -1 or 0
-    // 1/d = r * 2^-(e - 1023)
-    const long long yb = ((long long)(er - (e - 1023) + 1023) << 52) |
-                         ((long long)(rb & 0x7FFFFF) << 29);
-    const double y = __longlong_as_double(yb);
-    const double t = fma(-d, y, 1.0);
-    const double u = fma(t, t, t);
-    return fma(y, u, y);
-}
-
-// d > tau with d, tau >= 0 finite-or-not, decided on the integer pipe: non-negative
-// doubles order like their bit patterns; NaN / inf / negative fail.
-__device__ __forceinline__ bool pivot_ok(double d, double tau) {
-    const long long bd = __double_as_longlong(d), bt = __double_as_longlong(tau);
-    const bool finite_pos = bd > 0 && bd < 0x7FF0000000000000LL;
-    return finite_pos && bd > bt && ((bd >> 52) & 0x7FF) > 24 && ((bd >> 52) & 0x7FF) < 2022;
-}
-
-// Pairs (r, s), c < s <= r < 32, ordered by s descending: the group of s = 31 - k holds the
-// k + 1 rows r = s..31 and starts at k (k + 1) / 2, so the pairs with s > c form the prefix
-// of length (31 - c)(32 - c) / 2. Closed-form inverse of the group start (FP32 sqrt is
-// exact for these small integers; the two checks correct any rounding of the estimate).
-__device__ __forceinline__ unsigned short pair_code(int e) {
-    int k = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    if ((k + 1) * (k + 2) / 2 <= e) ++k;
-    if (k * (k + 1) / 2 > e) --k;
-    const int s = NB - 1 - k;
-    const int r = s + (e - k * (k + 1) / 2);
-    return (unsigned short)((r << 8) | s);
-}
-
 struct BlockSmem {
     double Ds[NB][NB + 1];
     double Ls[NB][NB + 1];
@@ -362,7 +319,7 @@ __device__ void factor_block(double* __restrict__ H, int R, int j0, int jb,
         S.Ds[r][c] = (r < jb && c <= r) ? __ldcg(H + (size_t)(j0 + r) * R + j0 + c) : 0.0;
         S.Ls[r][c] = (r == c) ? 1.0 : 0.0;
     }
-    for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code(e);
+    for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code<NB>(e);
     __syncthreads();
     if (tid == 0) {
         S.bad = 0;
@@ -553,10 +510,13 @@ k_bsolve_unit(double* __restrict__ Yf, double* __restrict__ A, int R,
 }
 
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode, int* counters) {
+                DevScalars* sc, int mode, int* counters, int* flow_sync) {
     const int nrows = R + n;
     const int nJ = cdiv(R, NB);
-    {
+    if (flow_sync && flow_prepare(R, n)) {
+        ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
+        ldl_flow(st, R, n, Haug, P, dinv, sc, mode, flow_sync);
+    } else {
         ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
         k_ldl_diag<<<1, 128, 0, st>>>(Haug, dinv, R, std::min(NB, R), sc, mode, counters, nJ);
         count_launch();

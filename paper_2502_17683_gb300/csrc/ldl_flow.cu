@@ -1,0 +1,571 @@
+// Dataflow LDL^T of the normal matrix with the forward solve fused (the rows of M are
+// carried along as extra rows), in one persistent launch per solve.
+//
+// Why: the factorisation has one pivot per column on its critical path, and GB300 runs
+// FP64 at about two FMA per clock per SM (one warp-instruction per SM sub-partition every
+// 64 clocks). A launch per block step serialises the diagonal factorisation, the panel
+// substitution and the trailing update, and the diagonal factorisation shares its SM with
+// update CTAs that saturate the FP64 pipe. Here one CTA (the chain) owns the critical
+// path on an SM of its own, and the other CTAs work through the off-path tiles while it
+// runs, so the trailing update of step k overlaps the diagonal work of steps k+1, k+2...
+//
+// Tiles are FB x FB (FB = 16). With T = ceil(R / FB) column tiles, row tiles 0..T-1 are
+// the rows of H and row tiles T.. the appended rows of M. Tasks:
+//   F(s)      LDL^T of the diagonal tile (s, s)                       [chain]
+//   S(t, k)   X L_kk^T = B for tile (t, k), then L = X D_k^-1            [chain if t = k+1]
+//   U(t,j,k)  tile (t, j) -= L(t, k) X(j, k)^T (lower half if t = j)   [chain if t = j = k+1]
+// Chain step s runs S(s, s-1), U(s, s, s-1), F(s) back to back in shared memory. The
+// other tasks form one list in a fixed order; worker groups (128 threads) claim entries
+// with an atomic ticket and wait for their inputs on per-tile progress counters:
+//   sdone[t] = k + 1 once S(t, k) is stored; cnt[t][j] = number of panels applied to tile
+//   (t, j); fdone = s + 1 once F(s) is stored.
+// Every tile receives its updates in panel order (a U task waits for the previous panel's
+// update of the same tile), so the result does not depend on the schedule: bit-identical
+// from run to run.
+//
+// Progress without deadlock, whatever the number of resident CTAs: the chain role goes to
+// the first CTA that starts, tickets are claimed in list order only by running groups, and
+// the list order (checked on the host before the first launch) puts every task that the
+// chain or a task waits for before the waiting task. So the lowest unfinished ticket can
+// always run. Every wait is bounded (1 s); on expiry the kernel raises an abort flag that
+// ends all waits, and the host reports ERR_TIMEOUT.
+//
+// Result layout (same as the blocked factorisation): strictly-lower L and diag(D) in H,
+// D^-1 in dinv, Y = M L^-T D^-1 in the appended rows; P (R x R) holds X = L D per tile.
+#include <float.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "thc_cpd.h"
+#include "f64.cuh"
+#include "ldl_common.cuh"
+#include "prof.cuh"
+
+namespace thc {
+
+__device__ int g_flow_error = 0;
+
+namespace {
+
+constexpr int FB = 16;
+constexpr int kGroups = 4;                 // worker groups (128 threads) per CTA
+constexpr int kFlowThreads = 128 * kGroups;
+constexpr int kFlowSmem = 120 * 1024;      // more than half an SM: one CTA per SM
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr int kSyncHead = 4;               // ticket, arrivals, fdone, abort
+constexpr int kMaxTiles = 256;             // larger R: the blocked factorisation
+
+struct FlowTask {
+    short type, t, j, k;                   // type 0: S(t, k); 1: U(t, j, k)
+};
+
+struct ChainSmem {
+    double Lp[FB][FB + 1];   // L of the previous diagonal tile (strictly lower)
+    double dp[FB];           // its D^-1
+    double Xs[FB][FB + 1];   // X(s, s-1)
+    double Ls[FB][FB + 1];   // L(s, s-1)
+    double D[FB][FB + 1];    // diagonal tile being factorised
+    double L[FB][FB + 1];
+    double dinv[FB];
+    unsigned short pairs[FB * (FB + 1) / 2];
+    int bad;
+    int ok;
+};
+
+struct WorkerSmem {
+    double A[FB][FB + 1];
+    double B[FB][FB + 1];
+    int ticket;
+    int ok;
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void group_sync(int id) {
+    asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+}
+
+// *p >= v (true), or the launch is aborting / this wait gave up (false).
+__device__ bool flow_wait(const int* p, int v, int* abort_flag) {
+    if (ld_acquire(p) >= v) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0;; ++it) {
+        if (it > 8) __nanosleep(40);
+        if (ld_acquire(p) >= v) return true;
+        if ((it & 31) == 31) {
+            if (ld_acquire(abort_flag)) return false;
+            if (global_ns() - t0 > kWaitNs) {
+                atomicExch(abort_flag, 1);
+                atomicExch(&g_flow_error, 1);
+                return false;
+            }
+        }
+    }
+}
+
+// LDL^T of the jb x jb tile in S.D (lower triangle) into S.L (strictly lower), S.D's
+// diagonal and S.dinv. Threads 0..127 compute, every thread of the CTA passes the
+// barriers: thread 0 carries the pivot chain one column ahead, warps 1-3 apply column c to
+// the rest of the tile over the packed pair list. A pivot <= tau sets S.bad and continues
+// with 1 (the caller then replays the mode with the pseudo-inverse).
+__device__ void factor_tile(ChainSmem& S, int jb, double tau) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        S.bad = 0;
+        double d = S.D[0][0];
+        if (!pivot_ok(d, tau)) {
+            S.bad = 1;
+            d = 1.0;
+            S.D[0][0] = d;
+        }
+        S.dinv[0] = recip_nr(d);
+    }
+    for (int c = 0; c < jb; ++c) {
+        __syncthreads();  // dinv[c] and column c are final
+        const double inv = S.dinv[c];
+        if (tid == 0) {
+            if (c + 1 < jb) {
+                const double x = S.D[c + 1][c];
+                const double l = x * inv;
+                double d1 = fma(-l, x, S.D[c + 1][c + 1]);
+                S.L[c + 1][c] = l;
+                if (!pivot_ok(d1, tau)) {
+                    S.bad = 1;
+                    d1 = 1.0;
+                }
+                S.D[c + 1][c + 1] = d1;
+                S.dinv[c + 1] = recip_nr(d1);
+            }
+        } else if (tid >= 32 && tid < 128) {
+            const int hi = FB - 1 - c;
+            const int npair = hi * (hi + 1) / 2;
+            for (int e = tid - 32; e < npair; e += 96) {
+                const int rs = S.pairs[e];
+                const int r = rs >> 8, ss = rs & 0xFF;
+                if (r >= jb || (r == c + 1 && ss == c + 1)) continue;
+                const double l = S.D[r][c] * inv;
+                if (ss == c + 1) S.L[r][c] = l;
+                S.D[r][ss] = fma(-l, S.D[ss][c], S.D[r][ss]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+struct FlowArgs {
+    double* H;
+    double* P;
+    double* dinv;
+    int R, nrows, nT, nM;
+    const FlowTask* tasks;
+    int ntasks;
+    int* sync;
+    DevScalars* sc;
+    int mode;
+};
+
+__device__ __forceinline__ int* sdone_of(const FlowArgs& a) { return a.sync + kSyncHead; }
+__device__ __forceinline__ int* cnt_of(const FlowArgs& a) {
+    return a.sync + kSyncHead + a.nT + a.nM;
+}
+
+// The critical path: for s = 0..T-1, S(s, s-1), U(s, s, s-1), F(s).
+__device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
+    const int tid = threadIdx.x, R = a.R, nT = a.nT;
+    int* fdone = a.sync + 2;
+    int* abort_flag = a.sync + 3;
+    int* sdone = sdone_of(a);
+    int* cnt = cnt_of(a);
+    const double tau = (double)R * DBL_EPSILON * a.sc->maxdiag;
+    for (int e = tid; e < FB * (FB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code<FB>(e);
+    if (tid < FB * FB) S.L[tid >> 4][tid & 15] = 0.0;
+    const int r = (tid >> 4) & 15, c = tid & 15;  // element of a tile (threads 0..255)
+    const bool el = tid < FB * FB;
+    int bad = 0;
+    for (int s = 0; s < nT; ++s) {
+        const int s0 = s * FB, sb = min(FB, R - s0);
+        if (tid == 0) {
+            bool ok = true;
+            if (s >= 1)
+                ok = flow_wait(&cnt[s * nT + s - 1], s - 1, abort_flag) &&
+                     flow_wait(&cnt[s * nT + s], s - 1, abort_flag);
+            S.ok = ok;
+        }
+        __syncthreads();
+        if (!S.ok) break;
+        double dss = 0.0, b = 0.0;
+        if (el && r < sb) {
+            if (c <= r) dss = __ldcg(a.H + (size_t)(s0 + r) * R + s0 + c);
+            if (s >= 1) b = __ldcg(a.H + (size_t)(s0 + r) * R + s0 - FB + c);
+        }
+        if (s >= 1) {
+            if (el) {
+                // X L_{s-1}^T = B: column sweep, x[r][q] passed along the row's half-warp
+#pragma unroll
+                for (int q = 0; q < FB - 1; ++q) {
+                    const double xq = __shfl_sync(0xffffffffu, b, (tid & 16) | q);
+                    if (c > q) b = fma(-xq, S.Lp[c][q], b);
+                }
+                const double l = b * S.dp[c];
+                if (r < sb) {
+                    a.H[(size_t)(s0 + r) * R + s0 - FB + c] = l;
+                    a.P[(size_t)(s0 + r) * R + s0 - FB + c] = b;
+                }
+                S.Xs[r][c] = b;
+                S.Ls[r][c] = l;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                st_release(&sdone[s], s);
+            }
+            if (el && c <= r) {
+                double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+                for (int q = 0; q < FB; q += 2) {
+                    a0 = fma(S.Ls[r][q], S.Xs[c][q], a0);
+                    a1 = fma(S.Ls[r][q + 1], S.Xs[c][q + 1], a1);
+                }
+                dss -= (a0 + a1);
+            }
+        }
+        if (el) S.D[r][c] = dss;
+        __syncthreads();
+        factor_tile(S, sb, tau);
+        if (el && r < sb && c <= r)
+            a.H[(size_t)(s0 + r) * R + s0 + c] = (c < r) ? S.L[r][c] : S.D[r][r];
+        if (tid < sb) a.dinv[s0 + tid] = S.dinv[tid];
+        if (el) S.Lp[r][c] = (c < r && r < sb) ? S.L[r][c] : 0.0;
+        if (tid < FB) S.dp[tid] = tid < sb ? S.dinv[tid] : 0.0;
+        bad |= S.bad;
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release(fdone, s + 1);
+        }
+    }
+    if (tid == 0 && bad) atomicOr(&a.sc->fail_mask, 1 << a.mode);
+}
+
+// Rows of row tile t: [r0, rlim) with r0 = first row (H rows, then M rows).
+__device__ __forceinline__ void tile_rows(const FlowArgs& a, int t, int& r0, int& rlim) {
+    if (t < a.nT) {
+        r0 = t * FB;
+        rlim = a.R;
+    } else {
+        r0 = a.R + (t - a.nT) * FB;
+        rlim = a.nrows;
+    }
+}
+
+// S(t, k) by one worker group: thread gt owns column c of rows rr and rr + 8.
+__device__ void task_S(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t, int k) {
+    const int R = a.R;
+    int* sdone = sdone_of(a);
+    if (gt == 0)
+        W.ok = flow_wait(a.sync + 2, k + 1, a.sync + 3) &&
+               flow_wait(&cnt_of(a)[t * a.nT + k], k, a.sync + 3);
+    group_sync(bar);
+    if (!W.ok) return;
+    int r0, rlim;
+    tile_rows(a, t, r0, rlim);
+    const int k0 = k * FB, kb = min(FB, R - k0);
+    const int c = gt & 15, rr = gt >> 4;
+    const int row0 = r0 + rr, row1 = r0 + rr + 8;
+    const bool cv = c < kb;
+    double b0 = (cv && row0 < rlim) ? __ldcg(a.H + (size_t)row0 * R + k0 + c) : 0.0;
+    double b1 = (cv && row1 < rlim) ? __ldcg(a.H + (size_t)row1 * R + k0 + c) : 0.0;
+    double lr[FB];
+#pragma unroll
+    for (int q = 0; q < FB; ++q)
+        lr[q] = (q < c && cv) ? __ldcg(a.H + (size_t)(k0 + c) * R + k0 + q) : 0.0;
+    const double di = cv ? __ldcg(a.dinv + k0 + c) : 0.0;
+    const int src = gt & 16;
+#pragma unroll
+    for (int q = 0; q < FB - 1; ++q) {
+        const double x0 = __shfl_sync(0xffffffffu, b0, src | q);
+        const double x1 = __shfl_sync(0xffffffffu, b1, src | q);
+        if (c > q) {
+            b0 = fma(-x0, lr[q], b0);
+            b1 = fma(-x1, lr[q], b1);
+        }
+    }
+    const bool hrow = t < a.nT;
+    if (cv && row0 < rlim) {
+        a.H[(size_t)row0 * R + k0 + c] = b0 * di;
+        if (hrow) a.P[(size_t)row0 * R + k0 + c] = b0;
+    }
+    if (cv && row1 < rlim) {
+        a.H[(size_t)row1 * R + k0 + c] = b1 * di;
+        if (hrow) a.P[(size_t)row1 * R + k0 + c] = b1;
+    }
+    group_sync(bar);
+    if (gt == 0) {
+        __threadfence();
+        st_release(&sdone[t], k + 1);
+    }
+}
+
+// U(t, j, k) by one worker group: tile (t, j) -= L(t, k) X(j, k)^T.
+__device__ void task_U(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t, int j, int k) {
+    const int R = a.R;
+    int* sdone = sdone_of(a);
+    int* cnt = cnt_of(a);
+    if (gt == 0)
+        W.ok = flow_wait(&sdone[t], k + 1, a.sync + 3) && flow_wait(&sdone[j], k + 1, a.sync + 3) &&
+               flow_wait(&cnt[t * a.nT + j], k, a.sync + 3);
+    group_sync(bar);
+    if (!W.ok) return;
+    int r0, rlim;
+    tile_rows(a, t, r0, rlim);
+    const int k0 = k * FB, kb = min(FB, R - k0), c0 = j * FB;
+    const int c = gt & 15, rr = gt >> 4;
+    const int row0 = r0 + rr, row1 = r0 + rr + 8, col = c0 + c;
+    const bool cv = c < kb;
+    W.A[rr][c] = (cv && row0 < rlim) ? __ldcg(a.H + (size_t)row0 * R + k0 + c) : 0.0;
+    W.A[rr + 8][c] = (cv && row1 < rlim) ? __ldcg(a.H + (size_t)row1 * R + k0 + c) : 0.0;
+    W.B[rr][c] = (cv && c0 + rr < R) ? __ldcg(a.P + (size_t)(c0 + rr) * R + k0 + c) : 0.0;
+    W.B[rr + 8][c] = (cv && c0 + rr + 8 < R) ? __ldcg(a.P + (size_t)(c0 + rr + 8) * R + k0 + c) : 0.0;
+    const bool diag = t == j;
+    const bool v0 = row0 < rlim && col < R && !(diag && c > rr);
+    const bool v1 = row1 < rlim && col < R && !(diag && c > rr + 8);
+    const double h0 = v0 ? __ldcg(a.H + (size_t)row0 * R + col) : 0.0;
+    const double h1 = v1 ? __ldcg(a.H + (size_t)row1 * R + col) : 0.0;
+    group_sync(bar);
+    double s0 = 0.0, s1 = 0.0, u0 = 0.0, u1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < FB; q += 2) {
+        const double b0 = W.B[c][q], b1 = W.B[c][q + 1];
+        s0 = fma(W.A[rr][q], b0, s0);
+        s1 = fma(W.A[rr][q + 1], b1, s1);
+        u0 = fma(W.A[rr + 8][q], b0, u0);
+        u1 = fma(W.A[rr + 8][q + 1], b1, u1);
+    }
+    if (v0) a.H[(size_t)row0 * R + col] = h0 - (s0 + s1);
+    if (v1) a.H[(size_t)row1 * R + col] = h1 - (u0 + u1);
+    group_sync(bar);
+    if (gt == 0) {
+        __threadfence();
+        st_release(&cnt[t * a.nT + j], k + 1);
+    }
+}
+
+__device__ void flow_worker(const FlowArgs& a, WorkerSmem* ws) {
+    const int g = threadIdx.x >> 7, gt = threadIdx.x & 127, bar = 1 + g;
+    WorkerSmem& W = ws[g];
+    for (;;) {
+        if (gt == 0) W.ticket = atomicAdd(a.sync, 1);
+        group_sync(bar);
+        const int ti = W.ticket;
+        if (ti >= a.ntasks) break;
+        const FlowTask tk = a.tasks[ti];
+        if (tk.type == 0)
+            task_S(a, W, gt, bar, tk.t, tk.k);
+        else
+            task_U(a, W, gt, bar, tk.t, tk.j, tk.k);
+    }
+}
+
+__global__ void __launch_bounds__(kFlowThreads, 1) k_ldl_flow(FlowArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int role;
+    if (threadIdx.x == 0) role = atomicAdd(a.sync + 1, 1);
+    __syncthreads();
+    if (role == 0)
+        flow_chain(a, *reinterpret_cast<ChainSmem*>(smem));
+    else
+        flow_worker(a, reinterpret_cast<WorkerSmem*>(smem));
+}
+
+static_assert(sizeof(ChainSmem) <= kFlowSmem, "chain shared memory");
+static_assert(kGroups * sizeof(WorkerSmem) <= kFlowSmem, "worker shared memory");
+
+// ---- host: the task list ---------------------------------------------------------------
+// Ticket order: panel by panel (right-looking), so that the updates of a tile arrive one
+// panel period apart instead of queueing up behind each other; within panel k the
+// substitutions first (row tile ascending: S(k+2, k) feeds the chain two steps ahead),
+// then the updates by column tile (column k+1 first: the chain's next input), rows of H
+// before rows of M.
+bool build_tasks(int R, int n, std::vector<FlowTask>& out, int& nT, int& nM) {
+    nT = cdiv(R, FB);
+    nM = cdiv(n, FB);
+    const int nRT = nT + nM;
+    std::vector<FlowTask> it;  // generated in ticket order
+    auto push = [&](int type, int t, int j, int k) {
+        it.push_back(FlowTask{(short)type, (short)t, (short)j, (short)k});
+    };
+    for (int k = 0; k < nT; ++k) {
+        for (int t = k + 2; t < nT; ++t) push(0, t, 0, k);
+        for (int t = nT; t < nRT; ++t) push(0, t, 0, k);
+        for (int j = k + 1; j < nT; ++j)
+            for (int t = j; t < nT; ++t)
+                if (!(t == j && j == k + 1)) push(1, t, j, k);
+        for (int j = k + 1; j < nT; ++j)
+            for (int t = nT; t < nRT; ++t) push(1, t, j, k);
+    }
+    if (it.size() >= 0x7fffffff) return false;
+    // index of every ticket task, -1 for chain tasks or tasks that do not exist
+    std::vector<int> sidx((size_t)nRT * nT, -1), uidx((size_t)nRT * nT * nT, -1);
+    for (size_t i = 0; i < it.size(); ++i) {
+        const FlowTask& x = it[i];
+        if (x.type == 0)
+            sidx[(size_t)x.t * nT + x.k] = (int)i;
+        else
+            uidx[((size_t)x.t * nT + x.j) * nT + x.k] = (int)i;
+    }
+    auto U = [&](int t, int j, int k) { return uidx[((size_t)t * nT + j) * nT + k]; };
+    // every row tile below the chain is substituted with every panel (the updates are then
+    // complete too: each S task depends on all updates of its tile)
+    for (int k = 0; k < nT; ++k)
+        for (int t = k + 2; t < nRT; ++t)
+            if (sidx[(size_t)t * nT + k] < 0) return false;
+    // chain step s waits for U(s, s-1, m) and U(s, s, m), m <= s - 2; wmax[s] = the largest
+    // ticket any chain step up to s waits for
+    std::vector<int> wmax(nT, -1);
+    for (int s = 0; s < nT; ++s) {
+        int w = s ? wmax[s - 1] : -1;
+        for (int m = 0; m + 2 <= s; ++m) {
+            const int a = U(s, s - 1, m), b = U(s, s, m);
+            if (a < 0 || b < 0) return false;
+            w = std::max(w, std::max(a, b));
+        }
+        wmax[s] = w;
+    }
+    // every task's inputs come earlier in the list; a task that waits for chain step s comes
+    // after everything chain steps 0..s wait for
+    for (size_t i = 0; i < it.size(); ++i) {
+        const FlowTask& x = it[i];
+        const int me = (int)i;
+        if (x.type == 0) {
+            for (int m = 0; m < x.k; ++m) {
+                const int d = U(x.t, x.k, m);
+                if (d < 0 || d >= me) return false;
+            }
+            if (wmax[x.k] >= me) return false;
+        } else {
+            const int t = x.t, j = x.j, k = x.k;
+            const bool s_t_chain = t < nT && t == k + 1, s_j_chain = j == k + 1;
+            if (!s_t_chain) {
+                const int d = sidx[(size_t)t * nT + k];
+                if (d < 0 || d >= me) return false;
+            }
+            if (!s_j_chain) {
+                const int d = sidx[(size_t)j * nT + k];
+                if (d < 0 || d >= me) return false;
+            }
+            if (k >= 1) {
+                const int d = U(t, j, k - 1);
+                if (d < 0 || d >= me) return false;
+            }
+            if (s_j_chain && wmax[k + 1] >= me) return false;
+        }
+    }
+    out.swap(it);
+    return true;
+}
+
+struct Plan {
+    FlowTask* tasks = nullptr;
+    int ntasks = 0, nT = 0, nM = 0, grid = 0;
+    bool ok = false;
+};
+
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int>, Plan> g_plans;  // (device, R, n) -> plan (kept)
+
+const Plan* get_plan(int R, int n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto key = std::make_tuple(dev, R, n);
+    auto f = g_plans.find(key);
+    if (f != g_plans.end()) return f->second.ok ? &f->second : nullptr;
+    Plan& p = g_plans[key];
+    if (cdiv(R, FB) > kMaxTiles || cdiv(n, FB) > kMaxTiles) return nullptr;
+    std::vector<FlowTask> h;
+    if (!build_tasks(R, n, h, p.nT, p.nM)) return nullptr;
+    p.ntasks = (int)h.size();
+    if (p.ntasks > 0) {
+        if (cudaMalloc(&p.tasks, sizeof(FlowTask) * h.size()) != cudaSuccess) return nullptr;
+        if (cudaMemcpy(p.tasks, h.data(), sizeof(FlowTask) * h.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return nullptr;
+    }
+    int nsm = kNumSM;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // about one worker group per task of an average panel step, one CTA per SM at most
+    const long per_step = (p.ntasks + p.nT - 1) / std::max(1, p.nT);
+    p.grid = (int)std::min<long>(nsm, 1 + std::max<long>(1, (per_step + kGroups - 1) / kGroups));
+    if (cudaFuncSetAttribute(k_ldl_flow, cudaFuncAttributeMaxDynamicSharedMemorySize, kFlowSmem) !=
+        cudaSuccess)
+        return nullptr;
+    p.ok = true;
+    return &p;
+}
+
+}  // namespace
+
+size_t flow_sync_ints(int R, int nmax) {
+    const size_t nT = cdiv(R, FB), nRT = nT + cdiv(nmax, FB);
+    return kSyncHead + nRT + nRT * nT;
+}
+
+bool flow_prepare(int R, int n) { return get_plan(R, n) != nullptr; }
+
+cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
+                     DevScalars* sc, int mode, int* sync) {
+    const Plan* p = get_plan(R, n);
+    if (!p) return cudaErrorInvalidValue;
+    const size_t nsync = kSyncHead + (size_t)(p->nT + p->nM) * (1 + p->nT);
+    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * nsync, st);
+    if (e != cudaSuccess) return e;
+    FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, p->tasks, p->ntasks, sync, sc, mode};
+    k_ldl_flow<<<p->grid, kFlowThreads, kFlowSmem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int flow_take_error() {
+    int h = 0, z = 0;
+    cudaMemcpyFromSymbol(&h, g_flow_error, sizeof(int));
+    if (h) cudaMemcpyToSymbol(g_flow_error, &z, sizeof(int));
+    return h;
+}
+
+}  // namespace thc
+
+extern "C" int thc_cpd_ldl_schedule(int R, int n, short* out, int cap) {
+    using namespace thc;
+    if (R < 1 || n < 0 || cdiv(R, FB) > kMaxTiles || cdiv(n, FB) > kMaxTiles) return -1;
+    std::vector<FlowTask> h;
+    int nT = 0, nM = 0;
+    if (!build_tasks(R, n, h, nT, nM)) return -1;
+    if (out) {
+        const size_t m = std::min(h.size(), (size_t)std::max(cap, 0));
+        for (size_t i = 0; i < m; ++i) {
+            out[4 * i] = h[i].type;
+            out[4 * i + 1] = h[i].t;
+            out[4 * i + 2] = h[i].j;
+            out[4 * i + 3] = h[i].k;
+        }
+    }
+    return (int)h.size();
+}

@@ -53,7 +53,13 @@ def test_batched_fp64_matches_oracle_and_stops_per_problem(api):
         p = d["host"]
         ref = O.als(p.Xo, p.Xv, p.Z, p.A, 200, tol=1e-5)
         assert r["sweeps"] == ref["sweeps"]
-        assert abs(r["fit"] - ref["fits"][-1]) <= 1e-10
+        nG2 = ref["normG2"]
+        assert abs(r["loss"] - ref["losses"][-1]) <= 1e-10 * nG2
+        # fit = 1 - sqrt(loss / ||G||^2): at an exact fit (loss at the rounding floor of the
+        # factor form, ~eps ||G||^2) the square root turns a rounding-level loss into
+        # ~sqrt(eps) of fit, so the fits are compared only above that floor
+        if ref["losses"][-1] > 1e-12 * nG2:
+            assert abs(r["fit"] - ref["fits"][-1]) <= 1e-10
     assert len({r["sweeps"] for r in res}) >= 1
 
 

@@ -75,7 +75,20 @@ typedef struct thc_cpd_opts {
     int accepted_out;    /* out (thc_cpd_als with mlp): accepted extrapolated steps */
     const float* mlp;    /* thc_cpd_als: device parameters of the step-proposer network
                             (THC_CPD_MLP_NPARAM floats) or NULL for plain ALS; see below */
+    int ldl;             /* thc_cpd_ldl: how the LDL^T of the normal equations runs.
+                            AUTO (0): the dataflow kernel for a single problem with R <= 1280,
+                            the blocked launches for larger R and for thc_cpd_als_batched
+                            (problems side by side fill the GPU better with short launches).
+                            Both give the same factorisation up to rounding order; each is
+                            bit-reproducible on its own. */
 } thc_cpd_opts;
+
+/* Values of thc_cpd_opts.ldl. */
+typedef enum {
+    THC_CPD_LDL_AUTO = 0,
+    THC_CPD_LDL_BLOCKED = 1,   /* one launch per 32-column block step */
+    THC_CPD_LDL_DATAFLOW = 2   /* one persistent launch (R <= 1280; blocked beyond) */
+} thc_cpd_ldl;
 
 /* One independent problem of a batched run (thc_cpd_als_batched). Inputs as for
  * thc_cpd_als (device pointers); sweeps_done, flags_out, loss and fit are outputs. */

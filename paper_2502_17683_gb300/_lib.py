@@ -14,6 +14,7 @@ OK, ERR_ARG, ERR_SHAPE, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_ALLOC, ERR_UNS
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
                 5: "ERR_TIMEOUT", 6: "ERR_ALLOC", 7: "ERR_UNSUPPORTED"}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+LDL_VARIANTS = {"auto": 0, "blocked": 1, "dataflow": 2}
 
 # every symbol include/thc_cpd.h declares
 EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
@@ -46,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("polish_sweeps", ctypes.c_int),
                 ("autotune", ctypes.c_int),
                 ("accepted_out", ctypes.c_int),
-                ("mlp", ctypes.c_void_p)]
+                ("mlp", ctypes.c_void_p),
+                ("ldl", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):

@@ -10,8 +10,8 @@ import ctypes
 
 import torch
 
-from ._lib import (ERR_ARG, KCLASS_NAMES, MLP_NPARAM, PRECISIONS, PTR4, KStat, Opts, Problem,
-                   ThcCpdError, check, load)
+from ._lib import (ERR_ARG, KCLASS_NAMES, LDL_VARIANTS, MLP_NPARAM, PRECISIONS, PTR4, KStat,
+                   Opts, Problem, ThcCpdError, check, load)
 
 __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
            "thc_cpd_als", "thc_cpd_version", "thc_cpd_launch_count", "thc_cpd_profile",
@@ -41,8 +41,11 @@ def _fdev(t: torch.Tensor, name: str, shape=None) -> int:
 
 
 def _opts(precision="fp64", stream=None, loss_every=0, history=None, polish_sweeps=0,
-          autotune=False) -> Opts:
+          autotune=False, ldl="auto") -> Opts:
     o = Opts()
+    if ldl not in LDL_VARIANTS:
+        raise ThcCpdError(ERR_ARG, f"unknown ldl variant {ldl!r}")
+    o.ldl = LDL_VARIANTS[ldl]
     o.polish_sweeps = int(polish_sweeps)
     o.autotune = 1 if autotune else 0
     if isinstance(precision, str):
@@ -122,11 +125,12 @@ def thc_cpd_loss(Xo, Xv, Z, A, lam=None, normG2: float = 0.0, stream=None):
     return loss.value, fit.value
 
 
-def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", stream=None):
+def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", stream=None,
+                      ldl="auto"):
     o, v, Rt = _dims(Xo, Xv, Z)
     R = A[0].shape[1]
     loss, fit = ctypes.c_double(), ctypes.c_double()
-    opts = _opts(precision, stream)
+    opts = _opts(precision, stream, ldl=ldl)
     check(load().thc_cpd_als_sweep(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
                                    _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R),
                                    _dev(lam, "lam", (R,)), float(normG2), ctypes.byref(loss),
@@ -136,14 +140,14 @@ def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", 
 
 def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision="fp64",
                 stream=None, loss_every: int = 0, history: bool = False, polish_sweeps: int = 0,
-                autotune: bool = False, mlp=None):
+                autotune: bool = False, mlp=None, ldl="auto"):
     o, v, Rt = _dims(Xo, Xv, Z)
     R = A[0].shape[1]
     loss, fit, done = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
     hist = (ctypes.c_double * max(1, 2 * max_sweeps))() if history else None
     opts = _opts(precision, stream, loss_every,
                  ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
-                 polish_sweeps, autotune)
+                 polish_sweeps, autotune, ldl)
     if mlp is not None:
         opts.mlp = _fdev(mlp, "mlp", (MLP_NPARAM,))
     check(load().thc_cpd_als(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
@@ -208,7 +212,7 @@ def thc_cpd_profile_read() -> dict:
 
 
 def thc_cpd_als_batched(problems, max_sweeps: int, tol: float = 0.0, precision="fp64",
-                        stream=None, autotune: bool = False):
+                        stream=None, autotune: bool = False, ldl="auto"):
     """problems: list of dicts with Xo, Xv, Z, A (list of 4), lam (device tensors, updated in
     place). Returns a list of dict(sweeps, loss, fit, flags) per problem."""
     n = len(problems)
@@ -223,7 +227,7 @@ def thc_cpd_als_batched(problems, max_sweeps: int, tol: float = 0.0, precision="
         for k, a in enumerate(pr["A"]):
             arr[i].A[k] = _dev(a, f"A[{k}]", ((o, v, o, v)[k], R))
         arr[i].lam = _dev(pr["lam"], "lam", (R,))
-    opts = _opts(precision, stream, autotune=autotune)
+    opts = _opts(precision, stream, autotune=autotune, ldl=ldl)
     check(load().thc_cpd_als_batched(n, ctypes.cast(arr, ctypes.c_void_p), int(max_sweeps),
                                      float(tol), ctypes.byref(opts)))
     return [dict(sweeps=arr[i].sweeps_done, loss=arr[i].loss, fit=arr[i].fit, flags=arr[i].flags_out)
@@ -269,7 +273,8 @@ def thc_cpd_mlp_train(params, X, y, epochs: int, batch: int = 64, lr: float = 1e
     return loss.value
 
 
-def thc_cpd_als_trajectory(Xo, Xv, Z, A, lam, sweeps: int, alphas, precision="fp64", stream=None):
+def thc_cpd_als_trajectory(Xo, Xv, Z, A, lam, sweeps: int, alphas, precision="fp64", stream=None,
+                           ldl="auto"):
     """Plain ALS for `sweeps` sweeps, recording per sweep the 40 features and the exact losses
     of the trial points at each alpha. Returns (features (sweeps, 40), losses (sweeps, na))."""
     import numpy as np
@@ -278,7 +283,7 @@ def thc_cpd_als_trajectory(Xo, Xv, Z, A, lam, sweeps: int, alphas, precision="fp
     al = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
     feats = np.zeros((sweeps, 40), dtype=np.float32)
     tl = np.zeros((sweeps, len(al)), dtype=np.float64)
-    opts = _opts(precision, stream)
+    opts = _opts(precision, stream, ldl=ldl)
     check(load().thc_cpd_als_trajectory(
         o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)), _dev(Z, "Z", (Rt, Rt)),
         _ptr4(A, (o, v, o, v), R), _dev(lam, "lam", (R,)), int(sweeps),

@@ -88,21 +88,14 @@ thc_cpd_status check_prec(const thc_cpd_opts* opts) {
         return set_err(THC_CPD_ERR_ARG, "unknown precision %d", p);
     if (p != THC_CPD_FP64 && !mixed_supported())
         return set_err(THC_CPD_ERR_UNSUPPORTED, "split tensor-core precision needs an sm_103 device");
+    const int l = opts ? opts->ldl : THC_CPD_LDL_AUTO;
+    if (l != THC_CPD_LDL_AUTO && l != THC_CPD_LDL_BLOCKED && l != THC_CPD_LDL_DATAFLOW)
+        return set_err(THC_CPD_ERR_ARG, "unknown ldl variant %d", l);
     return THC_CPD_OK;
 }
 
 cudaStream_t stream_of(const thc_cpd_opts* o) {
     return o ? (cudaStream_t)o->stream : (cudaStream_t)0;
-}
-
-// The factorisation runs as one dataflow launch per solve unless THC_CPD_LDL=blocked
-// (one launch per block step, kept for comparison).
-bool ldl_dataflow() {
-    static const bool on = [] {
-        const char* e = getenv("THC_CPD_LDL");
-        return !(e && strcmp(e, "blocked") == 0);
-    }();
-    return on;
 }
 
 // Bounded device waits that gave up during this call (flags read and cleared; call after
@@ -141,6 +134,10 @@ struct Ctx {
     double* LinvD = nullptr;
     int* counters = nullptr;
     int* flow_sync = nullptr;
+    // Dataflow factorisation (one persistent launch per solve); flow_ctas > 0 caps its grid
+    // for the batched driver, where problems share the GPU.
+    bool dataflow = true;
+    int flow_ctas = 0;
     double* part = nullptr;
     size_t part_cap = 0;
     double* red = nullptr;
@@ -179,7 +176,10 @@ struct Ctx {
     }
 };
 
-enum : unsigned { NEED_ALS = 1, NEED_NORM = 2, NEED_SAFE = 4 };
+enum : unsigned { NEED_ALS = 1, NEED_NORM = 2, NEED_SAFE = 4, NEED_BATCHED = 8 };
+
+// grid cap of the dataflow factorisation when the batched driver is asked for it
+constexpr int kBatchedFlowCtas = 32;
 
 thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* Xv,
                         const double* Z, const thc_cpd_opts* opts, unsigned need) {
@@ -256,7 +256,10 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     }
     fill(c.st, c.ones, R, 1.0);
     // dataflow task lists (allocated and uploaded once per shape, never inside a capture)
-    if (ldl_dataflow()) {
+    const int ldl = opts ? opts->ldl : THC_CPD_LDL_AUTO;
+    c.dataflow = ldl == THC_CPD_LDL_DATAFLOW || (ldl == THC_CPD_LDL_AUTO && !(need & NEED_BATCHED));
+    c.flow_ctas = (need & NEED_BATCHED) ? kBatchedFlowCtas : 0;
+    if (c.dataflow) {
         flow_prepare(R, s.o);
         flow_prepare(R, s.v);
     }
@@ -361,7 +364,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
         CK(cudaMemcpyAsync(c.Haug, c.Hsave, sizeof(double) * R * R, cudaMemcpyDeviceToDevice, c.st));
     }
     chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * R, c.sc, k, c.counters,
-               ldl_dataflow() ? c.flow_sync : nullptr);
+               c.dataflow ? c.flow_sync : nullptr, c.flow_ctas);
     if (safe) {
         DevScalars* h = host_scalars();
         if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
@@ -844,7 +847,7 @@ thc_cpd_status run_batched(int np, thc_cpd_problem* P, int max_sweeps, double to
         thc_cpd_opts o2 = opts ? *opts : thc_cpd_opts{};
         o2.stream = r.streams[p];
         Ctx& c = *r.ctx[p];
-        CKS(ctx_init(c, shp[p], P[p].Xo, P[p].Xv, P[p].Z, &o2, NEED_ALS | NEED_NORM));
+        CKS(ctx_init(c, shp[p], P[p].Xo, P[p].Xv, P[p].Z, &o2, NEED_ALS | NEED_NORM | NEED_BATCHED));
         c.sc = r.dsc + p;
         c.sc_snap = r.dsc + np + p;
         double nG2;

@@ -29,8 +29,10 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   flow_sync: flow_sync_ints(R, n) ints, or null: with it (and a plan for (R, n)) the
 //   factorisation runs as one persistent dataflow launch (P is then R x R), else as one
 //   launch per block step.
+//   flow_ctas: 0 = the dataflow kernel takes one CTA per SM; > 0 = at most that many CTAs
+//   with only the shared memory they use (problems running side by side).
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode, int* counters, int* flow_sync);
+                DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas = 0);
 
 // Dataflow LDL^T (ldl_flow.cu): ints of progress state for R and n <= nmax; plan set-up
 // for (R, n) (false: too large or the task order failed its check; use the blocked path);
@@ -38,7 +40,7 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
 size_t flow_sync_ints(int R, int nmax);
 bool flow_prepare(int R, int n);
 cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
-                     DevScalars* sc, int mode, int* sync);
+                     DevScalars* sc, int mode, int* sync, int max_ctas = 0);
 int flow_take_error();
 
 // lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column); scratch >= R doubles.

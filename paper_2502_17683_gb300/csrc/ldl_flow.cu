@@ -57,7 +57,11 @@ constexpr int kFlowThreads = 128 * kGroups;
 constexpr int kFlowSmem = 120 * 1024;      // more than half an SM: one CTA per SM
 constexpr unsigned long long kWaitNs = 1000000000ull;
 constexpr int kSyncHead = 4;               // ticket, arrivals, fdone, abort
-constexpr int kMaxTiles = 256;             // larger R: the blocked factorisation
+constexpr int kMaxTiles = 256;             // largest schedule the host builds
+// Beyond 80 tiles (R > 1280) the solve is bound by FP64 throughput rather than by the
+// pivot chain, and the blocked factorisation's update launches keep the pipes busier
+// (3.25 vs 3.6 ms per solve at R = 1800), so it runs instead.
+constexpr int kFlowMaxTiles = 80;
 
 struct FlowTask {
     short type, t, j, k;                   // type 0: S(t, k); 1: U(t, j, k)
@@ -71,9 +75,15 @@ struct ChainSmem {
     double D[FB][FB + 1];    // diagonal tile being factorised
     double L[FB][FB + 1];
     double dinv[FB];
+    double Bn[2][FB][FB + 1];  // tile (s, s-1) for step s, buffer s & 1 (from the producer)
+    double Dn[2][FB][FB + 1];  // tile (s, s)
     unsigned short pairs[FB * (FB + 1) / 2];
     int bad;
     int ok;
+    int pstat;               // producer: inputs of its current step ready
+    volatile int valid[2];   // buffer holds complete tiles (0: the launch is aborting)
+    volatile int full[2];    // last step written to buffer b
+    volatile int empty[2];   // last step the chain has taken out of buffer b
 };
 
 struct WorkerSmem {
@@ -103,13 +113,24 @@ __device__ __forceinline__ void group_sync(int id) {
     asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
 }
 
-// *p >= v (true), or the launch is aborting / this wait gave up (false).
-__device__ bool flow_wait(const int* p, int v, int* abort_flag) {
-    if (ld_acquire(p) >= v) return true;
+// *p[i] >= v[i] for every i (true), or the launch is aborting / this wait gave up (false).
+// The counters are read together: one round trip per poll.
+template <int N>
+__device__ bool flow_wait(const int* const (&p)[N], const int (&v)[N], int* abort_flag) {
+    auto ready = [&]() {
+        int x[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = ld_acquire(p[i]);
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < N; ++i) ok = ok && x[i] >= v[i];
+        return ok;
+    };
+    if (ready()) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0;; ++it) {
         if (it > 8) __nanosleep(40);
-        if (ld_acquire(p) >= v) return true;
+        if (ready()) return true;
         if ((it & 31) == 31) {
             if (ld_acquire(abort_flag)) return false;
             if (global_ns() - t0 > kWaitNs) {
@@ -121,53 +142,78 @@ __device__ bool flow_wait(const int* p, int v, int* abort_flag) {
     }
 }
 
+// Barrier of the chain's compute threads 0..255 (the producer warps 8-15 run apart).
+__device__ __forceinline__ void chain_sync() { asm volatile("bar.sync 5, 256;" ::: "memory"); }
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 6, 256;" ::: "memory"); }
+
+// Bounded wait for a shared-memory step counter written by the other half of the chain
+// CTA: *p >= v (true), or the launch aborts / the wait gives up (false).
+__device__ bool smem_wait(const volatile int* p, int v, int* abort_flag) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; *p < v; ++it) {
+        if ((it & 63) == 63) {
+            if (ld_acquire(abort_flag)) return false;
+            if (global_ns() - t0 > kWaitNs) {
+                atomicExch(abort_flag, 1);
+                atomicExch(&g_flow_error, 1);
+                return false;
+            }
+        }
+    }
+    __threadfence_block();  // what was written before the flag is read after it
+    return true;
+}
+
 // LDL^T of the jb x jb tile in S.D (lower triangle) into S.L (strictly lower), S.D's
-// diagonal and S.dinv. Threads 0..127 compute, every thread of the CTA passes the
-// barriers: thread 0 carries the pivot chain one column ahead, warps 1-3 apply column c to
-// the rest of the tile over the packed pair list. A pivot <= tau sets S.bad and continues
-// with 1 (the caller then replays the mode with the pseudo-inverse).
+// diagonal and S.dinv. Threads 0..127 compute with a barrier of their own per column:
+// thread 0 carries the pivot chain one column ahead (pivot update and its reciprocal),
+// warps 1-3 apply column c to the rest of the tile over the packed pair list. A pivot
+// <= tau sets S.bad and continues with 1 (the caller then replays the mode with the
+// pseudo-inverse). Ends with a barrier of the chain's threads 0..255.
 __device__ void factor_tile(ChainSmem& S, int jb, double tau) {
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        S.bad = 0;
-        double d = S.D[0][0];
-        if (!pivot_ok(d, tau)) {
-            S.bad = 1;
-            d = 1.0;
-            S.D[0][0] = d;
-        }
-        S.dinv[0] = recip_nr(d);
-    }
-    for (int c = 0; c < jb; ++c) {
-        __syncthreads();  // dinv[c] and column c are final
-        const double inv = S.dinv[c];
+    if (tid < 128) {
         if (tid == 0) {
-            if (c + 1 < jb) {
-                const double x = S.D[c + 1][c];
-                const double l = x * inv;
-                double d1 = fma(-l, x, S.D[c + 1][c + 1]);
-                S.L[c + 1][c] = l;
-                if (!pivot_ok(d1, tau)) {
-                    S.bad = 1;
-                    d1 = 1.0;
-                }
-                S.D[c + 1][c + 1] = d1;
-                S.dinv[c + 1] = recip_nr(d1);
+            S.bad = 0;
+            double d = S.D[0][0];
+            if (!pivot_ok(d, tau)) {
+                S.bad = 1;
+                d = 1.0;
+                S.D[0][0] = d;
             }
-        } else if (tid >= 32 && tid < 128) {
-            const int hi = FB - 1 - c;
-            const int npair = hi * (hi + 1) / 2;
-            for (int e = tid - 32; e < npair; e += 96) {
-                const int rs = S.pairs[e];
-                const int r = rs >> 8, ss = rs & 0xFF;
-                if (r >= jb || (r == c + 1 && ss == c + 1)) continue;
-                const double l = S.D[r][c] * inv;
-                if (ss == c + 1) S.L[r][c] = l;
-                S.D[r][ss] = fma(-l, S.D[ss][c], S.D[r][ss]);
+            S.dinv[0] = recip_nr(d);
+        }
+        for (int c = 0; c < jb; ++c) {
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // dinv[c] and column c are final
+            const double inv = S.dinv[c];
+            if (tid == 0) {
+                if (c + 1 < jb) {
+                    const double x = S.D[c + 1][c];
+                    const double l = x * inv;
+                    double d1 = fma(-l, x, S.D[c + 1][c + 1]);
+                    S.L[c + 1][c] = l;
+                    if (!pivot_ok(d1, tau)) {
+                        S.bad = 1;
+                        d1 = 1.0;
+                    }
+                    S.D[c + 1][c + 1] = d1;
+                    S.dinv[c + 1] = recip_nr(d1);
+                }
+            } else if (tid >= 32) {
+                const int hi = FB - 1 - c;
+                const int npair = hi * (hi + 1) / 2;
+                for (int e = tid - 32; e < npair; e += 96) {
+                    const int rs = S.pairs[e];
+                    const int r = rs >> 8, ss = rs & 0xFF;
+                    if (r >= jb || (r == c + 1 && ss == c + 1)) continue;
+                    const double l = S.D[r][c] * inv;
+                    if (ss == c + 1) S.L[r][c] = l;
+                    S.D[r][ss] = fma(-l, S.D[ss][c], S.D[r][ss]);
+                }
             }
         }
     }
-    __syncthreads();
+    chain_sync();
 }
 
 struct FlowArgs {
@@ -187,57 +233,84 @@ __device__ __forceinline__ int* cnt_of(const FlowArgs& a) {
     return a.sync + kSyncHead + a.nT + a.nM;
 }
 
-// The critical path: for s = 0..T-1, S(s, s-1), U(s, s, s-1), F(s).
+// Producer half of the chain CTA (warps 8-15): for steps s = 1..T-1, waits until tiles
+// (s, s-1) and (s, s) hold all updates through panel s-2, copies them into buffer s & 1 and
+// flags it, so the chain finds them in shared memory; a buffer is reused once the chain
+// has taken its previous content out.
+__device__ void flow_producer(const FlowArgs& a, ChainSmem& S) {
+    const int t2 = threadIdx.x - 256, R = a.R, nT = a.nT;
+    int* abort_flag = a.sync + 3;
+    int* cnt = cnt_of(a);
+    const int rr = t2 >> 4, cc = t2 & 15;
+    for (int sn = 1; sn < nT; ++sn) {
+        const int b = sn & 1;
+        if (t2 == 0) {
+            bool ok = sn < 3 || smem_wait(&S.empty[b], sn - 2, abort_flag);
+            if (ok) {
+                const int* const pc[2] = {&cnt[sn * nT + sn - 1], &cnt[sn * nT + sn]};
+                const int vc[2] = {sn - 1, sn - 1};
+                ok = flow_wait(pc, vc, abort_flag);
+            }
+            S.pstat = ok;
+        }
+        producer_sync();
+        const bool ok = S.pstat;
+        if (ok) {
+            const int n0 = sn * FB, nb = min(FB, R - n0);
+            S.Bn[b][rr][cc] = rr < nb ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 - FB + cc) : 0.0;
+            S.Dn[b][rr][cc] =
+                (rr < nb && cc <= rr) ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 + cc) : 0.0;
+        }
+        producer_sync();
+        if (t2 == 0) {
+            S.valid[b] = ok;
+            __threadfence_block();
+            S.full[b] = sn;
+        }
+        if (!ok) break;
+    }
+}
+
+// The critical path (threads 0..255): for s = 0..T-1, S(s, s-1), U(s, s, s-1), F(s).
 __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
     const int tid = threadIdx.x, R = a.R, nT = a.nT;
     int* fdone = a.sync + 2;
     int* abort_flag = a.sync + 3;
     int* sdone = sdone_of(a);
-    int* cnt = cnt_of(a);
     const double tau = (double)R * DBL_EPSILON * a.sc->maxdiag;
-    for (int e = tid; e < FB * (FB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code<FB>(e);
-    if (tid < FB * FB) S.L[tid >> 4][tid & 15] = 0.0;
-    const int r = (tid >> 4) & 15, c = tid & 15;  // element of a tile (threads 0..255)
-    const bool el = tid < FB * FB;
+    const int r = tid >> 4, c = tid & 15;  // element of a tile
     int bad = 0;
     for (int s = 0; s < nT; ++s) {
-        const int s0 = s * FB, sb = min(FB, R - s0);
-        if (tid == 0) {
-            bool ok = true;
-            if (s >= 1)
-                ok = flow_wait(&cnt[s * nT + s - 1], s - 1, abort_flag) &&
-                     flow_wait(&cnt[s * nT + s], s - 1, abort_flag);
-            S.ok = ok;
-        }
-        __syncthreads();
-        if (!S.ok) break;
-        double dss = 0.0, b = 0.0;
-        if (el && r < sb) {
-            if (c <= r) dss = __ldcg(a.H + (size_t)(s0 + r) * R + s0 + c);
-            if (s >= 1) b = __ldcg(a.H + (size_t)(s0 + r) * R + s0 - FB + c);
-        }
-        if (s >= 1) {
-            if (el) {
-                // X L_{s-1}^T = B: column sweep, x[r][q] passed along the row's half-warp
+        const int s0 = s * FB, sb = min(FB, R - s0), b = s & 1;
+        double dss = 0.0, x = 0.0;
+        if (s == 0) {
+            if (r < sb && c <= r) dss = __ldcg(a.H + (size_t)r * R + c);
+        } else {
+            if (tid == 0) S.ok = smem_wait(&S.full[b], s, abort_flag) && S.valid[b];
+            chain_sync();
+            if (!S.ok) break;
+            dss = S.Dn[b][r][c];
+            x = S.Bn[b][r][c];
+            // X L_{s-1}^T = B: column sweep, x[r][q] passed along the row's half-warp
 #pragma unroll
-                for (int q = 0; q < FB - 1; ++q) {
-                    const double xq = __shfl_sync(0xffffffffu, b, (tid & 16) | q);
-                    if (c > q) b = fma(-xq, S.Lp[c][q], b);
-                }
-                const double l = b * S.dp[c];
-                if (r < sb) {
-                    a.H[(size_t)(s0 + r) * R + s0 - FB + c] = l;
-                    a.P[(size_t)(s0 + r) * R + s0 - FB + c] = b;
-                }
-                S.Xs[r][c] = b;
-                S.Ls[r][c] = l;
+            for (int q = 0; q < FB - 1; ++q) {
+                const double xq = __shfl_sync(0xffffffffu, x, (tid & 16) | q);
+                if (c > q) x = fma(-xq, S.Lp[c][q], x);
             }
-            __syncthreads();
+            const double l = x * S.dp[c];
+            if (r < sb) {
+                a.H[(size_t)(s0 + r) * R + s0 - FB + c] = l;
+                a.P[(size_t)(s0 + r) * R + s0 - FB + c] = x;
+            }
+            S.Xs[r][c] = x;
+            S.Ls[r][c] = l;
+            chain_sync();
             if (tid == 0) {
+                S.empty[b] = s;  // buffer b read out (before the barrier above)
                 __threadfence();
                 st_release(&sdone[s], s);
             }
-            if (el && c <= r) {
+            if (c <= r) {
                 double a0 = 0.0, a1 = 0.0;
 #pragma unroll
                 for (int q = 0; q < FB; q += 2) {
@@ -247,16 +320,16 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
                 dss -= (a0 + a1);
             }
         }
-        if (el) S.D[r][c] = dss;
-        __syncthreads();
+        S.D[r][c] = dss;
+        chain_sync();
         factor_tile(S, sb, tau);
-        if (el && r < sb && c <= r)
+        if (r < sb && c <= r)
             a.H[(size_t)(s0 + r) * R + s0 + c] = (c < r) ? S.L[r][c] : S.D[r][r];
         if (tid < sb) a.dinv[s0 + tid] = S.dinv[tid];
-        if (el) S.Lp[r][c] = (c < r && r < sb) ? S.L[r][c] : 0.0;
+        S.Lp[r][c] = (c < r && r < sb) ? S.L[r][c] : 0.0;
         if (tid < FB) S.dp[tid] = tid < sb ? S.dinv[tid] : 0.0;
         bad |= S.bad;
-        __syncthreads();
+        chain_sync();
         if (tid == 0) {
             __threadfence();
             st_release(fdone, s + 1);
@@ -280,9 +353,11 @@ __device__ __forceinline__ void tile_rows(const FlowArgs& a, int t, int& r0, int
 __device__ void task_S(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t, int k) {
     const int R = a.R;
     int* sdone = sdone_of(a);
-    if (gt == 0)
-        W.ok = flow_wait(a.sync + 2, k + 1, a.sync + 3) &&
-               flow_wait(&cnt_of(a)[t * a.nT + k], k, a.sync + 3);
+    if (gt == 0) {
+        const int* const pc[2] = {a.sync + 2, &cnt_of(a)[t * a.nT + k]};
+        const int vc[2] = {k + 1, k};
+        W.ok = flow_wait(pc, vc, a.sync + 3);
+    }
     group_sync(bar);
     if (!W.ok) return;
     int r0, rlim;
@@ -329,9 +404,11 @@ __device__ void task_U(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
     const int R = a.R;
     int* sdone = sdone_of(a);
     int* cnt = cnt_of(a);
-    if (gt == 0)
-        W.ok = flow_wait(&sdone[t], k + 1, a.sync + 3) && flow_wait(&sdone[j], k + 1, a.sync + 3) &&
-               flow_wait(&cnt[t * a.nT + j], k, a.sync + 3);
+    if (gt == 0) {
+        const int* const pc[3] = {&sdone[t], &sdone[j], &cnt[t * a.nT + j]};
+        const int vc[3] = {k + 1, k + 1, k};
+        W.ok = flow_wait(pc, vc, a.sync + 3);
+    }
     group_sync(bar);
     if (!W.ok) return;
     int r0, rlim;
@@ -371,16 +448,22 @@ __device__ void task_U(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
 __device__ void flow_worker(const FlowArgs& a, WorkerSmem* ws) {
     const int g = threadIdx.x >> 7, gt = threadIdx.x & 127, bar = 1 + g;
     WorkerSmem& W = ws[g];
+    if (gt == 0) W.ticket = atomicAdd(a.sync, 1);
+    group_sync(bar);
     for (;;) {
-        if (gt == 0) W.ticket = atomicAdd(a.sync, 1);
-        group_sync(bar);
         const int ti = W.ticket;
         if (ti >= a.ntasks) break;
+        // claim the next ticket while this one runs (holding one in reserve keeps the
+        // lowest unfinished ticket runnable: a group works on its lower ticket first)
+        int nxt = 0;
+        if (gt == 0) nxt = atomicAdd(a.sync, 1);
         const FlowTask tk = a.tasks[ti];
         if (tk.type == 0)
             task_S(a, W, gt, bar, tk.t, tk.k);
         else
             task_U(a, W, gt, bar, tk.t, tk.j, tk.k);
+        if (gt == 0) W.ticket = nxt;
+        group_sync(bar);
     }
 }
 
@@ -389,38 +472,62 @@ __global__ void __launch_bounds__(kFlowThreads, 1) k_ldl_flow(FlowArgs a) {
     __shared__ int role;
     if (threadIdx.x == 0) role = atomicAdd(a.sync + 1, 1);
     __syncthreads();
-    if (role == 0)
-        flow_chain(a, *reinterpret_cast<ChainSmem*>(smem));
-    else
+    if (role == 0) {
+        ChainSmem& S = *reinterpret_cast<ChainSmem*>(smem);
+        for (int e = threadIdx.x; e < FB * (FB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code<FB>(e);
+        if (threadIdx.x < FB * FB) S.L[threadIdx.x >> 4][threadIdx.x & 15] = 0.0;
+        if (threadIdx.x < 2) {
+            S.full[threadIdx.x] = 0;
+            S.empty[threadIdx.x] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x < 256)
+            flow_chain(a, S);
+        else
+            flow_producer(a, S);
+    } else {
         flow_worker(a, reinterpret_cast<WorkerSmem*>(smem));
+    }
 }
 
+constexpr size_t kFlowSmemUsed = sizeof(ChainSmem) > kGroups * sizeof(WorkerSmem)
+                                     ? sizeof(ChainSmem)
+                                     : kGroups * sizeof(WorkerSmem);
 static_assert(sizeof(ChainSmem) <= kFlowSmem, "chain shared memory");
 static_assert(kGroups * sizeof(WorkerSmem) <= kFlowSmem, "worker shared memory");
 
 // ---- host: the task list ---------------------------------------------------------------
-// Ticket order: panel by panel (right-looking), so that the updates of a tile arrive one
-// panel period apart instead of queueing up behind each other; within panel k the
-// substitutions first (row tile ascending: S(k+2, k) feeds the chain two steps ahead),
-// then the updates by column tile (column k+1 first: the chain's next input), rows of H
-// before rows of M.
+// Ticket order: a diagonal wavefront. S(t, k) sorts at 2k + 1 and U(t, j, k) at j + k, so
+// the updates near the diagonal (which the chain needs first) come early and those of
+// far columns later, while consecutive updates of one tile stay one position apart (they
+// never pile up behind each other). Ties: substitutions first, rows of H before rows of M,
+// then panel, column, row. Every task sorts after the tasks it waits for (the check below
+// confirms it): a U task's inputs S(t, k), S(j, k) sort at 2k + 1 <= j + k and its previous
+// update at j + k - 1; the chain's inputs for step s sort at most at 2s - 2, below the
+// tasks that wait for that step (2s + 1 and up).
 bool build_tasks(int R, int n, std::vector<FlowTask>& out, int& nT, int& nM) {
     nT = cdiv(R, FB);
     nM = cdiv(n, FB);
     const int nRT = nT + nM;
-    std::vector<FlowTask> it;  // generated in ticket order
+    std::vector<FlowTask> it;
     auto push = [&](int type, int t, int j, int k) {
         it.push_back(FlowTask{(short)type, (short)t, (short)j, (short)k});
     };
     for (int k = 0; k < nT; ++k) {
         for (int t = k + 2; t < nT; ++t) push(0, t, 0, k);
         for (int t = nT; t < nRT; ++t) push(0, t, 0, k);
-        for (int j = k + 1; j < nT; ++j)
+        for (int j = k + 1; j < nT; ++j) {
             for (int t = j; t < nT; ++t)
                 if (!(t == j && j == k + 1)) push(1, t, j, k);
-        for (int j = k + 1; j < nT; ++j)
             for (int t = nT; t < nRT; ++t) push(1, t, j, k);
+        }
     }
+    auto key = [&](const FlowTask& x) {
+        const int tau = x.type == 0 ? 2 * x.k + 1 : x.j + x.k;
+        return std::make_tuple(tau, (int)x.type, x.t >= nT ? 1 : 0, (int)x.k, (int)x.j, (int)x.t);
+    };
+    std::stable_sort(it.begin(), it.end(),
+                     [&](const FlowTask& x, const FlowTask& y) { return key(x) < key(y); });
     if (it.size() >= 0x7fffffff) return false;
     // index of every ticket task, -1 for chain tasks or tasks that do not exist
     std::vector<int> sidx((size_t)nRT * nT, -1), uidx((size_t)nRT * nT * nT, -1);
@@ -499,7 +606,7 @@ const Plan* get_plan(int R, int n) {
     auto f = g_plans.find(key);
     if (f != g_plans.end()) return f->second.ok ? &f->second : nullptr;
     Plan& p = g_plans[key];
-    if (cdiv(R, FB) > kMaxTiles || cdiv(n, FB) > kMaxTiles) return nullptr;
+    if (cdiv(R, FB) > kFlowMaxTiles || cdiv(n, FB) > kMaxTiles) return nullptr;
     std::vector<FlowTask> h;
     if (!build_tasks(R, n, h, p.nT, p.nM)) return nullptr;
     p.ntasks = (int)h.size();
@@ -531,14 +638,18 @@ size_t flow_sync_ints(int R, int nmax) {
 bool flow_prepare(int R, int n) { return get_plan(R, n) != nullptr; }
 
 cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
-                     DevScalars* sc, int mode, int* sync) {
+                     DevScalars* sc, int mode, int* sync, int max_ctas) {
     const Plan* p = get_plan(R, n);
     if (!p) return cudaErrorInvalidValue;
     const size_t nsync = kSyncHead + (size_t)(p->nT + p->nM) * (1 + p->nT);
     cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * nsync, st);
     if (e != cudaSuccess) return e;
     FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, p->tasks, p->ntasks, sync, sc, mode};
-    k_ldl_flow<<<p->grid, kFlowThreads, kFlowSmem, st>>>(a);
+    // alone on the GPU: one CTA per SM (the chain's SM is not shared); next to other
+    // problems (max_ctas > 0): a few CTAs with just the shared memory they use
+    const int grid = max_ctas > 0 ? std::max(2, std::min(p->grid, max_ctas)) : p->grid;
+    const int smem = max_ctas > 0 ? (int)kFlowSmemUsed : kFlowSmem;
+    k_ldl_flow<<<grid, kFlowThreads, smem, st>>>(a);
     count_launch();
     return cudaGetLastError();
 }

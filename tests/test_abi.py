@@ -44,10 +44,11 @@ def test_version(lib):
     assert b"sm_103a" in lib.thc_cpd_version()
 
 
-def _call_mttkrp(lib, o, v, Rt, R, mode, ptr=1, Aptrs=(1, 1, 1, 1), M=1, prec=0):
+def _call_mttkrp(lib, o, v, Rt, R, mode, ptr=1, Aptrs=(1, 1, 1, 1), M=1, prec=0, ldl=0):
     from paper_2502_17683_gb300._lib import PTR4, Opts
     opts = Opts()
     opts.precision = prec
+    opts.ldl = ldl
     return lib.thc_cpd_mttkrp(o, v, Rt, R, ptr, ptr, ptr, PTR4(*Aptrs), mode, M, ctypes.byref(opts))
 
 
@@ -63,6 +64,8 @@ def test_argument_validation_happens_before_device_work(lib):
     assert _call_mttkrp(lib, 5, 5, 5, 5, 0, M=None) == _lib.ERR_ARG
     assert _call_mttkrp(lib, 5, 5, 5, 5, 0, prec=9) == _lib.ERR_ARG
     assert b"mode" in lib.thc_cpd_last_error() or b"precision" in lib.thc_cpd_last_error()
+    assert _call_mttkrp(lib, 5, 5, 5, 5, 0, ldl=3) == _lib.ERR_ARG
+    assert b"ldl" in lib.thc_cpd_last_error()
     out = ctypes.c_double()
     assert lib.thc_cpd_thc_norm2(3, 4, 5, None, 1, 1, ctypes.byref(out), None) == _lib.ERR_ARG
     assert lib.thc_cpd_thc_norm2(3, 4, 5, 1, 1, 1, None, None) == _lib.ERR_ARG

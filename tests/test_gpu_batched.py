@@ -38,7 +38,9 @@ def test_batched_equals_single_problem_runs(api, prec):
     solo = _problems(shapes, 100)
     res = api.thc_cpd_als_batched(batch, 8, 0.0, precision=prec)
     for b, s_, r in zip(batch, solo, res):
-        out = api.thc_cpd_als(s_["Xo"], s_["Xv"], s_["Z"], s_["A"], s_["lam"], 8, 0.0, precision=prec)
+        # the batched driver factorises with the blocked LDL^T; so does this reference run
+        out = api.thc_cpd_als(s_["Xo"], s_["Xv"], s_["Z"], s_["A"], s_["lam"], 8, 0.0, precision=prec,
+                              ldl="blocked")
         assert r["sweeps"] == out["sweeps"] == 8
         assert r["fit"] == out["fit"]  # same kernels in the same order: same bits
         for a, c in zip(b["A"], s_["A"]):

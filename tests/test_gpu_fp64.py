@@ -84,14 +84,16 @@ def test_one_sweep_identical_inputs(api, shape):
     assert rel(got, ref) <= 1e-9
 
 
+@pytest.mark.parametrize("ldl", ["dataflow", "blocked"])
 @pytest.mark.parametrize("name,shape,sweeps", [("c1", (5, 15, 60, 80), 25),
                                                ("c2", (20, 100, 480, 720), 50)])
-def test_trajectory(api, name, shape, sweeps):
+def test_trajectory(api, name, shape, sweeps, ldl):
     o, v, Rt, R = shape
     p = make_problem(o, v, Rt, R, seed=0, decay=Rt / 5)
     d = to_dev(p, torch)
     lam = torch.ones(R, dtype=torch.float64, device="cuda")
-    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, sweeps, 0.0, history=True)
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, sweeps, 0.0, history=True,
+                          ldl=ldl)
     ref = O.als(p.Xo, p.Xv, p.Z, p.A, sweeps)
     assert out["sweeps"] == sweeps
     fits = np.array(out["fits"])
@@ -127,17 +129,19 @@ def test_planted_recovery_gpu(api):
     assert relerr < 1e-10
 
 
-def test_pinv_fallback_rollback(api):
+@pytest.mark.parametrize("ldl,R", [("dataflow", 6), ("blocked", 6), ("dataflow", 40)])
+def test_pinv_fallback_rollback(api, ldl, R):
     # two identical columns in every start factor make each H singular: the optimistic
-    # sweep fails its Cholesky, is rolled back, and is replayed with the pseudo-inverse
-    p = make_problem(4, 9, 20, 6, seed=6)
+    # sweep fails its LDL^T pivot test, is rolled back, and is replayed with the
+    # pseudo-inverse (R = 40: the failing pivot sits in the dataflow kernel's third tile)
+    p = make_problem(4, 9, 20, R, seed=6)
     A = [a.copy() for a in p.A]
     for a in A:
-        a[:, 5] = a[:, 4]
+        a[:, R - 1] = a[:, R - 2]
     d = to_dev(p, torch)
     d["A"] = [torch.from_numpy(a).cuda() for a in A]
-    lam = torch.ones(6, dtype=torch.float64, device="cuda")
-    out = api.thc_cpd_als_sweep(d["Xo"], d["Xv"], d["Z"], d["A"], lam)
+    lam = torch.ones(R, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als_sweep(d["Xo"], d["Xv"], d["Z"], d["A"], lam, ldl=ldl)
     A_ref, lam_ref, loss_ref, fit_ref, flags = O.als_sweep(p.Xo, p.Xv, p.Z, tuple(A))
     assert flags[0] and (out["flags"] & 1) and (out["flags"] & 2)
     nG2 = O.thc_norm2(p.Xo, p.Xv, p.Z)
@@ -171,3 +175,30 @@ def test_graph_replay_is_bit_identical_to_direct_launches(api, prec, monkeypatch
     for a, b in zip(outs[0][1], outs[1][1]):
         assert np.array_equal(a, b)
     assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_dataflow_and_blocked_ldl_agree_and_reproduce(api):
+    # the two factorisations run the same LDL^T in different rounding orders; each is
+    # bit-reproducible (tiles get their updates in a fixed order, whatever the schedule)
+    p = make_problem(20, 100, 480, 720, seed=9)
+    runs = {}
+    for ldl in ("dataflow", "dataflow", "blocked"):
+        d = to_dev(p, torch)
+        lam = torch.ones(720, dtype=torch.float64, device="cuda")
+        out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 5, 0.0, ldl=ldl)
+        runs.setdefault(ldl, []).append((out["fit"], [a.cpu().numpy() for a in d["A"]]))
+    (f0, A0), (f1, A1) = runs["dataflow"]
+    assert f0 == f1 and all(np.array_equal(a, b) for a, b in zip(A0, A1))
+    fb, Ab = runs["blocked"][0]
+    assert abs(f0 - fb) <= 1e-12
+    for a, b in zip(A0, Ab):
+        assert rel(a, b) <= 1e-8
+
+
+def test_unknown_ldl_variant_rejected(api):
+    from paper_2502_17683_gb300._lib import ThcCpdError
+    p = make_problem(3, 4, 5, 6, seed=7)
+    d = to_dev(p, torch)
+    lam = torch.ones(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(ThcCpdError):
+        api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 1, ldl="cholesky")

@@ -71,6 +71,31 @@ def peaks():
 # nominal dense rates (TFLOP/s) used to carry the measured bf16 peak over to other dtypes
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 
+# The LDL^T and the FP64 GEMMs run on the FP64 FMA units, not on the tensor cores: their
+# roofline is 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz (the maximum SM clock)
+# = 1.259 TFLOP/s, the part's nominal 1.25 TFLOP/s.
+FP64_ALU_PEAK = 152 * 2 * 2 * 2070e6 / 1e12
+
+# DRAM bytes per launch of the dataflow LDL^T kernel, from one ncu capture of one sweep of
+# the default workload (the four modes' launches averaged; ncu starts every launch from a
+# flushed cache, so this is the cold-cache figure), and the SHA-256 of the kernel source it
+# was taken on: reported only while that source is unchanged.
+LDL_TRAFFIC = {"bytes_per_launch": 2723936,
+               "sha256": "1ae90fe65788e6f5ae2cb010015e591bf42d0f87229c0b5a705cb7f58ec8f853",
+               "source": os.path.join("paper_2502_17683_gb300", "csrc", "ldl_flow.cu")}
+
+
+def ldl_traffic():
+    import hashlib
+    if not LDL_TRAFFIC["bytes_per_launch"]:
+        return None
+    try:
+        with open(os.path.join(ROOT, LDL_TRAFFIC["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return LDL_TRAFFIC["bytes_per_launch"] if sha == LDL_TRAFFIC["sha256"] else None
+
 
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -407,6 +432,8 @@ def main():
 
     # ---- roofline: per-kernel-class CUDA events over one more profiled step ----
     pk, pk_kind = peaks()
+    # the factorisation a single problem gets (thc_cpd_opts.ldl = auto): dataflow up to R = 1280
+    ldl_path = "dataflow" if W["R"] <= 1280 else "blocked"
     reset()
     api.thc_cpd_profile(True)
     step()
@@ -416,18 +443,25 @@ def main():
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     achieved = d["flops"] / (d["ms"] / 1000.0) / 1e12 if d["ms"] > 0 else 0.0
+    # the LDL^T is one launch per solve on the dataflow path; per launch = per solve
+    kernel = {"cholesky": "k_ldl_flow (LDL^T + forward solve, one launch per mode)"
+              if ldl_path == "dataflow" else "blocked LDL^T launches (per mode)",
+              "backward_solve": "k_bsolve_rows", "fp64_gemm": "k_dgemm",
+              "tc_gemm": "k_tc_gemm", "elementwise": "element-wise kernels"}[dom]
+    traffic = None
     if dom == "tc_gemm":
-        peak = pk["bf16_tflops_sustained"]
+        bound, peak = "tensor", pk["bf16_tflops_sustained"]
         note = "bf16 sustained, " + pk_kind
     elif dom == "elementwise":
-        peak = None
-        note = pk_kind
+        bound, peak, note = "hbm", None, pk_kind
     else:
-        peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-        note = f"{pk_kind} bf16 burst x nominal fp64/bf16 ratio"
-    roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak,
+        bound, peak = "alu", FP64_ALU_PEAK
+        note = "FP64 FMA units: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (nominal 1.25 TF)"
+        if dom == "cholesky" and ldl_path == "dataflow":
+            traffic = ldl_traffic()
+    roofline = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
-                "traffic": None, "peak_source": note,
+                "traffic": traffic, "peak_source": note,
                 "classes_ms_per_step": {k: round(v["ms"], 3) for k, v in prof.items()}}
     tc = prof.get("tc_gemm", {"ms": 0.0})
     if tc["ms"] > 0:
@@ -448,6 +482,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "o": W["o"], "v": W["v"], "R_thc": W["Rt"],
                    "R_cp": W["R"], "sweeps_per_step": W["sweeps"], "precision": precision,
+                   "ldl": ldl_path,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "fit": fit,
         "clocks": clk.summary(),

@@ -134,6 +134,7 @@ struct Ctx {
     double* LinvD = nullptr;
     int* counters = nullptr;
     int* flow_sync = nullptr;
+    int* bs_sync = nullptr;
     // Dataflow factorisation (one persistent launch per solve); flow_ctas > 0 caps its grid
     // for the batched driver, where problems share the GPU.
     bool dataflow = true;
@@ -213,6 +214,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     bytes += Arena::need<double>(RR + R);                  // X = L D and D^{-1}
     bytes += Arena::need<int>(cdiv(R, 32));               // arrival counters of the LDL^T
     bytes += Arena::need<int>(flow_sync_ints(R, nmax));   // dataflow LDL^T progress
+    bytes += Arena::need<int>(bsolve_sync_ints(nmax));    // sliced backward solve progress
     bytes += Arena::need<double>(pc);
     bytes += Arena::need<double>(loss_red_need() + 2 * kNumSM * 2);
     bytes += Arena::need<double>(R);
@@ -236,6 +238,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     c.LinvD = ar.take<double>(RR + R);
     c.counters = ar.take<int>(cdiv(R, 32));
     c.flow_sync = ar.take<int>(flow_sync_ints(R, nmax));
+    c.bs_sync = ar.take<int>(bsolve_sync_ints(nmax));
     c.part = ar.take<double>(pc);
     c.red = ar.take<double>(loss_red_need() + 2 * kNumSM * 2);
     c.ones = ar.take<double>(R);
@@ -364,7 +367,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
         CK(cudaMemcpyAsync(c.Haug, c.Hsave, sizeof(double) * R * R, cudaMemcpyDeviceToDevice, c.st));
     }
     chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * R, c.sc, k, c.counters,
-               c.dataflow ? c.flow_sync : nullptr, c.flow_ctas);
+               c.dataflow ? c.flow_sync : nullptr, c.flow_ctas, c.bs_sync);
     if (safe) {
         DevScalars* h = host_scalars();
         if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");

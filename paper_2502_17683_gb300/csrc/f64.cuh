@@ -31,8 +31,11 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   launch per block step.
 //   flow_ctas: 0 = the dataflow kernel takes one CTA per SM; > 0 = at most that many CTAs
 //   with only the shared memory they use (problems running side by side).
+//   bs_sync: bsolve_sync_ints(n) ints for the sliced backward solve, or null for one CTA
+//   per row.
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas = 0);
+                DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas = 0,
+                int* bs_sync = nullptr);
 
 // Dataflow LDL^T (ldl_flow.cu): ints of progress state for R and n <= nmax; plan set-up
 // for (R, n) (false: too large or the task order failed its check; use the blocked path);
@@ -42,6 +45,12 @@ bool flow_prepare(int R, int n);
 cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
                      DevScalars* sc, int mode, int* sync, int max_ctas = 0);
 int flow_take_error();
+
+// Backward solve A L = Y (unit lower L in the strictly-lower part of H, R x R; Y and A n x R)
+// by column slices claimed from a ticket (ldl_flow.cu); sync: bsolve_sync_ints(n) ints.
+size_t bsolve_sync_ints(int nmax);
+cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, double* A,
+                          const double* H, int* sync);
 
 // lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column); scratch >= R doubles.
 void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch);

@@ -610,7 +610,8 @@ k_bsolve_rows(const double* __restrict__ Yf, double* __restrict__ A, int R,
 size_t bsolve_smem_bytes(int R) { return sizeof(BsolveSmem) + sizeof(double) * (size_t)R; }
 
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas) {
+                DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
+                int* bs_sync) {
     const int nrows = R + n;
     const int nJ = cdiv(R, NB);
     if (flow_sync && flow_prepare(R, n)) {
@@ -640,6 +641,10 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
     if (n <= 0) return;
     ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
     double* Yf = Haug + (size_t)R * R;
+    if (bs_sync) {
+        bsolve_slices(st, R, n, Yf, A, Haug, bs_sync);
+        return;
+    }
     const size_t smem = bsolve_smem_bytes(R);
     if (smem <= kBsolveSmemMax) {  // else (R above ~20000): one launch per block
         static bool attr = false;

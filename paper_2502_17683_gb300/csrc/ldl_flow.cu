@@ -142,6 +142,8 @@ __device__ bool flow_wait(const int* const (&p)[N], const int (&v)[N], int* abor
     }
 }
 
+constexpr int kPublisher = 224;  // chain thread that fences and releases the progress flags
+
 // Barrier of the chain's compute threads 0..255 (the producer warps 8-15 run apart).
 __device__ __forceinline__ void chain_sync() { asm volatile("bar.sync 5, 256;" ::: "memory"); }
 __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 6, 256;" ::: "memory"); }
@@ -305,7 +307,9 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
             S.Xs[r][c] = x;
             S.Ls[r][c] = l;
             chain_sync();
-            if (tid == 0) {
+            // published by a thread of warp 7 (idle in the tile factorisation), so that the
+            // fence does not hold up thread 0's pivot chain
+            if (tid == kPublisher) {
                 S.empty[b] = s;  // buffer b read out (before the barrier above)
                 __threadfence();
                 st_release(&sdone[s], s);
@@ -330,12 +334,12 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
         if (tid < FB) S.dp[tid] = tid < sb ? S.dinv[tid] : 0.0;
         bad |= S.bad;
         chain_sync();
-        if (tid == 0) {
+        if (tid == kPublisher) {
             __threadfence();
             st_release(fdone, s + 1);
         }
     }
-    if (tid == 0 && bad) atomicOr(&a.sc->fail_mask, 1 << a.mode);
+    if (tid == kPublisher && bad) atomicOr(&a.sc->fail_mask, 1 << a.mode);
 }
 
 // Rows of row tile t: [r0, rlim) with r0 = first row (H rows, then M rows).
@@ -496,6 +500,128 @@ constexpr size_t kFlowSmemUsed = sizeof(ChainSmem) > kGroups * sizeof(WorkerSmem
 static_assert(sizeof(ChainSmem) <= kFlowSmem, "chain shared memory");
 static_assert(kGroups * sizeof(WorkerSmem) <= kFlowSmem, "worker shared memory");
 
+// ---- backward solve A L = Y by column slices -------------------------------------------
+// Row r of A: a_J = (y_J - sum_{K > J} a_K L_{K,J}) L_JJ^-1 over 32-column blocks J from the
+// last to the first (unit lower L). Work item = (row, slice of 4 blocks); each of the 128
+// threads owns one column of the slice (its y in a register) and the warp that owns block J
+// runs that block's substitution. An item first applies the a_K of all higher blocks as the
+// items above publish them (per-row counter prog[r] = blocks solved from the top), then
+// solves its own blocks and publishes each. Items are claimed highest slice first, so an item
+// only waits for items claimed before it: progress for any number of resident CTAs. Each
+// row's work (R^2 / 2 FMA) is spread over R / 128 SMs instead of one.
+constexpr int BB = 32;
+constexpr int kSliceBlocks = 4;
+constexpr int kSlice = BB * kSliceBlocks;
+constexpr int kBsThreads = kSlice;
+
+struct BsArgs {
+    const double* Yf;
+    double* A;
+    const double* H;
+    int R, n, nJ, C;
+    int* sync;  // [0] ticket, [1] abort, [2 + r] prog of row r
+};
+
+// 32-term dot product in four independent FMA chains (fixed order)
+__device__ __forceinline__ double dot32(const double* x, const double* h) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+    for (int k = 0; k < BB; k += 4) {
+        s0 = fma(x[k], h[k], s0);
+        s1 = fma(x[k + 1], h[k + 1], s1);
+        s2 = fma(x[k + 2], h[k + 2], s2);
+        s3 = fma(x[k + 3], h[k + 3], s3);
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+__global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
+    __shared__ double as[2][BB];
+    __shared__ int tk, kmin, ok;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, R = a.R;
+    int* abort_flag = a.sync + 1;
+    int* prog = a.sync + 2;
+    for (;;) {
+        if (tid == 0) tk = atomicAdd(a.sync, 1);
+        __syncthreads();
+        const int t = tk;
+        if (t >= a.n * a.C) break;
+        const int c = a.C - 1 - t / a.n, r = t % a.n;  // highest slices first
+        const int cs = c * kSlice, ce = min(R, cs + kSlice);
+        const int Jlo = c * kSliceBlocks, Jhi = min(a.nJ, Jlo + kSliceBlocks);
+        const int q = cs + tid;  // this thread's column
+        const bool qv = q < ce;
+        double y = qv ? a.Yf[(size_t)r * R + q] : 0.0;
+        // this warp's diagonal block (if it owns one): column `lane` of L_JJ, in registers
+        const int Jw = Jlo + w, c0w = Jw * BB, jbw = min(BB, R - c0w);
+        double lc[BB];
+#pragma unroll
+        for (int k = 0; k < BB; ++k)
+            lc[k] = (Jw < Jhi && k > lane && k < jbw) ? __ldg(a.H + (size_t)(c0w + k) * R + c0w + lane)
+                                                     : 0.0;
+        // a_K of the higher blocks, as they are published; the L rows are loaded first
+        bool good = true;
+        int published = a.nJ;  // blocks K >= published are known to be solved
+        for (int K = a.nJ - 1; K >= Jhi; --K) {
+            const int k0 = K * BB, kb = min(BB, R - k0);
+            double hv[BB], av[BB];
+#pragma unroll
+            for (int k = 0; k < BB; ++k)
+                hv[k] = (k < kb && qv) ? __ldg(a.H + (size_t)(k0 + k) * R + q) : 0.0;
+            if (K < published) {
+                if (tid == 0) {
+                    const int* const pc[1] = {&prog[r]};
+                    const int vc[1] = {a.nJ - K};
+                    ok = flow_wait(pc, vc, abort_flag);
+                    kmin = a.nJ - ld_acquire(&prog[r]);
+                }
+                __syncthreads();
+                good = ok;
+                published = kmin;
+                __syncthreads();  // ok / kmin are rewritten at the next wait
+                if (!good) break;
+            }
+#pragma unroll
+            for (int k = 0; k < BB; ++k) av[k] = k < kb ? __ldcg(a.A + (size_t)r * R + k0 + k) : 0.0;
+            y -= dot32(av, hv);
+        }
+        if (!good) break;
+        // own blocks, top to bottom; one barrier per block (a_J double-buffered), the solving
+        // warp publishes after the barrier while the next block's warp goes on
+        for (int J = Jhi - 1; J >= Jlo; --J) {
+            const int c0 = J * BB, jb = min(BB, R - c0), b = J & 1;
+            const bool mine = w == J - Jlo;
+            if (mine) {
+                double v = y;
+#pragma unroll
+                for (int k = BB - 1; k > 0; --k) {
+                    if (k < jb) {  // uniform over the warp
+                        const double ak = __shfl_sync(0xffffffffu, v, k);
+                        if (lane < k) v = fma(-ak, lc[k], v);
+                    }
+                }
+                y = v;
+                as[b][lane] = v;
+                if (lane < jb) a.A[(size_t)r * R + c0 + lane] = v;
+            }
+            __syncthreads();
+            if (mine) {
+                if (lane == 0) {
+                    __threadfence();
+                    st_release(&prog[r], a.nJ - J);
+                }
+            } else if (qv && q < c0) {
+                double hv[BB];
+#pragma unroll
+                for (int k = 0; k < BB; ++k)
+                    hv[k] = k < jb ? __ldg(a.H + (size_t)(c0 + k) * R + q) : 0.0;
+                y -= dot32(as[b], hv);
+            }
+        }
+        __syncthreads();  // tk is rewritten by the next claim
+    }
+}
+
 // ---- host: the task list ---------------------------------------------------------------
 // Ticket order: a diagonal wavefront. S(t, k) sorts at 2k + 1 and U(t, j, k) at j + k, so
 // the updates near the diagonal (which the chain needs first) come early and those of
@@ -650,6 +776,21 @@ cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, dou
     const int grid = max_ctas > 0 ? std::max(2, std::min(p->grid, max_ctas)) : p->grid;
     const int smem = max_ctas > 0 ? (int)kFlowSmemUsed : kFlowSmem;
     k_ldl_flow<<<grid, kFlowThreads, smem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+size_t bsolve_sync_ints(int nmax) { return 2 + (size_t)nmax; }
+
+cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, double* A,
+                          const double* H, int* sync) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * bsolve_sync_ints(n), st);
+    if (e != cudaSuccess) return e;
+    const int nJ = cdiv(R, BB), C = cdiv(R, kSlice);
+    BsArgs a{Yf, A, H, R, n, nJ, C, sync};
+    const int grid = std::min(n * C, kNumSM * 4);
+    k_bsolve_slices<<<grid, kBsThreads, 0, st>>>(a);
     count_launch();
     return cudaGetLastError();
 }

@@ -113,6 +113,72 @@ __global__ void k_splitk_reduce(int M, int N, int splits, const double* __restri
     }
 }
 
+// Symmetric C = A^T B (A, B: K x N row-major with leading dimension ld; the product is
+// symmetric, e.g. a Gram matrix A^T A) on 32 x 32 tiles of the lower triangle, mirrored.
+// Small tiles so that every SM gets a tile (a 720 x 720 Gram has 276 of them) and K is not
+// split (no partials); the last K chunk runs only its valid columns. 256 threads, 2 x 2
+// outputs each, fixed summation order.
+constexpr int SYT = 32;
+__global__ void __launch_bounds__(256)
+k_dsyrk32(int N, int K, const double* __restrict__ A, const double* __restrict__ B, int ld,
+          double* __restrict__ C, int ldc) {
+    constexpr int BK = 16;
+    __shared__ double As[BK][SYT + 1];
+    __shared__ double Bs[BK][SYT + 1];
+    // lower-triangle tile (ti, tj), tj <= ti, from the linear index
+    const int t = blockIdx.x;
+    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    if ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    if (ti * (ti + 1) / 2 > t) --ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    const int m0 = ti * SYT, n0 = tj * SYT;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BK * SYT; e += 256) {
+            const int kk = e / SYT, r = e % SYT, k = k0 + kk;
+            As[kk][r] = (k < K && m0 + r < N) ? A[(size_t)k * ld + m0 + r] : 0.0;
+            Bs[kk][r] = (k < K && n0 + r < N) ? B[(size_t)k * ld + n0 + r] : 0.0;
+        }
+        __syncthreads();
+        const int kn = min(BK, K - k0);
+        if (kn == BK) {
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+                const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+                c00 = fma(a0, b0, c00);
+                c01 = fma(a0, b1, c01);
+                c10 = fma(a1, b0, c10);
+                c11 = fma(a1, b1, c11);
+            }
+        } else {
+            for (int kk = 0; kk < kn; ++kk) {
+                const double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+                const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+                c00 = fma(a0, b0, c00);
+                c01 = fma(a0, b1, c01);
+                c10 = fma(a1, b0, c10);
+                c11 = fma(a1, b1, c11);
+            }
+        }
+        __syncthreads();
+    }
+    const double cv[2][2] = {{c00, c01}, {c10, c11}};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= N) continue;
+            C[(size_t)m * ldc + n] = cv[i][j];
+            C[(size_t)n * ldc + m] = cv[i][j];
+        }
+    }
+}
+
 namespace {
 struct GemmPlan {
     int BM, BN, splits, kchunk, tiles;
@@ -205,6 +271,12 @@ void dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, 
     }
     const bool hadb = B2 != nullptr;
     ProfScope prof(st, KC_DGEMM, (symm ? 1.0 : 2.0) * M * (double)N * K);
+    if (symm && trans_a && !hadb && !E && M == N && lda == ldb && K > 0) {
+        const int nt = cdiv(N, SYT);
+        count_launch();
+        k_dsyrk32<<<nt * (nt + 1) / 2, 256, 0, st>>>(N, K, A, B, lda, C, ldc);
+        return;
+    }
     count_launch(p.splits > 1 ? 2 : 1);
     if (p.BM == 32)
         dispatch_gemm<32>(st, p, trans_a, hadb, symm, M, N, K, A, lda, B, B2, ldb, C, ldc, E, part);

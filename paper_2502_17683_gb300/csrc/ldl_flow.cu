@@ -744,9 +744,9 @@ const Plan* get_plan(int R, int n) {
     }
     int nsm = kNumSM;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // about one worker group per task of an average panel step, one CTA per SM at most
-    const long per_step = (p.ntasks + p.nT - 1) / std::max(1, p.nT);
-    p.grid = (int)std::min<long>(nsm, 1 + std::max<long>(1, (per_step + kGroups - 1) / kGroups));
+    // every SM (measured: 152 CTAs beat 120 and 80 at R = 720; the chain's waits for
+    // workers shrink), fewer only when there are fewer tasks than worker groups
+    p.grid = (int)std::min<long>(nsm, 1 + std::max<long>(1, ((long)p.ntasks + kGroups - 1) / kGroups));
     if (cudaFuncSetAttribute(k_ldl_flow, cudaFuncAttributeMaxDynamicSharedMemorySize, kFlowSmem) !=
         cudaSuccess)
         return nullptr;

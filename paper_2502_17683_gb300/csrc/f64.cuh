@@ -31,11 +31,11 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   launch per block step.
 //   flow_ctas: 0 = the dataflow kernel takes one CTA per SM; > 0 = at most that many CTAs
 //   with only the shared memory they use (problems running side by side).
-//   bs_sync: bsolve_sync_ints(n) ints for the sliced backward solve, or null for one CTA
-//   per row.
+//   bs_sync: bsolve_sync_ints(n) ints, the progress counters of the backward solve (by
+//   column slices, ldl_flow.cu).
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
-                DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas = 0,
-                int* bs_sync = nullptr);
+                DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
+                int* bs_sync);
 
 // Dataflow LDL^T (ldl_flow.cu): ints of progress state for R and n <= nmax; plan set-up
 // for (R, n) (false: too large or the task order failed its check; use the blocked path);

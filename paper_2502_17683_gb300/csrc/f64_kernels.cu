@@ -351,7 +351,8 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 // Solve of the ALS normal equations A H = M: blocked right-looking LDL^T factorisation
 // of H (the square-root-free form of the Cholesky factorisation, same pivots) with the
 // M rows carried along as extra rows, so that the forward solve is fused into the
-// factorisation; then a blocked backward solve with the unit lower factor.
+// factorisation (this file: the blocked variant, one launch per 32-column step; the
+// dataflow variant and the backward solve with the unit lower factor are in ldl_flow.cu).
 //
 // GB300 issues one FP64 warp-instruction per SM sub-partition every 64 clocks, whatever
 // the number of active lanes, and FP64 divide / sqrt cost 400-700 clocks. So the
@@ -538,149 +539,6 @@ k_ldl_update(double* __restrict__ H, const double* __restrict__ P, double* __res
     factor_block(H, R, j1, jbn, dinv, sc, mode, S);
 }
 
-// Backward step J of A L = Y (unit lower L): warp 0 solves A_J L_JJ = Y_J for row r by
-// substitution, then every CTA applies Y[r, q] -= sum_c A_J[c] L[c0+c][q] to its chunk of
-// columns q < c0; CTA 0 stores A_J.
-__global__ void __launch_bounds__(256)
-k_bsolve_unit(double* __restrict__ Yf, double* __restrict__ A, int R,
-              const double* __restrict__ H, int J) {
-    const int c0 = J * NB, jb = min(NB, R - c0);
-    const int r = blockIdx.y;
-    __shared__ double Lj[NB][NB + 1];
-    __shared__ double a_s[NB];
-    const int tid = threadIdx.x, lane = tid & 31;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e / NB, t = e % NB;
-        Lj[i][t] = (i < jb && t < i) ? H[(size_t)(c0 + i) * R + c0 + t] : 0.0;
-    }
-    __syncthreads();
-    if (tid < 32) {
-        double y = (lane < jb) ? Yf[(size_t)r * R + c0 + lane] : 0.0;
-        for (int c = jb - 1; c >= 0; --c) {
-            const double ac = __shfl_sync(0xffffffffu, y, c);
-            if (lane < c) y = fma(-ac, Lj[c][lane], y);
-        }
-        a_s[lane] = y;
-        if (blockIdx.x == 0 && lane < jb) A[(size_t)r * R + c0 + lane] = y;
-    }
-    __syncthreads();
-    const int q = blockIdx.x * blockDim.x + tid;
-    if (q < c0) {
-        // all 32 L2 loads in flight before the dependent FMAs (jb == 32 except the last
-        // block, and that one has c0 = 0 here only when R <= 32)
-        double hv[NB];
-#pragma unroll
-        for (int c = 0; c < NB; ++c) hv[c] = (c < jb) ? H[(size_t)(c0 + c) * R + q] : 0.0;
-        double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-        for (int c = 0; c < NB; c += 2) {
-            s0 = fma(a_s[c], hv[c], s0);
-            s1 = fma(a_s[c + 1], hv[c + 1], s1);
-        }
-        Yf[(size_t)r * R + q] -= (s0 + s1);
-    }
-}
-
-// Backward solve A L = Y (unit lower L, strictly-lower part in H) in one launch: one CTA
-// per row r of A. y (the row of Y, in shared memory) is consumed block by block from the
-// last 32-column block J to the first: warp 0 solves a_J L_JJ = y_J by substitution (the
-// diagonal block comes from shared memory, prefetched with cp.async during the previous
-// block), applies a_J to the next block y_{J-1} itself, and moves on; warps 1-15 apply a_J
-// to the columns left of y_{J-1}. One barrier per block hands a_J over. The row's FP64 work
-// (R^2 / 2 FMA) sets the time when R is large, the substitution chain when it is small.
-constexpr int BW = 32;
-constexpr int BS_THREADS = 512;
-constexpr size_t kBsolveSmemMax = 200 * 1024;
-
-// 8-byte global -> shared copy; an invalid source is not read (zero fill) and is replaced
-// by `safe`, a valid address, so that no out-of-range address is formed.
-__device__ __forceinline__ void cp_async8(double* dst, const double* src, bool valid,
-                                          const double* safe) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d),
-                 "l"(valid ? src : safe), "r"(valid ? 8 : 0)
-                 : "memory");
-}
-
-struct BsolveSmem {
-    double Ld[2][BW][BW + 1];  // diagonal block L_JJ (strictly lower used)
-    double Lo[2][BW][BW + 1];  // block L_{J, J-1} (rows of block J, columns of block J-1)
-    double a[2][BW];           // a_J
-};
-
-// warp 0: copy the blocks that step J needs into buffer b (rows of block J; Lo for J >= 1)
-__device__ __forceinline__ void bsolve_prefetch(BsolveSmem& S, int b, const double* __restrict__ H,
-                                                int R, int J, int lane) {
-    const int c0 = J * BW, jb = min(BW, R - c0);
-    for (int i = 0; i < BW; ++i) {
-        const bool row = i < jb;
-        const double* src = H + (size_t)(c0 + (row ? i : 0)) * R;
-        cp_async8(&S.Ld[b][i][lane], src + c0 + lane, row && lane < i, H);
-        if (J >= 1) cp_async8(&S.Lo[b][i][lane], src + c0 - BW + lane, row, H);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-__global__ void __launch_bounds__(BS_THREADS)
-k_bsolve_rows(const double* __restrict__ Yf, double* __restrict__ A, int R,
-              const double* __restrict__ H) {
-    extern __shared__ __align__(16) unsigned char bs_smem[];
-    BsolveSmem& S = *reinterpret_cast<BsolveSmem*>(bs_smem);
-    double* y = reinterpret_cast<double*>(bs_smem + sizeof(BsolveSmem));
-    const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
-    const int nJ = (R + BW - 1) / BW;
-    for (int q = tid; q < R; q += BS_THREADS) y[q] = Yf[(size_t)r * R + q];
-    if (tid < 32) bsolve_prefetch(S, (nJ - 1) & 1, H, R, nJ - 1, lane);
-    __syncthreads();
-    for (int J = nJ - 1; J >= 0; --J) {
-        const int c0 = J * BW, jb = min(BW, R - c0), b = J & 1;
-        double v = 0.0;
-        if (tid < 32) {
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            __syncwarp();
-            if (J >= 1) bsolve_prefetch(S, b ^ 1, H, R, J - 1, lane);
-            v = lane < jb ? y[c0 + lane] : 0.0;
-            for (int c = jb - 1; c > 0; --c) {
-                const double ac = __shfl_sync(0xffffffffu, v, c);
-                if (lane < c) v = fma(-ac, S.Ld[b][c][lane], v);
-            }
-            S.a[b][lane] = v;
-            if (lane < jb) A[(size_t)r * R + c0 + lane] = v;
-        }
-        __syncthreads();  // a_J visible; the bulk of the previous block is done
-        if (tid < 32) {
-            if (J >= 1) {
-                // y_{J-1} -= a_J L_{J, J-1}: the next block, by warp 0 itself
-                double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-                for (int c = 0; c < BW; c += 2) {
-                    s0 = fma(__shfl_sync(0xffffffffu, v, c), S.Lo[b][c][lane], s0);
-                    s1 = fma(__shfl_sync(0xffffffffu, v, c + 1), S.Lo[b][c + 1][lane], s1);
-                }
-                y[c0 - BW + lane] -= (s0 + s1);
-            }
-            __syncwarp();
-        } else {
-            // columns q < c0 - 32: y_q -= sum_c a_c L[c0 + c][q]
-            const double* a = S.a[b];
-            for (int q = tid - 32; q < c0 - BW; q += BS_THREADS - 32) {
-                double hv[BW];
-#pragma unroll
-                for (int c = 0; c < BW; ++c) hv[c] = c < jb ? H[(size_t)(c0 + c) * R + q] : 0.0;
-                double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-                for (int c = 0; c < BW; c += 2) {
-                    s0 = fma(a[c], hv[c], s0);
-                    s1 = fma(a[c + 1], hv[c + 1], s1);
-                }
-                y[q] -= (s0 + s1);
-            }
-        }
-    }
-}
-
-size_t bsolve_smem_bytes(int R) { return sizeof(BsolveSmem) + sizeof(double) * (size_t)R; }
-
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
                 int* bs_sync) {
@@ -712,29 +570,7 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
     }
     if (n <= 0) return;
     ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
-    double* Yf = Haug + (size_t)R * R;
-    if (bs_sync) {
-        bsolve_slices(st, R, n, Yf, A, Haug, bs_sync);
-        return;
-    }
-    const size_t smem = bsolve_smem_bytes(R);
-    if (smem <= kBsolveSmemMax) {  // else (R above ~20000): one launch per block
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_bsolve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kBsolveSmemMax);
-            attr = true;
-        }
-        k_bsolve_rows<<<n, BS_THREADS, smem, st>>>(Yf, A, R, Haug);
-        count_launch();
-        return;
-    }
-    for (int J = nJ - 1; J >= 0; --J) {
-        const int c0 = J * NB;
-        dim3 grid(std::max(1, cdiv(c0, 256)), n);
-        k_bsolve_unit<<<grid, 256, 0, st>>>(Yf, A, R, Haug, J);
-        count_launch();
-    }
+    bsolve_slices(st, R, n, Haug + (size_t)R * R, A, Haug, bs_sync);
 }
 
 // ------------------------------------------------------------------------------------

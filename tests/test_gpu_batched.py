@@ -73,3 +73,20 @@ def test_batched_autotune_keeps_results(api):
     res0 = api.thc_cpd_als_batched(ref, 5, 0.0, precision="bf16x3")
     for a, b in zip(res, res0):
         assert abs(a["fit"] - b["fit"]) <= 1e-6
+
+
+def test_dataflow_factorisation_does_not_depend_on_the_grid(api):
+    # Asked for the dataflow LDL^T, the batched driver runs it on at most 32 CTAs per problem
+    # (problems share the GPU), a single call on one CTA per SM. Every tile gets its updates
+    # in a fixed order whatever the schedule, so both give the same bits.
+    shapes = [(8, 40, 192, 288), (9, 45, 216, 324)]  # 18 and 21 tile rows: thousands of tasks
+    batch = _problems(shapes, 500)
+    solo = _problems(shapes, 500)
+    res = api.thc_cpd_als_batched(batch, 4, 0.0, precision="fp64", ldl="dataflow")
+    for b, s_, r in zip(batch, solo, res):
+        out = api.thc_cpd_als(s_["Xo"], s_["Xv"], s_["Z"], s_["A"], s_["lam"], 4, 0.0,
+                              precision="fp64", ldl="dataflow")
+        assert r["sweeps"] == out["sweeps"] == 4
+        assert r["fit"] == out["fit"]
+        for a, c in zip(b["A"], s_["A"]):
+            assert torch.equal(a, c)

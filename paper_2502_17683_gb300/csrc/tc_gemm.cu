@@ -20,7 +20,9 @@ namespace {
 constexpr int BM = 128;             // MMA M (one CTA, cta_group::1)
 constexpr int KBYTES = 128;         // bytes of K per stage (one 128-byte swizzle atom)
 constexpr int TILE_A = BM * KBYTES;  // 16 KB
-constexpr int TMEM_COLS = 256;
+constexpr int ACC_COLS = 256;        // one FP32 accumulator (tile N <= 256)
+constexpr int TMEM_COLS = 2 * ACC_COLS;  // two: the epilogue drains one while the next fills
+constexpr int EPI_STAGE_BYTES = 4 * 32 * 17 * 4;  // per-warp 32 x 16 staging of the epilogue
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int NTHREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM, warps 2..5: epilogue
 
@@ -37,6 +39,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -146,7 +152,8 @@ __host__ __device__ constexpr uint32_t make_idesc(bool tf32, int M, int N) {
 
 struct KArgs {
     int M, N, nkb, BN, stages;
-    int kper;          // k-blocks per CTA along grid z (split-K of the FP64-out epilogue)
+    int tn, tm, ntiles;  // tiles along N and M, and tn x tm x K splits in all
+    int kper;          // k-blocks per tile along the K split (split-K of the FP64-out epilogue)
     double* part;      // split-K partials [z][N][ld_f64t] (when gridDim.z > 1)
     TcEpilogue ep;
     void* out_hi;
@@ -173,6 +180,12 @@ __device__ __forceinline__ void store_split(void* hi, void* lo, size_t idx, floa
     }
 }
 
+// Persistent split GEMM: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the
+// (N tile, M tile, K split) grid. Warp 0 streams the operand tiles through the TMA ring
+// without stopping between tiles; warp 1 issues the MMAs of tile i into TMEM accumulator
+// i & 1 and commits it; warps 2..5 drain accumulator i & 1 (TMEM -> registers -> fused
+// outputs) while the MMAs of tile i + 1 run into the other one, then release it. Every
+// wait is bounded and records a code when it gives up.
 template <bool TF32>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
@@ -184,24 +197,26 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     const int BN = args.BN, S = args.stages;
     const int tileB = BN * KBYTES;
     const int stage_bytes = 2 * TILE_A + 2 * tileB;
-    uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
+    float* epi = (float*)(smem + (size_t)S * stage_bytes);
+    uint64_t* full = (uint64_t*)((uint8_t*)epi + EPI_STAGE_BYTES);
     uint64_t* empty = full + S;
-    uint64_t* tmem_full = empty + S;
-    uint32_t* tmem_slot = (uint32_t*)(tmem_full + 1);
+    uint64_t* acc_full = empty + S;   // [2]
+    uint64_t* acc_empty = acc_full + 2;  // [2]
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kel = TF32 ? 32 : 64;  // elements per 128-byte K block
-    const int kb0 = blockIdx.z * args.kper;
-    const int kb1 = min(args.nkb, kb0 + args.kper);
-    const int nk = kb1 - kb0;        // k-blocks of this CTA (>= 1)
+    const int tnm = args.tn * args.tm;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(tmem_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrive per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -216,111 +231,138 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
     if (warp == 0 && lane == 0) {
         // ---- TMA producer ----
         const uint32_t tx = (uint32_t)stage_bytes;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % S;
-            if (!mbar_wait(&empty[s], ((kb / S) & 1) ^ 1, 1)) break;
-            uint8_t* st = smem + (size_t)s * stage_bytes;
-            const int kx = (kb0 + kb) * kel;
-            mbar_expect_tx(&full[s], tx);
-            tma_load_2d(st, &tAh, &full[s], kx, m0);
-            tma_load_2d(st + TILE_A, &tAl, &full[s], kx, m0);
-            tma_load_2d(st + 2 * TILE_A, &tBh, &full[s], kx, n0);
-            tma_load_2d(st + 2 * TILE_A + tileB, &tBl, &full[s], kx, n0);
+        int it = 0;  // position in the ring, over all tiles of this CTA
+        bool ok = true;
+        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x) {
+            const int z = t / tnm, r = t % tnm, m0 = (r / args.tn) * BM, n0 = (r % args.tn) * BN;
+            const int kb0 = z * args.kper, nk = min(args.nkb, kb0 + args.kper) - kb0;
+            for (int kb = 0; kb < nk; ++kb, ++it) {
+                const int s = it % S;
+                if (!mbar_wait(&empty[s], ((it / S) & 1) ^ 1, 1)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* st = smem + (size_t)s * stage_bytes;
+                const int kx = (kb0 + kb) * kel;
+                mbar_expect_tx(&full[s], tx);
+                tma_load_2d(st, &tAh, &full[s], kx, m0);
+                tma_load_2d(st + TILE_A, &tAl, &full[s], kx, m0);
+                tma_load_2d(st + 2 * TILE_A, &tBh, &full[s], kx, n0);
+                tma_load_2d(st + 2 * TILE_A + tileB, &tBl, &full[s], kx, n0);
+            }
         }
-        // drain: wait until the consumer released every stage still in flight
-        for (int kb = max(0, nk - S); kb < nk; ++kb)
-            mbar_wait(&empty[kb % S], (kb / S) & 1, 2);
+        // drain: wait until the MMAs released every stage still in flight
+        for (int j = max(0, it - S); j < it; ++j) mbar_wait(&empty[j % S], (j / S) & 1, 2);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
         const uint32_t idesc = make_idesc(TF32, BM, BN);
+        int it = 0, i = 0;
         bool ok = true;
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % S;
-            if (!mbar_wait(&full[s], (kb / S) & 1, 3)) {
-                ok = false;
-                break;
-            }
+        for (int t = blockIdx.x; t < args.ntiles && ok; t += gridDim.x, ++i) {
+            const int z = t / tnm;
+            const int kb0 = z * args.kper, nk = min(args.nkb, kb0 + args.kper) - kb0;
+            const int b = i & 1;
+            // accumulator b is free once the epilogue has drained tile i - 2
+            if (i >= 2 && !mbar_wait(&acc_empty[b], ((i >> 1) - 1) & 1, 5)) break;
             tc_fence_after();
-            uint8_t* st = smem + (size_t)s * stage_bytes;
-            const uint64_t ah = sw128_desc(smem_u32(st));
-            const uint64_t al = sw128_desc(smem_u32(st + TILE_A));
-            const uint64_t bh = sw128_desc(smem_u32(st + 2 * TILE_A));
-            const uint64_t bl = sw128_desc(smem_u32(st + 2 * TILE_A + tileB));
+            const uint32_t acc = tmem + (uint32_t)(b * ACC_COLS);
+            for (int kb = 0; kb < nk; ++kb, ++it) {
+                const int s = it % S;
+                if (!mbar_wait(&full[s], (it / S) & 1, 3)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint8_t* st = smem + (size_t)s * stage_bytes;
+                const uint64_t ah = sw128_desc(smem_u32(st));
+                const uint64_t al = sw128_desc(smem_u32(st + TILE_A));
+                const uint64_t bh = sw128_desc(smem_u32(st + 2 * TILE_A));
+                const uint64_t bl = sw128_desc(smem_u32(st + 2 * TILE_A + tileB));
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {  // 4 MMAs of 32 bytes of K per stage
-                const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                tc_mma<TF32>(tmem, ah + o, bh + o, idesc, (kb | kk) ? 1u : 0u);
-                tc_mma<TF32>(tmem, ah + o, bl + o, idesc, 1u);
-                tc_mma<TF32>(tmem, al + o, bh + o, idesc, 1u);
+                for (int kk = 0; kk < 4; ++kk) {  // 4 MMAs of 32 bytes of K per stage
+                    const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                    tc_mma<TF32>(acc, ah + o, bh + o, idesc, (kb | kk) ? 1u : 0u);
+                    tc_mma<TF32>(acc, ah + o, bl + o, idesc, 1u);
+                    tc_mma<TF32>(acc, al + o, bh + o, idesc, 1u);
+                }
+                tc_commit(&empty[s]);
             }
-            tc_commit(&empty[s]);
+            if (!ok) break;
+            tc_commit(&acc_full[b]);
         }
-        tc_commit(tmem_full);
     } else if (warp >= 2) {
         // ---- epilogue: TMEM -> registers -> fused outputs ----
         const int q = warp & 3;  // TMEM lane quarter this warp may access
         const TcEpilogue& ep = args.ep;
-        const int m = m0 + 32 * q + lane;
-        // per-warp staging of a 32 x 16 slice (the ring is idle once the MMAs are done), so
-        // that row-major outputs and the Hadamard partner are accessed row-contiguously
-        float* stg = (float*)smem + (warp - 2) * 32 * 17;
+        float* stg = epi + (warp - 2) * 32 * 17;  // this warp's 32 x 16 staging slice
         const bool rowmajor = ep.out_f32 || ep.mul;
-        double* f64t = gridDim.z > 1 ? args.part + (size_t)blockIdx.z * args.N * ep.ld_f64t
-                                     : ep.out_f64t;
         const int col = lane & 15, half = lane >> 4;
-        // partner values of one 32 x 16 slice: lane (col, half) holds rows 2 rr + half
-        float cur[16], nxt[16];
-        auto load_partner = [&](int c, float* dst) {
-            const int n = n0 + c + col;
-#pragma unroll
-            for (int rr = 0; rr < 16; ++rr) {
-                const int mm = m0 + 32 * q + 2 * rr + half;
-                dst[rr] = (mm < args.M && n < args.N) ? __ldg(ep.mul + (size_t)mm * ep.ld_mul + n)
-                                                      : 0.f;
-            }
-        };
-        // the first slice's partner loads overlap the main loop
-        if (ep.mul) load_partner(0, cur);
-        const bool ok = mbar_wait(tmem_full, 0, 4);
-        tc_fence_after();
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-            // software pipeline: the next slice's partner loads are in flight while this
-            // slice is written
-            if (ep.mul && c + 16 < BN) load_partner(c + 16, nxt);
-            if (ok && f64t && m < args.M) {
-                // transposed FP64 output: consecutive lanes hold consecutive m (coalesced)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + c + j;
-                    if (n < args.N) f64t[(size_t)n * ep.ld_f64t + m] = (double)v[j];
-                }
-            }
-            if (ok && rowmajor) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
-                __syncwarp();
+        int i = 0;
+        for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++i) {
+            const int z = t / tnm, r = t % tnm, m0 = (r / args.tn) * BM, n0 = (r % args.tn) * BN;
+            const int b = i & 1;
+            const int m = m0 + 32 * q + lane;
+            double* f64t = args.part ? args.part + (size_t)z * args.N * ep.ld_f64t : ep.out_f64t;
+            // partner values of one 32 x 16 slice: lane (col, half) holds rows 2 rr + half
+            float cur[16], nxt[16];
+            auto load_partner = [&](int c, float* dst) {
                 const int n = n0 + c + col;
 #pragma unroll
                 for (int rr = 0; rr < 16; ++rr) {
-                    const int row = 2 * rr + half;
-                    const int mm = m0 + 32 * q + row;
-                    if (mm < args.M && n < args.N) {
-                        const float d = stg[row * 17 + col];
-                        if (ep.out_f32) ep.out_f32[(size_t)mm * ep.ld_f32 + n] = d;
-                        if (ep.mul)
-                            store_split<TF32>(args.out_hi, args.out_lo,
-                                              (size_t)mm * args.ld_split + n, d * cur[rr]);
+                    const int mm = m0 + 32 * q + 2 * rr + half;
+                    dst[rr] = (mm < args.M && n < args.N)
+                                  ? __ldg(ep.mul + (size_t)mm * ep.ld_mul + n)
+                                  : 0.f;
+                }
+            };
+            // the first slice's partner loads overlap the main loop
+            if (ep.mul) load_partner(0, cur);
+            if (!mbar_wait(&acc_full[b], (i >> 1) & 1, 4)) break;
+            tc_fence_after();
+            const uint32_t acc = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tmem_ld16(acc + (uint32_t)c, v);
+                // software pipeline: the next slice's partner loads are in flight while this
+                // slice is written
+                if (ep.mul && c + 16 < BN) load_partner(c + 16, nxt);
+                if (f64t && m < args.M) {
+                    // transposed FP64 output: consecutive lanes hold consecutive m (coalesced)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = n0 + c + j;
+                        if (n < args.N) f64t[(size_t)n * ep.ld_f64t + m] = (double)v[j];
                     }
                 }
-                __syncwarp();
-            }
-            if (ep.mul) {
+                if (rowmajor) {
 #pragma unroll
-                for (int rr = 0; rr < 16; ++rr) cur[rr] = nxt[rr];
+                    for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
+                    __syncwarp();
+                    const int n = n0 + c + col;
+#pragma unroll
+                    for (int rr = 0; rr < 16; ++rr) {
+                        const int row = 2 * rr + half;
+                        const int mm = m0 + 32 * q + row;
+                        if (mm < args.M && n < args.N) {
+                            const float d = stg[row * 17 + col];
+                            if (ep.out_f32) ep.out_f32[(size_t)mm * ep.ld_f32 + n] = d;
+                            if (ep.mul)
+                                store_split<TF32>(args.out_hi, args.out_lo,
+                                                  (size_t)mm * args.ld_split + n, d * cur[rr]);
+                        }
+                    }
+                    __syncwarp();
+                }
+                if (ep.mul) {
+#pragma unroll
+                    for (int rr = 0; rr < 16; ++rr) cur[rr] = nxt[rr];
+                }
             }
+            // every TMEM read of this tile has completed (tcgen05.wait::ld in tmem_ld16)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
     }
     tc_fence_before();
@@ -402,9 +444,9 @@ cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const Split
     const int tileB = BN * KBYTES;
     const int stage_bytes = 2 * TILE_A + 2 * tileB;
     const int nkb = std::max(1, cdiv((long)K * (tf32 ? 4 : 2), KBYTES));
-    const int avail = g_max_smem - 1024 - 256;
+    const int avail = g_max_smem - 1024 - EPI_STAGE_BYTES - 256;
     const int stages = std::max(2, std::min(6, avail / stage_bytes));
-    const size_t smem = 1024 + (size_t)stages * stage_bytes + 256;
+    const size_t smem = 1024 + (size_t)stages * stage_bytes + EPI_STAGE_BYTES + 256;
     CUtensorMap mAh, mAl, mBh, mBl;
     if (!make_map(&mAh, tf32, A.hi, M, K, A.pitch, BM) || !make_map(&mAl, tf32, A.lo, M, K, A.pitch, BM) ||
         !make_map(&mBh, tf32, B.hi, N, K, B.pitch, BN) || !make_map(&mBl, tf32, B.lo, N, K, B.pitch, BN))
@@ -426,13 +468,16 @@ cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const Split
     args.nkb = nkb;
     args.BN = BN;
     args.stages = stages;
+    args.tn = cdiv(N, BN);
+    args.tm = mt;
+    args.ntiles = args.tn * mt * splits;
     args.kper = kper;
     args.part = splits > 1 ? part : nullptr;
     args.ep = ep;
     args.out_hi = ep.out_split ? ep.out_split->hi : nullptr;
     args.out_lo = ep.out_split ? ep.out_split->lo : nullptr;
     args.ld_split = ep.out_split ? ep.out_split->pitch : 0;
-    dim3 grid(cdiv(N, BN), mt, splits);
+    const int grid = std::min(args.ntiles, kNumSM);  // persistent: at most one CTA per SM
     ProfScope prof(st, KC_TC, 2.0 * M * (double)N * K);
     count_launch(splits > 1 ? 2 : 1);
     static std::once_flag attr_once;

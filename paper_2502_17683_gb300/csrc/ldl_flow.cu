@@ -56,7 +56,7 @@ constexpr int kGroups = 4;                 // worker groups (128 threads) per CT
 constexpr int kFlowThreads = 128 * kGroups;
 constexpr int kFlowSmem = 120 * 1024;      // more than half an SM: one CTA per SM
 constexpr unsigned long long kWaitNs = 1000000000ull;
-constexpr int kSyncHead = 4;               // ticket, arrivals, fdone, abort
+constexpr int kSyncHead = 5;               // ticket, arrivals, fdone, abort, critical ticket
 constexpr int kMaxTiles = 256;             // largest schedule the host builds
 // Beyond 80 tiles (R > 1280) the solve is bound by FP64 throughput rather than by the
 // pivot chain, and the blocked factorisation's update launches keep the pipes busier
@@ -67,6 +67,15 @@ struct FlowTask {
     short type, t, j, k;                   // type 0: S(t, k); 1: U(t, j, k)
 };
 
+// The tasks on the two panels just behind chain step s in row tile s: S(s, s-2),
+// U(s, s-1, s-2), U(s, s, s-2), which feed step s directly, and S(s, s-3), U(s, j, s-3)
+// (j = s-2, s-1, s), which feed those. They are served by worker groups of their own that
+// run alone on their SMs, so that the FP64 pipes they issue to are not shared with three
+// other groups (which makes a task several times slower and, here, holds up the chain).
+__host__ __device__ __forceinline__ bool critical_task(const FlowTask& x, int nT) {
+    return x.t < nT && x.k >= x.t - 3;
+}
+
 struct ChainSmem {
     double Lp[FB][FB + 1];   // L of the previous diagonal tile (strictly lower)
     double dp[FB];           // its D^-1
@@ -75,6 +84,7 @@ struct ChainSmem {
     double D[FB][FB + 1];    // diagonal tile being factorised
     double L[FB][FB + 1];
     double dinv[FB];
+    double x2[FB];           // x2[r] = a(r, r-1)^2 once column r-2 has been applied to it
     double Bn[2][FB][FB + 1];  // tile (s, s-1) for step s, buffer s & 1 (from the producer)
     double Dn[2][FB][FB + 1];  // tile (s, s)
     unsigned short pairs[FB * (FB + 1) / 2];
@@ -167,14 +177,20 @@ __device__ bool smem_wait(const volatile int* p, int v, int* abort_flag) {
 }
 
 // LDL^T of the jb x jb tile in S.D (lower triangle) into S.L (strictly lower), S.D's
-// diagonal and S.dinv. Threads 0..127 compute with a barrier of their own per column:
-// thread 0 carries the pivot chain one column ahead (pivot update and its reciprocal),
-// warps 1-3 apply column c to the rest of the tile over the packed pair list. A pivot
-// <= tau sets S.bad and continues with 1 (the caller then replays the mode with the
-// pseudo-inverse). Ends with a barrier of the chain's threads 0..255.
+// diagonal and S.dinv. Threads 0..127 compute with a barrier of their own per column.
+// Thread 0 carries only the pivot chain, one column ahead: d(c+1) = a(c+1, c+1) -
+// a(c+1, c)^2 / d(c) and its reciprocal, with 1/d(c) in a register and a(c+1, c)^2 formed,
+// one column earlier, by the thread that finished a(c+1, c). (Each FP64 instruction of a
+// warp costs tens of clocks of issue on this part, so the chain thread issues four per
+// column and nothing else.) Warps 1-3 apply column c to the rest of the tile over the
+// packed pair list, at most two pairs per thread whose operands are all read before
+// either is written. A pivot <= tau sets S.bad and continues with 1 (the caller then
+// replays the mode with the pseudo-inverse). Ends with a barrier of the chain's threads
+// 0..255.
 __device__ void factor_tile(ChainSmem& S, int jb, double tau) {
     const int tid = threadIdx.x;
     if (tid < 128) {
+        double inv = 0.0;  // thread 0: 1/d(c) of the current column
         if (tid == 0) {
             S.bad = 0;
             double d = S.D[0][0];
@@ -183,34 +199,66 @@ __device__ void factor_tile(ChainSmem& S, int jb, double tau) {
                 d = 1.0;
                 S.D[0][0] = d;
             }
-            S.dinv[0] = recip_nr(d);
+            inv = recip_nr(d);
+            S.dinv[0] = inv;
+            if (jb > 1) {
+                const double x = S.D[1][0];
+                S.x2[1] = x * x;
+            }
         }
         for (int c = 0; c < jb; ++c) {
             asm volatile("bar.sync 1, 128;" ::: "memory");  // dinv[c] and column c are final
-            const double inv = S.dinv[c];
             if (tid == 0) {
                 if (c + 1 < jb) {
-                    const double x = S.D[c + 1][c];
-                    const double l = x * inv;
-                    double d1 = fma(-l, x, S.D[c + 1][c + 1]);
-                    S.L[c + 1][c] = l;
-                    if (!pivot_ok(d1, tau)) {
+                    double d1 = fma(-S.x2[c + 1], inv, S.D[c + 1][c + 1]);
+                    // the check runs beside the reciprocal, off the chain
+                    const bool ok = pivot_ok(d1, tau);
+                    double r = recip_nr(d1);
+                    if (!ok) {
                         S.bad = 1;
                         d1 = 1.0;
+                        r = 1.0;
                     }
                     S.D[c + 1][c + 1] = d1;
-                    S.dinv[c + 1] = recip_nr(d1);
+                    S.dinv[c + 1] = r;
+                    inv = r;
                 }
             } else if (tid >= 32) {
+                // pair (r, s), c < s <= r: L(r, c) = a(r, c) / d(c) when s = c + 1, and
+                // a(r, s) -= L(r, c) a(s, c) except for the pivot (c+1, c+1), thread 0's.
+                // Column c is read-only in this step and every pair writes its own entry.
+                const double inv_c = S.dinv[c];
                 const int hi = FB - 1 - c;
                 const int npair = hi * (hi + 1) / 2;
-                for (int e = tid - 32; e < npair; e += 96) {
-                    const int rs = S.pairs[e];
-                    const int r = rs >> 8, ss = rs & 0xFF;
-                    if (r >= jb || (r == c + 1 && ss == c + 1)) continue;
-                    const double l = S.D[r][c] * inv;
-                    if (ss == c + 1) S.L[r][c] = l;
-                    S.D[r][ss] = fma(-l, S.D[ss][c], S.D[r][ss]);
+                int r[2], ss[2];
+                double x[2], y[2], z[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int e = tid - 32 + 96 * k;
+                    r[k] = FB;
+                    ss[k] = 0;
+                    if (e < npair) {
+                        const int rs = S.pairs[e];
+                        r[k] = rs >> 8;
+                        ss[k] = rs & 0xFF;
+                    }
+                    x[k] = y[k] = z[k] = 0.0;
+                    if (r[k] < jb) {
+                        x[k] = S.D[r[k]][c];
+                        y[k] = S.D[ss[k]][c];
+                        if (r[k] != c + 1) z[k] = S.D[r[k]][ss[k]];
+                    }
+                }
+                const double l0 = x[0] * inv_c, l1 = x[1] * inv_c;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (r[k] >= jb) continue;
+                    const double l = k ? l1 : l0;
+                    if (ss[k] == c + 1) S.L[r[k]][c] = l;
+                    if (r[k] == c + 1) continue;
+                    const double a = fma(-l, y[k], z[k]);
+                    S.D[r[k]][ss[k]] = a;
+                    if (r[k] == c + 2 && ss[k] == c + 1) S.x2[r[k]] = a * a;
                 }
             }
         }
@@ -223,8 +271,9 @@ struct FlowArgs {
     double* P;
     double* dinv;
     int R, nrows, nT, nM;
-    const FlowTask* tasks;
-    int ntasks;
+    const FlowTask* tasks;  // [0, nmain): served by the worker CTAs; [nmain, ntasks): the
+    int ntasks, nmain;      // critical tasks, served by the critical CTAs
+    int ncrit;              // critical CTAs (one group each), roles 1..ncrit
     int* sync;
     DevScalars* sc;
     int mode;
@@ -449,19 +498,20 @@ __device__ void task_U(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
     }
 }
 
-__device__ void flow_worker(const FlowArgs& a, WorkerSmem* ws) {
-    const int g = threadIdx.x >> 7, gt = threadIdx.x & 127, bar = 1 + g;
-    WorkerSmem& W = ws[g];
-    if (gt == 0) W.ticket = atomicAdd(a.sync, 1);
+// Worker group loop over tickets [0, count) of `list`, handed out by `counter` in order.
+__device__ void flow_worker(const FlowArgs& a, WorkerSmem& W, int g, const FlowTask* list,
+                            int count, int* counter) {
+    const int gt = threadIdx.x & 127, bar = 1 + g;
+    if (gt == 0) W.ticket = atomicAdd(counter, 1);
     group_sync(bar);
     for (;;) {
         const int ti = W.ticket;
-        if (ti >= a.ntasks) break;
+        if (ti >= count) break;
         // claim the next ticket while this one runs (holding one in reserve keeps the
         // lowest unfinished ticket runnable: a group works on its lower ticket first)
         int nxt = 0;
-        if (gt == 0) nxt = atomicAdd(a.sync, 1);
-        const FlowTask tk = a.tasks[ti];
+        if (gt == 0) nxt = atomicAdd(counter, 1);
+        const FlowTask tk = list[ti];
         if (tk.type == 0)
             task_S(a, W, gt, bar, tk.t, tk.k);
         else
@@ -490,7 +540,15 @@ __global__ void __launch_bounds__(kFlowThreads, 1) k_ldl_flow(FlowArgs a) {
         else
             flow_producer(a, S);
     } else {
-        flow_worker(a, reinterpret_cast<WorkerSmem*>(smem));
+        WorkerSmem* ws = reinterpret_cast<WorkerSmem*>(smem);
+        const int g = threadIdx.x >> 7;
+        if (role <= a.ncrit) {
+            // a critical CTA: one group, alone on its SM
+            if (g == 0)
+                flow_worker(a, ws[0], 0, a.tasks + a.nmain, a.ntasks - a.nmain, a.sync + 4);
+        } else {
+            flow_worker(a, ws[g], g, a.tasks, a.nmain, a.sync);
+        }
     }
 }
 
@@ -716,8 +774,8 @@ bool build_tasks(int R, int n, std::vector<FlowTask>& out, int& nT, int& nM) {
 }
 
 struct Plan {
-    FlowTask* tasks = nullptr;
-    int ntasks = 0, nT = 0, nM = 0, grid = 0;
+    FlowTask* tasks = nullptr;  // main tasks, then the critical ones, each in list order
+    int ntasks = 0, nmain = 0, nT = 0, nM = 0, grid = 0, ncrit = 0;
     bool ok = false;
 };
 
@@ -736,6 +794,13 @@ const Plan* get_plan(int R, int n) {
     std::vector<FlowTask> h;
     if (!build_tasks(R, n, h, p.nT, p.nM)) return nullptr;
     p.ntasks = (int)h.size();
+    // split the list into the main and the critical subsequences; each keeps the list
+    // order, so the argument for progress (every task comes after all it waits for; a
+    // group works on its lower ticket first) holds for each, given one group serves it
+    std::stable_partition(h.begin(), h.end(),
+                          [&](const FlowTask& x) { return !critical_task(x, p.nT); });
+    p.nmain = 0;
+    while (p.nmain < p.ntasks && !critical_task(h[p.nmain], p.nT)) ++p.nmain;
     if (p.ntasks > 0) {
         if (cudaMalloc(&p.tasks, sizeof(FlowTask) * h.size()) != cudaSuccess) return nullptr;
         if (cudaMemcpy(p.tasks, h.data(), sizeof(FlowTask) * h.size(), cudaMemcpyHostToDevice) !=
@@ -746,7 +811,11 @@ const Plan* get_plan(int R, int n) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // every SM (measured: 152 CTAs beat 120 and 80 at R = 720; the chain's waits for
     // workers shrink), fewer only when there are fewer tasks than worker groups
-    p.grid = (int)std::min<long>(nsm, 1 + std::max<long>(1, ((long)p.ntasks + kGroups - 1) / kGroups));
+    p.grid = (int)std::min<long>(nsm, 1 + std::max<long>(1, ((long)p.nmain + kGroups - 1) / kGroups));
+    // four critical CTAs on a full grid (seven critical tasks per chain step), else one
+    p.ncrit = p.ntasks > p.nmain ? (p.grid >= 16 ? 4 : 1) : 0;
+    p.grid = std::min(nsm, p.grid + p.ncrit);
+    if (p.grid < 1 + p.ncrit + (p.nmain > 0 ? 1 : 0)) return nullptr;
     if (cudaFuncSetAttribute(k_ldl_flow, cudaFuncAttributeMaxDynamicSharedMemorySize, kFlowSmem) !=
         cudaSuccess)
         return nullptr;
@@ -770,10 +839,13 @@ cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, dou
     const size_t nsync = kSyncHead + (size_t)(p->nT + p->nM) * (1 + p->nT);
     cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * nsync, st);
     if (e != cudaSuccess) return e;
-    FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, p->tasks, p->ntasks, sync, sc, mode};
     // alone on the GPU: one CTA per SM (the chain's SM is not shared); next to other
-    // problems (max_ctas > 0): a few CTAs with just the shared memory they use
-    const int grid = max_ctas > 0 ? std::max(2, std::min(p->grid, max_ctas)) : p->grid;
+    // problems (max_ctas > 0): a few CTAs with just the shared memory they use, one of them
+    // for the critical tasks
+    const int ncrit = max_ctas > 0 ? std::min(p->ncrit, 1) : p->ncrit;
+    const int grid = max_ctas > 0 ? std::max(2 + ncrit, std::min(p->grid, max_ctas)) : p->grid;
+    FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, p->tasks, p->ntasks, p->nmain, ncrit,
+               sync, sc, mode};
     const int smem = max_ctas > 0 ? (int)kFlowSmemUsed : kFlowSmem;
     k_ldl_flow<<<grid, kFlowThreads, smem, st>>>(a);
     count_launch();

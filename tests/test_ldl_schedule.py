@@ -7,7 +7,9 @@ other tasks in list order, each waiting on per-tile progress counters. These tes
 the list from the library and check, independently of the C++ checker, that (1) it holds
 every task exactly once, (2) every task comes after the tasks it waits for, and (3)
 replayed with tile arithmetic under random worker schedules (counters as in the kernel),
-it never deadlocks and reproduces L, D and Y = M L^-T D^-1 from numpy's Cholesky.
+it never deadlocks and reproduces L, D and Y = M L^-T D^-1 from numpy's Cholesky, also
+when, as in the kernel, the tasks of row tile s on panels s-2 and s-3 (those that feed chain
+step s) are taken out of the list and served in order by groups of their own.
 """
 import random
 
@@ -79,10 +81,17 @@ def test_schedule_rejects_out_of_range(api):
         api.thc_cpd_ldl_schedule(16 * 257, 4)
 
 
-def _replay(R, n, tasks, workers, seed):
+def _critical(tk, nT):
+    ty, t, j, k = tk
+    return t < nT and k >= t - 3
+
+
+def _replay(R, n, tasks, workers, seed, crit_workers=0):
     """Run the tasks with `workers` groups claiming tickets in order and a random choice,
     at every step, among the runnable actions (a group whose inputs are ready, or the
-    chain). Tile arithmetic as in the kernel; returns the final augmented matrix."""
+    chain). With crit_workers > 0 the critical tasks form a second list, claimed in order
+    by that many groups of their own. Tile arithmetic as in the kernel; returns the final
+    augmented matrix."""
     rng = np.random.default_rng(seed)
     pick = random.Random(seed)
     nT, nM = _tiles(R, n)
@@ -134,8 +143,14 @@ def _replay(R, n, tasks, workers, seed):
 
     cnt = np.zeros((nT + nM, nT), int)
     sdone = np.zeros(nT + nM, int)
-    fdone = chain = ticket = 0
-    held = [None] * workers
+    fdone = chain = 0
+    if crit_workers:
+        lists = [[x for x in tasks if not _critical(x, nT)], [x for x in tasks if _critical(x, nT)]]
+        lanes = [0] * workers + [1] * crit_workers
+    else:
+        lists, lanes = [tasks], [0] * workers
+    tickets = [0] * len(lists)
+    held = [None] * len(lanes)
 
     def ready(tk):
         ty, t, j, k = tk
@@ -144,16 +159,17 @@ def _replay(R, n, tasks, workers, seed):
         return sdone[t] >= k + 1 and sdone[j] >= k + 1 and cnt[t, j] >= k
 
     while True:
-        for w in range(workers):
-            if held[w] is None and ticket < len(tasks):
-                held[w], ticket = tasks[ticket], ticket + 1
-        acts = [w for w in range(workers) if held[w] is not None and ready(held[w])]
+        for w, lane in enumerate(lanes):
+            if held[w] is None and tickets[lane] < len(lists[lane]):
+                held[w] = lists[lane][tickets[lane]]
+                tickets[lane] += 1
+        acts = [w for w in range(len(lanes)) if held[w] is not None and ready(held[w])]
         if chain < nT and (chain == 0 or (cnt[chain, chain - 1] >= chain - 1 and
                                           cnt[chain, chain] >= chain - 1)):
             acts.append("chain")
         if not acts:
-            assert chain == nT and ticket == len(tasks) and all(h is None for h in held), \
-                "schedule deadlocked"
+            assert chain == nT and all(tk == len(ls) for tk, ls in zip(tickets, lists)) and \
+                all(h is None for h in held), "schedule deadlocked"
             return H, M, Hg
         a = pick.choice(acts)
         if a == "chain":
@@ -178,11 +194,11 @@ def _replay(R, n, tasks, workers, seed):
 
 
 @pytest.mark.parametrize("R,n", [(70, 21), (64, 40), (33, 17), (129, 35)])
-@pytest.mark.parametrize("workers", [1, 3, 64])
-def test_schedule_replay_reproduces_ldlt(api, R, n, workers):
+@pytest.mark.parametrize("workers,crit", [(1, 0), (3, 0), (64, 0), (1, 1), (3, 2), (64, 1)])
+def test_schedule_replay_reproduces_ldlt(api, R, n, workers, crit):
     tasks = api.thc_cpd_ldl_schedule(R, n)
     for seed in (0, 1):
-        H, M, Hg = _replay(R, n, tasks, workers, seed)
+        H, M, Hg = _replay(R, n, tasks, workers, seed, crit)
         C = np.linalg.cholesky(H)
         d = np.diag(C) ** 2
         L = C / np.diag(C)

@@ -22,9 +22,11 @@ constexpr int KBYTES = 128;         // bytes of K per stage (one 128-byte swizzl
 constexpr int TILE_A = BM * KBYTES;  // 16 KB
 constexpr int ACC_COLS = 256;        // one FP32 accumulator (tile N <= 256)
 constexpr int TMEM_COLS = 2 * ACC_COLS;  // two: the epilogue drains one while the next fills
-constexpr int EPI_STAGE_BYTES = 4 * 32 * 17 * 4;  // per-warp 32 x 16 staging of the epilogue
+constexpr int EPI_WARPS = 8;       // two per TMEM lane quarter, alternate 16-column slices
+constexpr int EPI_PITCH = 20;      // floats per staged row (16 + 4: 16-byte rows, no conflicts)
+constexpr int EPI_STAGE_BYTES = EPI_WARPS * 32 * EPI_PITCH * 4;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
-constexpr int NTHREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM, warps 2..5: epilogue
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // warp 0: TMA, warp 1: MMA + TMEM, then epilogue
 
 // ---- PTX wrappers ------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -159,6 +161,7 @@ struct KArgs {
     void* out_hi;
     void* out_lo;
     int ld_split;
+    int vec;           // bit 0: out_f32, bit 1: mul, bit 2: split outputs take 16-/8-byte vectors
 };
 
 template <bool TF32>
@@ -180,12 +183,55 @@ __device__ __forceinline__ void store_split(void* hi, void* lo, size_t idx, floa
     }
 }
 
+// Four consecutive outputs split(e) at idx .. idx + lim - 1 (lim < 4 at the column tail); one
+// vector store per half when `vec` (16 bytes TF32, 8 bytes BF16).
+template <bool TF32>
+__device__ __forceinline__ void store_split4(void* hi, void* lo, size_t idx, const float4& e,
+                                             bool vec, int lim) {
+    const float x[4] = {e.x, e.y, e.z, e.w};
+    if (vec && lim >= 4) {
+        if (TF32) {
+            float h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t b = __float_as_uint(x[u]);
+                h[u] = __uint_as_float((b + 0x1000u) & 0xFFFFE000u);
+                const uint32_t br = __float_as_uint(x[u] - h[u]);
+                l[u] = __uint_as_float((br + 0x1000u) & 0xFFFFE000u);
+            }
+            *(float4*)((float*)hi + idx) = make_float4(h[0], h[1], h[2], h[3]);
+            *(float4*)((float*)lo + idx) = make_float4(l[0], l[1], l[2], l[3]);
+        } else {
+            __nv_bfloat16 h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                h[u] = __float2bfloat16_rn(x[u]);
+                l[u] = __float2bfloat16_rn(x[u] - __bfloat162float(h[u]));
+            }
+            uint2 ph, pl;
+            ph.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+            ph.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+            pl.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+            pl.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+            *(uint2*)((__nv_bfloat16*)hi + idx) = ph;
+            *(uint2*)((__nv_bfloat16*)lo + idx) = pl;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (u < lim) store_split<TF32>(hi, lo, idx + u, x[u]);
+    }
+}
+
 // Persistent split GEMM: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the
 // (N tile, M tile, K split) grid. Warp 0 streams the operand tiles through the TMA ring
 // without stopping between tiles; warp 1 issues the MMAs of tile i into TMEM accumulator
-// i & 1 and commits it; warps 2..5 drain accumulator i & 1 (TMEM -> registers -> fused
-// outputs) while the MMAs of tile i + 1 run into the other one, then release it. Every
-// wait is bounded and records a code when it gives up.
+// i & 1 and commits it; the eight epilogue warps drain accumulator i & 1 while the MMAs of
+// tile i + 1 run into the other one, then release it. An epilogue warp reads 32 rows x 16
+// columns from TMEM (one row per lane) and, for the row-major outputs, restages them in
+// shared memory so that each lane holds 4 consecutive columns of 4 rows: partner loads and
+// output stores are then 16-byte (8-byte for BF16 halves) vectors, 8 rows per instruction.
+// Every wait is bounded and records a code when it gives up.
 template <bool TF32>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
@@ -215,7 +261,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);  // one arrive per epilogue warp
+            mbar_init(&acc_empty[b], EPI_WARPS);  // one arrive per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -292,41 +338,51 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
         }
     } else if (warp >= 2) {
         // ---- epilogue: TMEM -> registers -> fused outputs ----
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        const int q = warp & 3;          // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2;   // slices 16 h, 16 h + 32, ...
         const TcEpilogue& ep = args.ep;
-        float* stg = epi + (warp - 2) * 32 * 17;  // this warp's 32 x 16 staging slice
+        float* stg = epi + (warp - 2) * 32 * EPI_PITCH;  // this warp's 32 x 16 staging
         const bool rowmajor = ep.out_f32 || ep.mul;
-        const int col = lane & 15, half = lane >> 4;
+        const bool vf32 = args.vec & 1, vmul = args.vec & 2, vsplit = args.vec & 4;
+        const int rl = lane >> 2, cg = lane & 3;  // restaged: rows rl + 8k, columns 4cg..4cg+3
         int i = 0;
         for (int t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++i) {
             const int z = t / tnm, r = t % tnm, m0 = (r / args.tn) * BM, n0 = (r % args.tn) * BN;
             const int b = i & 1;
-            const int m = m0 + 32 * q + lane;
+            const int mq = m0 + 32 * q;  // first row of this warp's quarter
+            const int m = mq + lane;
             double* f64t = args.part ? args.part + (size_t)z * args.N * ep.ld_f64t : ep.out_f64t;
-            // partner values of one 32 x 16 slice: lane (col, half) holds rows 2 rr + half
-            float cur[16], nxt[16];
-            auto load_partner = [&](int c, float* dst) {
-                const int n = n0 + c + col;
+            float4 cur[4], nxt[4];
+            auto load_partner = [&](int c, float4* dst) {
+                const int n = n0 + c + 4 * cg;
 #pragma unroll
-                for (int rr = 0; rr < 16; ++rr) {
-                    const int mm = m0 + 32 * q + 2 * rr + half;
-                    dst[rr] = (mm < args.M && n < args.N)
-                                  ? __ldg(ep.mul + (size_t)mm * ep.ld_mul + n)
-                                  : 0.f;
+                for (int k = 0; k < 4; ++k) {
+                    const int mm = mq + rl + 8 * k;
+                    const float* src = ep.mul + (size_t)mm * ep.ld_mul + n;
+                    if (mm < args.M && n + 3 < args.N && vmul) {
+                        dst[k] = __ldg((const float4*)src);
+                    } else {
+                        float e[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            e[u] = (mm < args.M && n + u < args.N) ? __ldg(src + u) : 0.f;
+                        dst[k] = make_float4(e[0], e[1], e[2], e[3]);
+                    }
                 }
             };
+            const int c0 = 16 * h;
             // the first slice's partner loads overlap the main loop
-            if (ep.mul) load_partner(0, cur);
+            if (ep.mul && c0 < BN) load_partner(c0, cur);
             if (!mbar_wait(&acc_full[b], (i >> 1) & 1, 4)) break;
             tc_fence_after();
             const uint32_t acc = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 16) {
+            for (int c = c0; c < BN; c += 32) {
                 float v[16];
                 tmem_ld16(acc + (uint32_t)c, v);
                 // software pipeline: the next slice's partner loads are in flight while this
                 // slice is written
-                if (ep.mul && c + 16 < BN) load_partner(c + 16, nxt);
+                if (ep.mul && c + 32 < BN) load_partner(c + 32, nxt);
                 if (f64t && m < args.M) {
                     // transposed FP64 output: consecutive lanes hold consecutive m (coalesced)
 #pragma unroll
@@ -337,26 +393,40 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUten
                 }
                 if (rowmajor) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
+                    for (int k = 0; k < 4; ++k)
+                        *(float4*)&stg[lane * EPI_PITCH + 4 * k] =
+                            make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                     __syncwarp();
-                    const int n = n0 + c + col;
+                    const int n = n0 + c + 4 * cg;
+                    const int lim = args.N - n;
 #pragma unroll
-                    for (int rr = 0; rr < 16; ++rr) {
-                        const int row = 2 * rr + half;
-                        const int mm = m0 + 32 * q + row;
-                        if (mm < args.M && n < args.N) {
-                            const float d = stg[row * 17 + col];
-                            if (ep.out_f32) ep.out_f32[(size_t)mm * ep.ld_f32 + n] = d;
-                            if (ep.mul)
-                                store_split<TF32>(args.out_hi, args.out_lo,
-                                                  (size_t)mm * args.ld_split + n, d * cur[rr]);
+                    for (int k = 0; k < 4; ++k) {
+                        const int mm = mq + rl + 8 * k;
+                        if (mm >= args.M || lim <= 0) continue;
+                        const float4 d = *(const float4*)&stg[(rl + 8 * k) * EPI_PITCH + 4 * cg];
+                        if (ep.out_f32) {
+                            float* dst = ep.out_f32 + (size_t)mm * ep.ld_f32 + n;
+                            if (vf32 && lim >= 4) {
+                                *(float4*)dst = d;
+                            } else {
+                                const float x[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                                for (int u = 0; u < 4; ++u)
+                                    if (u < lim) dst[u] = x[u];
+                            }
+                        }
+                        if (ep.mul) {
+                            const float4 p = cur[k];
+                            const float4 e = make_float4(d.x * p.x, d.y * p.y, d.z * p.z, d.w * p.w);
+                            store_split4<TF32>(args.out_hi, args.out_lo,
+                                               (size_t)mm * args.ld_split + n, e, vsplit, lim);
                         }
                     }
                     __syncwarp();
                 }
                 if (ep.mul) {
 #pragma unroll
-                    for (int rr = 0; rr < 16; ++rr) cur[rr] = nxt[rr];
+                    for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
                 }
             }
             // every TMEM read of this tile has completed (tcgen05.wait::ld in tmem_ld16)
@@ -477,6 +547,13 @@ cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const Split
     args.out_hi = ep.out_split ? ep.out_split->hi : nullptr;
     args.out_lo = ep.out_split ? ep.out_split->lo : nullptr;
     args.ld_split = ep.out_split ? ep.out_split->pitch : 0;
+    auto al = [](const void* p, int bytes) { return ((uintptr_t)p % bytes) == 0; };
+    args.vec = ((ep.out_f32 && al(ep.out_f32, 16) && ep.ld_f32 % 4 == 0) ? 1 : 0) |
+               ((ep.mul && al(ep.mul, 16) && ep.ld_mul % 4 == 0) ? 2 : 0) |
+               ((args.out_hi && al(args.out_hi, tf32 ? 16 : 8) && al(args.out_lo, tf32 ? 16 : 8) &&
+                 args.ld_split % 4 == 0)
+                    ? 4
+                    : 0);
     const int grid = std::min(args.ntiles, kNumSM);  // persistent: at most one CTA per SM
     ProfScope prof(st, KC_TC, 2.0 * M * (double)N * K);
     count_launch(splits > 1 ? 2 : 1);

@@ -78,20 +78,28 @@ FP64_ALU_PEAK = 152 * 2 * 2 * 2070e6 / 1e12
 
 # DRAM bytes per launch of the dataflow LDL^T kernel, from one ncu capture of one sweep of
 # the default workload (the four modes' launches averaged; ncu starts every launch from a
-# flushed cache, so this is the cold-cache figure), and the SHA-256 of the kernel source it
-# was taken on: reported only while that source is unchanged.
-LDL_TRAFFIC = {"bytes_per_launch": 2749280,
-               "sha256": "67eff755c37932999f6471a5353321a66fd14dd6608c47590694e02e863dc5f7",
-               "source": os.path.join("paper_2502_17683_gb300", "csrc", "ldl_flow.cu")}
+# flushed cache, so this is the cold-cache figure), and the SHA-256 of the kernel's sources
+# (concatenated in this order) it was taken on: reported only while they are unchanged.
+LDL_TRAFFIC = {"bytes_per_launch": 0,
+               "sha256": "",
+               "sources": [os.path.join("paper_2502_17683_gb300", "csrc", f)
+                           for f in ("ldl_flow.cu", "ldl_common.cuh", "common.cuh")]}
+
+
+def ldl_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for src in LDL_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def ldl_traffic():
-    import hashlib
     if not LDL_TRAFFIC["bytes_per_launch"]:
         return None
     try:
-        with open(os.path.join(ROOT, LDL_TRAFFIC["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        sha = ldl_sources_sha256()
     except OSError:
         return None
     return LDL_TRAFFIC["bytes_per_launch"] if sha == LDL_TRAFFIC["sha256"] else None

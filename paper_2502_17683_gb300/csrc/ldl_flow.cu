@@ -58,10 +58,11 @@ constexpr int kFlowSmem = 120 * 1024;      // more than half an SM: one CTA per 
 constexpr unsigned long long kWaitNs = 1000000000ull;
 constexpr int kSyncHead = 5;               // ticket, arrivals, fdone, abort, critical ticket
 constexpr int kMaxTiles = 256;             // largest schedule the host builds
-// Beyond 80 tiles (R > 1280) the solve is bound by FP64 throughput rather than by the
-// pivot chain, and the blocked factorisation's update launches keep the pipes busier
-// (3.25 vs 3.6 ms per solve at R = 1800), so it runs instead.
-constexpr int kFlowMaxTiles = 80;
+// Up to 128 tiles (R <= 2048) the dataflow kernel is at least as fast as the blocked
+// launches (BF16x3 sweeps measured 5.00 vs 6.28 ms at R = 1080, 9.66 vs 10.54 at 1440,
+// 17.55 vs 17.67 at 1800, where the solve turns FP64-throughput bound); beyond, the blocked
+// factorisation runs.
+constexpr int kFlowMaxTiles = 128;
 
 struct FlowTask {
     short type, t, j, k;                   // type 0: S(t, k); 1: U(t, j, k)

@@ -1,6 +1,7 @@
 """Parity at the large paper-shaped size, o=50 v=250 R_thc=1200 R_cp=1800 (decay scale 240),
 through the same entry point and launch configuration as the benchmark (thc_cpd_als, CUDA
-graph replay, automatic factorisation choice: the blocked LDL^T at this R_cp).
+graph replay, automatic factorisation choice: the dataflow LDL^T at this R_cp), and with
+the blocked factorisation the batched driver uses.
 
 The oracle's full ALS sweep at this size takes seconds on the host cores, so the checks are
 one sweep from identical inputs (fit, loss and sampled entries of the reconstructed tensor)
@@ -35,12 +36,13 @@ def case():
     return p, nG2, A_ref, lam_ref, loss_ref, fit_ref
 
 
-def test_fp64_sweep_at_full_size(api, case):
+@pytest.mark.parametrize("ldl", ["auto", "blocked"])
+def test_fp64_sweep_at_full_size(api, case, ldl):
     p, nG2, A_ref, lam_ref, loss_ref, fit_ref = case
     o, v, Rt, R = SHAPE
     d = to_dev(p, torch)
     lam = torch.ones(R, dtype=torch.float64, device="cuda")
-    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 1, 0.0)
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 1, 0.0, ldl=ldl)
     assert out["sweeps"] == 1
     assert abs(out["loss"] - loss_ref) <= 1e-11 * nG2
     assert abs(out["fit"] - fit_ref) <= 1e-10

@@ -776,7 +776,9 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
             if (sweeps_done) *sweeps_done = done_sweeps;
             return set_err(THC_CPD_ERR_NONFINITE, "loss became non-finite at sweep %d", sw);
         }
-        if (h.done) break;
+        // a split-precision run that meets tol (|dfit| fell below 10 tol and tol in one
+        // sweep) still ends with FP64 sweeps: the hand-over above fires next sweep
+        if (h.done && !(split_run && c.prec != THC_CPD_FP64)) break;
     }
     if (opts) opts->flags_out = flags;
     if (sweeps_done) *sweeps_done = done_sweeps;

@@ -115,6 +115,18 @@ def test_mixed_with_fp64_polish_reaches_fp64_converged_fit(api, prec):
     assert abs(out["fit"] - ref["fits"][-1]) <= 1e-6 * abs(ref["fits"][-1])
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_split_run_meeting_tol_ends_with_fp64_sweeps(api, prec):
+    # tol so loose that |dfit| < tol (and < 10 tol) at the first comparison, sweep 2: the
+    # run does not stop in split precision but hands over and stops after one FP64 sweep
+    p = make_problem(5, 15, 60, 80, seed=1)
+    d = to_dev(p, torch)
+    lam = torch.ones(80, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 50, 1.0, precision=prec)
+    assert out["flags"] & 4
+    assert out["sweeps"] == 3
+
+
 def test_mixed_small_workload_trajectory(api):
     p = make_problem(5, 15, 60, 80, seed=0)
     d = to_dev(p, torch)

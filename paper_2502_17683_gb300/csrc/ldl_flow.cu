@@ -95,6 +95,7 @@ struct ChainSmem {
     volatile int valid[2];   // buffer holds complete tiles (0: the launch is aborting)
     volatile int full[2];    // last step written to buffer b
     volatile int empty[2];   // last step the chain has taken out of buffer b
+    volatile int live;       // 0 once the chain is aborting: the publisher releases nothing
 };
 
 struct WorkerSmem {
@@ -153,11 +154,17 @@ __device__ bool flow_wait(const int* const (&p)[N], const int (&v)[N], int* abor
     }
 }
 
-constexpr int kPublisher = 224;  // chain thread that fences and releases the progress flags
+constexpr int kPublisher = 224;  // chain thread that reports a failed pivot
+constexpr int kProducerThreads = 224;  // warps 8-14 prefetch the chain's tiles
+// Warp 15 publishes the chain's progress: after bar.arrive 7 / 8 by the 256 chain threads
+// (tile (s, s-1) substituted; tile (s, s) factorised) it fences and releases sdone[s] /
+// fdone, so that the fence's latency is not on the chain's path.
 
 // Barrier of the chain's compute threads 0..255 (the producer warps 8-15 run apart).
 __device__ __forceinline__ void chain_sync() { asm volatile("bar.sync 5, 256;" ::: "memory"); }
-__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 6, 256;" ::: "memory"); }
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 6, 224;" ::: "memory"); }
+__device__ __forceinline__ void chain_arrive_subst() { asm volatile("bar.arrive 7, 288;" ::: "memory"); }
+__device__ __forceinline__ void chain_arrive_factor() { asm volatile("bar.arrive 8, 288;" ::: "memory"); }
 
 // Bounded wait for a shared-memory step counter written by the other half of the chain
 // CTA: *p >= v (true), or the launch aborts / the wait gives up (false).
@@ -290,10 +297,9 @@ __device__ __forceinline__ int* cnt_of(const FlowArgs& a) {
 // flags it, so the chain finds them in shared memory; a buffer is reused once the chain
 // has taken its previous content out.
 __device__ void flow_producer(const FlowArgs& a, ChainSmem& S) {
-    const int t2 = threadIdx.x - 256, R = a.R, nT = a.nT;
+    const int t2 = threadIdx.x - 256, R = a.R, nT = a.nT;  // 0 .. kProducerThreads - 1
     int* abort_flag = a.sync + 3;
     int* cnt = cnt_of(a);
-    const int rr = t2 >> 4, cc = t2 & 15;
     for (int sn = 1; sn < nT; ++sn) {
         const int b = sn & 1;
         if (t2 == 0) {
@@ -309,9 +315,12 @@ __device__ void flow_producer(const FlowArgs& a, ChainSmem& S) {
         const bool ok = S.pstat;
         if (ok) {
             const int n0 = sn * FB, nb = min(FB, R - n0);
-            S.Bn[b][rr][cc] = rr < nb ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 - FB + cc) : 0.0;
-            S.Dn[b][rr][cc] =
-                (rr < nb && cc <= rr) ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 + cc) : 0.0;
+            for (int e = t2; e < FB * FB; e += kProducerThreads) {
+                const int rr = e >> 4, cc = e & 15;
+                S.Bn[b][rr][cc] = rr < nb ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 - FB + cc) : 0.0;
+                S.Dn[b][rr][cc] =
+                    (rr < nb && cc <= rr) ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 + cc) : 0.0;
+            }
         }
         producer_sync();
         if (t2 == 0) {
@@ -326,12 +335,11 @@ __device__ void flow_producer(const FlowArgs& a, ChainSmem& S) {
 // The critical path (threads 0..255): for s = 0..T-1, S(s, s-1), U(s, s, s-1), F(s).
 __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
     const int tid = threadIdx.x, R = a.R, nT = a.nT;
-    int* fdone = a.sync + 2;
     int* abort_flag = a.sync + 3;
-    int* sdone = sdone_of(a);
     const double tau = (double)R * DBL_EPSILON * a.sc->maxdiag;
     const int r = tid >> 4, c = tid & 15;  // element of a tile
     int bad = 0;
+    int s_end = nT;  // the step the loop stopped at (nT: all done)
     for (int s = 0; s < nT; ++s) {
         const int s0 = s * FB, sb = min(FB, R - s0), b = s & 1;
         double dss = 0.0, x = 0.0;
@@ -340,7 +348,10 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
         } else {
             if (tid == 0) S.ok = smem_wait(&S.full[b], s, abort_flag) && S.valid[b];
             chain_sync();
-            if (!S.ok) break;
+            if (!S.ok) {
+                s_end = s;
+                break;
+            }
             dss = S.Dn[b][r][c];
             x = S.Bn[b][r][c];
             // X L_{s-1}^T = B: column sweep, x[r][q] passed along the row's half-warp
@@ -357,13 +368,8 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
             S.Xs[r][c] = x;
             S.Ls[r][c] = l;
             chain_sync();
-            // published by a thread of warp 7 (idle in the tile factorisation), so that the
-            // fence does not hold up thread 0's pivot chain
-            if (tid == kPublisher) {
-                S.empty[b] = s;  // buffer b read out (before the barrier above)
-                __threadfence();
-                st_release(&sdone[s], s);
-            }
+            if (tid == 0) S.empty[b] = s;  // buffer b read out (before the barrier above)
+            chain_arrive_subst();          // the publisher warp releases sdone[s]
             if (c <= r) {
                 double a0 = 0.0, a1 = 0.0;
 #pragma unroll
@@ -384,12 +390,38 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
         if (tid < FB) S.dp[tid] = tid < sb ? S.dinv[tid] : 0.0;
         bad |= S.bad;
         chain_sync();
-        if (tid == kPublisher) {
+        chain_arrive_factor();  // the publisher warp releases fdone = s + 1
+    }
+    if (s_end < nT) {
+        // aborting (a wait gave up): run out the publisher's barriers, releasing nothing
+        if (tid == 0) S.live = 0;
+        for (int s2 = s_end; s2 < nT; ++s2) {
+            if (s2 > 0) chain_arrive_subst();
+            chain_arrive_factor();
+        }
+    }
+    if (tid == kPublisher && bad) atomicOr(&a.sc->fail_mask, 1 << a.mode);
+}
+
+// Warp 15: releases the chain's progress flags (see chain_arrive_*); the fences run here.
+__device__ void flow_publisher(const FlowArgs& a, ChainSmem& S) {
+    const int lane = threadIdx.x & 31;
+    int* fdone = a.sync + 2;
+    int* sdone = sdone_of(a);
+    for (int s = 0; s < a.nT; ++s) {
+        if (s > 0) {
+            asm volatile("bar.sync 7, 288;" ::: "memory");
+            if (lane == 0 && S.live) {
+                __threadfence();
+                st_release(&sdone[s], s);
+            }
+        }
+        asm volatile("bar.sync 8, 288;" ::: "memory");
+        if (lane == 0 && S.live) {
             __threadfence();
             st_release(fdone, s + 1);
         }
     }
-    if (tid == kPublisher && bad) atomicOr(&a.sc->fail_mask, 1 << a.mode);
 }
 
 // Rows of row tile t: [r0, rlim) with r0 = first row (H rows, then M rows).
@@ -531,6 +563,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) k_ldl_flow(FlowArgs a) {
         ChainSmem& S = *reinterpret_cast<ChainSmem*>(smem);
         for (int e = threadIdx.x; e < FB * (FB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code<FB>(e);
         if (threadIdx.x < FB * FB) S.L[threadIdx.x >> 4][threadIdx.x & 15] = 0.0;
+        if (threadIdx.x == 0) S.live = 1;
         if (threadIdx.x < 2) {
             S.full[threadIdx.x] = 0;
             S.empty[threadIdx.x] = 0;
@@ -538,8 +571,10 @@ __global__ void __launch_bounds__(kFlowThreads, 1) k_ldl_flow(FlowArgs a) {
         __syncthreads();
         if (threadIdx.x < 256)
             flow_chain(a, S);
-        else
+        else if (threadIdx.x < 256 + kProducerThreads)
             flow_producer(a, S);
+        else
+            flow_publisher(a, S);
     } else {
         WorkerSmem* ws = reinterpret_cast<WorkerSmem*>(smem);
         const int g = threadIdx.x >> 7;

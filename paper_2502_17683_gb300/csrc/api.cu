@@ -239,6 +239,9 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     c.counters = ar.take<int>(cdiv(R, 32));
     c.flow_sync = ar.take<int>(flow_sync_ints(R, nmax));
     c.bs_sync = ar.take<int>(bsolve_sync_ints(nmax));
+    // zero once: every launch that uses them leaves them zero again
+    CK(cudaMemsetAsync(c.flow_sync, 0, sizeof(int) * flow_sync_ints(R, nmax), c.st));
+    CK(cudaMemsetAsync(c.bs_sync, 0, sizeof(int) * bsolve_sync_ints(nmax), c.st));
     c.part = ar.take<double>(pc);
     c.red = ar.take<double>(loss_red_need() + 2 * kNumSM * 2);
     c.ones = ar.take<double>(R);

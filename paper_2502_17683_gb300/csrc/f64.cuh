@@ -26,13 +26,13 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   A pivot <= R * eps * sc->maxdiag sets bit `mode` of sc->fail_mask (the result is then
 //   garbage and the caller replays the mode with the pseudo-inverse).
 //   counters: cdiv(R, 32) ints (arrival counters of the update kernels, cleared inside).
-//   flow_sync: flow_sync_ints(R, n) ints, or null: with it (and a plan for (R, n)) the
-//   factorisation runs as one persistent dataflow launch (P is then R x R), else as one
-//   launch per block step.
+//   flow_sync: flow_sync_ints(R, n) ints, zero before the first use (each launch leaves
+//   them zero), or null: with it (and a plan for (R, n)) the factorisation runs as one
+//   persistent dataflow launch (P is then R x R), else as one launch per block step.
 //   flow_ctas: 0 = the dataflow kernel takes one CTA per SM; > 0 = at most that many CTAs
 //   with only the shared memory they use (problems running side by side).
 //   bs_sync: bsolve_sync_ints(n) ints, the progress counters of the backward solve (by
-//   column slices, ldl_flow.cu).
+//   column slices, ldl_flow.cu); zero before the first use, left zero by each launch.
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
                 int* bs_sync);

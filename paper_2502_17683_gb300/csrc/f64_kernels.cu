@@ -577,12 +577,13 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
 // column normalisation, loss, norms
 // ------------------------------------------------------------------------------------
 // lam_r = ||A[:, r]||_2 (32 columns x 8 row slices per block, fixed-order reduction) and
-// the reciprocal, then A[:, r] *= 1 / lam_r: one sqrt and one divide per column instead of
-// a divide per element (a divide costs ~430 clocks on GB300's FP64 pipe).
+// the reciprocal, then A[:, r] *= 1 / lam_r by the same block (it owns its 32 columns over
+// all rows): one sqrt and one divide per column instead of a divide per element (a divide
+// costs ~430 clocks on GB300's FP64 pipe), one launch per normalisation.
 __global__ void __launch_bounds__(256)
-k_colnorm(int n, int R, const double* __restrict__ A, double* __restrict__ lam,
-          double* __restrict__ inv) {
+k_colnorm(int n, int R, double* __restrict__ A, double* __restrict__ lam) {
     __shared__ double sh[8][33];
+    __shared__ double inv[32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int r = blockIdx.x * 32 + tx;
     double s = 0.0;
@@ -593,27 +594,29 @@ k_colnorm(int n, int R, const double* __restrict__ A, double* __restrict__ lam,
         }
     sh[ty][tx] = s;
     __syncthreads();
-    if (ty == 0 && r < R) {
-        double t = 0.0;
-        for (int k = 0; k < 8; ++k) t += sh[k][tx];
-        const double l = sqrt(t);
-        lam[r] = l;
-        inv[r] = l > 0.0 ? 1.0 / l : 1.0;  // zero columns are left as they are
+    if (ty == 0) {
+        double f = 1.0;
+        if (r < R) {
+            double t = 0.0;
+            for (int k = 0; k < 8; ++k) t += sh[k][tx];
+            const double l = sqrt(t);
+            lam[r] = l;
+            f = l > 0.0 ? 1.0 / l : 1.0;  // zero columns are left as they are
+        }
+        inv[tx] = f;
+    }
+    __syncthreads();
+    if (r < R) {
+        const double f = inv[tx];
+        for (int i = ty; i < n; i += 8) A[(size_t)i * R + r] *= f;
     }
 }
 
-__global__ void k_colscale(long total, int R, double* __restrict__ A, const double* __restrict__ inv) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
-         i += (long)gridDim.x * blockDim.x)
-        A[i] *= inv[i % R];
-}
-
 void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch) {
+    (void)scratch;
     ProfScope prof(st, KC_AUX, 3.0 * n * R, 24.0 * n * R);
-    count_launch(2);
-    k_colnorm<<<cdiv(R, 32), 256, 0, st>>>(n, R, A, lam, scratch);
-    const long total = (long)n * R;
-    k_colscale<<<(int)std::min<long>(cdiv(total, 256), 4L * kNumSM), 256, 0, st>>>(total, R, A, scratch);
+    count_launch(1);
+    k_colnorm<<<cdiv(R, 32), 256, 0, st>>>(n, R, A, lam);
 }
 
 constexpr int RED_BLOCKS = 2 * kNumSM;

@@ -56,7 +56,7 @@ constexpr int kGroups = 4;                 // worker groups (128 threads) per CT
 constexpr int kFlowThreads = 128 * kGroups;
 constexpr int kFlowSmem = 120 * 1024;      // more than half an SM: one CTA per SM
 constexpr unsigned long long kWaitNs = 1000000000ull;
-constexpr int kSyncHead = 5;               // ticket, arrivals, fdone, abort, critical ticket
+constexpr int kSyncHead = 6;  // ticket, arrivals, fdone, abort, critical ticket, CTAs done
 constexpr int kMaxTiles = 256;             // largest schedule the host builds
 // Up to 128 tiles (R <= 2048) the dataflow kernel is at least as fast as the blocked
 // launches (BF16x3 sweeps measured 5.00 vs 6.28 ms at R = 1080, 9.66 vs 10.54 at 1440,
@@ -282,7 +282,8 @@ struct FlowArgs {
     const FlowTask* tasks;  // [0, nmain): served by the worker CTAs; [nmain, ntasks): the
     int ntasks, nmain;      // critical tasks, served by the critical CTAs
     int ncrit;              // critical CTAs (one group each), roles 1..ncrit
-    int* sync;
+    int* sync;              // nsync progress ints, zero at entry; the last CTA out re-zeroes them
+    int nsync;
     DevScalars* sc;
     int mode;
 };
@@ -586,6 +587,18 @@ __global__ void __launch_bounds__(kFlowThreads, 1) k_ldl_flow(FlowArgs a) {
             flow_worker(a, ws[g], g, a.tasks, a.nmain, a.sync);
         }
     }
+    // the last CTA out clears this launch's counters for the next one (no memset node)
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(a.sync + 5, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        for (int i = threadIdx.x; i < a.nsync; i += blockDim.x) a.sync[i] = 0;
+    }
 }
 
 constexpr size_t kFlowSmemUsed = sizeof(ChainSmem) > kGroups * sizeof(WorkerSmem)
@@ -613,7 +626,7 @@ struct BsArgs {
     double* A;
     const double* H;
     int R, n, nJ, C;
-    int* sync;  // [0] ticket, [1] abort, [2 + r] prog of row r
+    int* sync;  // [0] ticket, [1] abort, [2] CTAs done, [3 + r] prog of row r; zero at entry
 };
 
 // 32-term dot product in four independent FMA chains (fixed order)
@@ -631,10 +644,10 @@ __device__ __forceinline__ double dot32(const double* x, const double* h) {
 
 __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
     __shared__ double as[2][BB];
-    __shared__ int tk, kmin, ok;
+    __shared__ int tk, kmin, ok, last;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, R = a.R;
     int* abort_flag = a.sync + 1;
-    int* prog = a.sync + 2;
+    int* prog = a.sync + 3;
     for (;;) {
         if (tid == 0) tk = atomicAdd(a.sync, 1);
         __syncthreads();
@@ -713,6 +726,17 @@ __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
             }
         }
         __syncthreads();  // tk is rewritten by the next claim
+    }
+    // the last CTA out clears the counters for the next launch (no memset node)
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(a.sync + 2, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        for (int i = tid; i < 3 + a.n; i += blockDim.x) a.sync[i] = 0;
     }
 }
 
@@ -872,29 +896,25 @@ cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, dou
                      DevScalars* sc, int mode, int* sync, int max_ctas) {
     const Plan* p = get_plan(R, n);
     if (!p) return cudaErrorInvalidValue;
-    const size_t nsync = kSyncHead + (size_t)(p->nT + p->nM) * (1 + p->nT);
-    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * nsync, st);
-    if (e != cudaSuccess) return e;
+    const int nsync = kSyncHead + (p->nT + p->nM) * (1 + p->nT);
     // alone on the GPU: one CTA per SM (the chain's SM is not shared); next to other
     // problems (max_ctas > 0): a few CTAs with just the shared memory they use, one of them
     // for the critical tasks
     const int ncrit = max_ctas > 0 ? std::min(p->ncrit, 1) : p->ncrit;
     const int grid = max_ctas > 0 ? std::max(2 + ncrit, std::min(p->grid, max_ctas)) : p->grid;
     FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, p->tasks, p->ntasks, p->nmain, ncrit,
-               sync, sc, mode};
+               sync, nsync, sc, mode};
     const int smem = max_ctas > 0 ? (int)kFlowSmemUsed : kFlowSmem;
     k_ldl_flow<<<grid, kFlowThreads, smem, st>>>(a);
     count_launch();
     return cudaGetLastError();
 }
 
-size_t bsolve_sync_ints(int nmax) { return 2 + (size_t)nmax; }
+size_t bsolve_sync_ints(int nmax) { return 3 + (size_t)nmax; }
 
 cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, double* A,
                           const double* H, int* sync) {
     if (n <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * bsolve_sync_ints(n), st);
-    if (e != cudaSuccess) return e;
     const int nJ = cdiv(R, BB), C = cdiv(R, kSlice);
     BsArgs a{Yf, A, H, R, n, nJ, C, sync};
     const int grid = std::min(n * C, kNumSM * 4);

@@ -14,9 +14,12 @@
 //   F(s)      LDL^T of the diagonal tile (s, s)                       [chain]
 //   S(t, k)   X L_kk^T = B for tile (t, k), then L = X D_k^-1            [chain if t = k+1]
 //   U(t,j,k)  tile (t, j) -= L(t, k) X(j, k)^T (lower half if t = j)   [chain if t = j = k+1]
-// Chain step s runs S(s, s-1), U(s, s, s-1), F(s) back to back in shared memory. The
-// other tasks form one list in a fixed order; worker groups (128 threads) claim entries
-// with an atomic ticket and wait for their inputs on per-tile progress counters:
+// Chain step s runs S(s, s-1), U(s, s, s-1), F(s) back to back in shared memory (warps 0-7
+// of the chain CTA; warps 8-14 prefetch its next two tiles, warp 15 publishes its
+// progress). The other tasks form one list in a fixed order, split into the critical
+// tasks (row tile s on panels s-2, s-3), served by CTAs of their own, and the rest; worker
+// groups (128 threads) claim entries with an atomic ticket and wait for their inputs on
+// per-tile progress counters:
 //   sdone[t] = k + 1 once S(t, k) is stored; cnt[t][j] = number of panels applied to tile
 //   (t, j); fdone = s + 1 once F(s) is stored.
 // Every tile receives its updates in panel order (a U task waits for the previous panel's
@@ -160,7 +163,7 @@ constexpr int kProducerThreads = 224;  // warps 8-14 prefetch the chain's tiles
 // (tile (s, s-1) substituted; tile (s, s) factorised) it fences and releases sdone[s] /
 // fdone, so that the fence's latency is not on the chain's path.
 
-// Barrier of the chain's compute threads 0..255 (the producer warps 8-15 run apart).
+// Barrier of the chain's compute threads 0..255 (producer and publisher warps run apart).
 __device__ __forceinline__ void chain_sync() { asm volatile("bar.sync 5, 256;" ::: "memory"); }
 __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 6, 224;" ::: "memory"); }
 __device__ __forceinline__ void chain_arrive_subst() { asm volatile("bar.arrive 7, 288;" ::: "memory"); }
@@ -293,7 +296,7 @@ __device__ __forceinline__ int* cnt_of(const FlowArgs& a) {
     return a.sync + kSyncHead + a.nT + a.nM;
 }
 
-// Producer half of the chain CTA (warps 8-15): for steps s = 1..T-1, waits until tiles
+// Producer warps of the chain CTA (8-14): for steps s = 1..T-1, waits until tiles
 // (s, s-1) and (s, s) hold all updates through panel s-2, copies them into buffer s & 1 and
 // flags it, so the chain finds them in shared memory; a buffer is reused once the chain
 // has taken its previous content out.

@@ -211,7 +211,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, **{k: W[k] for k in ("o", "v", "Rt", "R")},
+        "config": {"workload": WORKLOAD, "o": W["o"], "v": W["v"], "R_thc": W["Rt"],
+                   "R_cp": W["R"], "sweeps_per_step": W["sweeps"], "precision": "fp64",
                    "note": "each step is a bounded sample of sweeps of the workload"},
         "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": os.cpu_count(),
                          "kind": "oracle", "sample": f"{sweeps} sweeps over {args.steps} steps, "

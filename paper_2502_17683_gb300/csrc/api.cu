@@ -670,11 +670,16 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
             else
                 eval = tol > 0.0 || sw == max_sweeps;
         }
-        for (int k = 0; k < 4; ++k)
-            CK(cudaMemcpyAsync(c.Asnap[k], A[k], sizeof(double) * s.n[k] * R,
-                               cudaMemcpyDeviceToDevice, c.st));
-        CK(cudaMemcpyAsync(c.lamsnap, lam, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
-        CK(cudaMemcpyAsync(c.sc_snap, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+        {
+            // the state before this sweep, for a rollback: one launch
+            static_assert(sizeof(DevScalars) % sizeof(double) == 0, "DevScalars in doubles");
+            const double* src[6] = {A[0], A[1], A[2], A[3], lam, (const double*)c.sc};
+            double* dst[6] = {c.Asnap[0], c.Asnap[1], c.Asnap[2], c.Asnap[3], c.lamsnap,
+                              (double*)c.sc_snap};
+            const long len[6] = {(long)s.n[0] * R, (long)s.n[1] * R, (long)s.n[2] * R,
+                                 (long)s.n[3] * R, (long)R, (long)(sizeof(DevScalars) / sizeof(double))};
+            CK(copy_many(c.st, 6, src, dst, len));
+        }
         int used = 0;
         if (tune && sw == 1) {
             CKS(sweep(c, A, lam, false, eval, tol, &used));  // tuned on live operands

@@ -55,6 +55,11 @@ cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, doubl
 // lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column); scratch >= R doubles.
 void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch);
 
+// dst[p][0 .. len[p]) = src[p][...] for p < np (np <= 8) in one launch (the state snapshot
+// taken before every sweep for a rollback).
+cudaError_t copy_many(cudaStream_t st, int np, const double* const* src, double* const* dst,
+                      const long* len);
+
 // Loss in factor form after a sweep: inner = sum lam_r Y[Q,r] W3[Q,r] W4[Q,r],
 // cpdn2 = lam^T (G1 o G2 o G3 o G4) lam; loss, fit, convergence into sc.
 void loss_eval(cudaStream_t st, int Rt, int R, const double* Y, const double* W3,

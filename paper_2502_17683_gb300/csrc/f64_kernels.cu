@@ -619,6 +619,37 @@ void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, do
     k_colnorm<<<cdiv(R, 32), 256, 0, st>>>(n, R, A, lam);
 }
 
+struct CopyMany {
+    const double* src[8];
+    double* dst[8];
+    long len[8];
+    int np;
+};
+
+__global__ void __launch_bounds__(256) k_copy_many(CopyMany a) {
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (int p = 0; p < a.np; ++p)
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < a.len[p]; i += stride)
+            a.dst[p][i] = a.src[p][i];
+}
+
+cudaError_t copy_many(cudaStream_t st, int np, const double* const* src, double* const* dst,
+                      const long* len) {
+    if (np < 1 || np > 8) return cudaErrorInvalidValue;
+    CopyMany a{};
+    long total = 0;
+    for (int p = 0; p < np; ++p) {
+        a.src[p] = src[p];
+        a.dst[p] = dst[p];
+        a.len[p] = len[p];
+        total += len[p];
+    }
+    a.np = np;
+    count_launch();
+    k_copy_many<<<(int)std::max<long>(1, std::min<long>(cdiv(total, 256), 2L * kNumSM)), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 constexpr int RED_BLOCKS = 2 * kNumSM;
 constexpr int RED_THREADS = 256;
 

@@ -119,6 +119,15 @@ DevScalars* host_scalars() {
     return h;
 }
 
+// Two pinned slots for the scalars of consecutive sweeps of a pipelined run.
+DevScalars* host_scalar_slots() {
+    thread_local DevScalars* h = nullptr;
+    if (!h) {
+        if (cudaMallocHost((void**)&h, 2 * sizeof(DevScalars)) != cudaSuccess) h = nullptr;
+    }
+    return h;
+}
+
 // Everything one call needs on the device, carved from a single stream-ordered block.
 struct Ctx {
     Shape s;
@@ -144,9 +153,13 @@ struct Ctx {
     double* red = nullptr;
     double* ones = nullptr;
     DevScalars* sc = nullptr;
-    DevScalars* sc_snap = nullptr;
+    DevScalars* sc_snap = nullptr;  // rollback snapshot in use (one of the two slots below)
     double* Asnap[4] = {};
     double* lamsnap = nullptr;
+    DevScalars* sc_slot[2] = {};    // the state before sweeps of either parity
+    double* Asnap_slot[2][4] = {};
+    double* lamsnap_slot[2] = {};
+    cudaEvent_t ev_sc[2] = {nullptr, nullptr};  // a sweep's scalars reached the host slot
     // ||G||^2 set-up
     double* S = nullptr;
     double* T = nullptr;
@@ -169,6 +182,8 @@ struct Ctx {
     ~Ctx() {
         for (auto& g : gexec)
             if (g) cudaGraphExecDestroy(g);
+        for (auto& e : ev_sc)
+            if (e) cudaEventDestroy(e);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (gst) cudaStreamDestroy(gst);
@@ -219,9 +234,10 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     bytes += Arena::need<double>(loss_red_need() + 2 * kNumSM * 2);
     bytes += Arena::need<double>(R);
     bytes += 2 * Arena::need<DevScalars>(1);
-    if (need & NEED_ALS) {
-        bytes += 2 * Arena::need<double>((size_t)s.o * R) + 2 * Arena::need<double>((size_t)s.v * R);
-        bytes += Arena::need<double>(R);
+    if (need & NEED_ALS) {  // two rollback snapshots (pipelined runs alternate)
+        bytes += Arena::need<DevScalars>(1);
+        bytes += 2 * (2 * Arena::need<double>((size_t)s.o * R) + 2 * Arena::need<double>((size_t)s.v * R));
+        bytes += 2 * Arena::need<double>(R);
     }
     if (need & NEED_NORM) bytes += 3 * Arena::need<double>((size_t)Rt * Rt);
     const bool mixed = c.prec != THC_CPD_FP64;
@@ -248,8 +264,14 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     c.sc = ar.take<DevScalars>(1);
     c.sc_snap = ar.take<DevScalars>(1);
     if (need & NEED_ALS) {
-        for (int k = 0; k < 4; ++k) c.Asnap[k] = ar.take<double>((size_t)s.n[k] * R);
-        c.lamsnap = ar.take<double>(R);
+        c.sc_slot[0] = c.sc_snap;
+        c.sc_slot[1] = ar.take<DevScalars>(1);
+        for (int b = 0; b < 2; ++b) {
+            for (int k = 0; k < 4; ++k) c.Asnap_slot[b][k] = ar.take<double>((size_t)s.n[k] * R);
+            c.lamsnap_slot[b] = ar.take<double>(R);
+        }
+        for (int k = 0; k < 4; ++k) c.Asnap[k] = c.Asnap_slot[0][k];
+        c.lamsnap = c.lamsnap_slot[0];
     }
     if (need & NEED_NORM) {
         c.S = ar.take<double>((size_t)Rt * Rt);
@@ -610,6 +632,35 @@ void build_trial(Ctx& c, LearnWs& L, double* const A[4], const double* lam, doub
     lam_product(c.st, R, lk, L.lamT);
 }
 
+// Rollback snapshot: point the snapshot at slot b, copy the state (factors, lam, scalars)
+// there in one launch; and the way back.
+void use_snapshot_slot(Ctx& c, int b) {
+    for (int k = 0; k < 4; ++k) c.Asnap[k] = c.Asnap_slot[b][k];
+    c.lamsnap = c.lamsnap_slot[b];
+    c.sc_snap = c.sc_slot[b];
+}
+
+thc_cpd_status take_snapshot(Ctx& c, double* const A[4], const double* lam) {
+    static_assert(sizeof(DevScalars) % sizeof(double) == 0, "DevScalars in doubles");
+    const int R = c.s.R;
+    const double* src[6] = {A[0], A[1], A[2], A[3], lam, (const double*)c.sc};
+    double* dst[6] = {c.Asnap[0], c.Asnap[1], c.Asnap[2], c.Asnap[3], c.lamsnap, (double*)c.sc_snap};
+    const long len[6] = {(long)c.s.n[0] * R, (long)c.s.n[1] * R, (long)c.s.n[2] * R,
+                         (long)c.s.n[3] * R, (long)R, (long)(sizeof(DevScalars) / sizeof(double))};
+    CK(copy_many(c.st, 6, src, dst, len));
+    return THC_CPD_OK;
+}
+
+thc_cpd_status restore_snapshot(Ctx& c, double* const A[4], double* lam) {
+    const int R = c.s.R;
+    for (int k = 0; k < 4; ++k)
+        CK(cudaMemcpyAsync(A[k], c.Asnap[k], sizeof(double) * c.s.n[k] * R, cudaMemcpyDeviceToDevice,
+                           c.st));
+    CK(cudaMemcpyAsync(lam, c.lamsnap, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
+    CK(cudaMemcpyAsync(c.sc, c.sc_snap, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+    return THC_CPD_OK;
+}
+
 // The ALS driver shared by thc_cpd_als, thc_cpd_als_sweep and the trajectory recorder.
 thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
                        const double* Z, double* const A[4], double* lam, int max_sweeps,
@@ -652,7 +703,91 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
     double fit1 = nan(""), fit2 = nan("");  // fits of the last two evaluated sweeps
     bool use_graph = !prof_on() && getenv("THC_CPD_NO_GRAPH") == nullptr;
     const bool tune = opts && opts->autotune && split_run;
-    for (int sw = 1; sw <= max_sweeps; ++sw) {
+    // Fixed-length runs (tol <= 0: no convergence stop; the FP64 hand-over at a known sweep)
+    // are pipelined: sweep s+1 is queued before the host reads sweep s's scalars, so the GPU
+    // does not idle for the round trip. The state before each sweep goes to the snapshot
+    // slot of its parity; if sweep s reports a failed pivot, the speculative sweep s+1 is
+    // undone with sweep s's own rollback and sweep s is replayed exactly as below.
+    DevScalars* hs2 = host_scalar_slots();
+    const bool pipe = use_graph && !learning && !tune && tol <= 0.0 && max_sweeps >= 2 && hs2;
+    if (pipe) {
+        for (int b = 0; b < 2; ++b)
+            if (!c.ev_sc[b]) CK(cudaEventCreateWithFlags(&c.ev_sc[b], cudaEventDisableTiming));
+        bool evals[2] = {false, false};
+        auto hand_over_at = [&](int sw) {
+            return split_run && c.prec != THC_CPD_FP64 && polish > 0 && sw > max_sweeps - polish;
+        };
+        auto launch = [&](int sw) -> thc_cpd_status {
+            if (hand_over_at(sw)) {
+                c.prec = THC_CPD_FP64;
+                refresh_state(c, A);
+                flags |= 4;
+            }
+            bool eval = true;
+            if (c.prec != THC_CPD_FP64) eval = (loss_every > 0 && sw % loss_every == 0) || sw == max_sweeps;
+            const int b = sw & 1;
+            use_snapshot_slot(c, b);
+            CKS(take_snapshot(c, A, lam));
+            CKS(fast_sweep(c, A, lam, eval, tol, &use_graph));
+            CK(cudaMemcpyAsync(hs2 + b, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.st));
+            CK(cudaEventRecord(c.ev_sc[b], c.st));
+            evals[b] = eval;
+            return THC_CPD_OK;
+        };
+        CKS(launch(1));
+        int next = 2;  // the next sweep to queue
+        for (int sw = 1; sw <= max_sweeps; ++sw) {
+            const int b = sw & 1;
+            // queue sweep sw + 1 unless it starts the FP64 phase (that refreshes the state
+            // from the factors, which must be final)
+            bool spec = false;
+            if (next == sw + 1 && sw + 1 <= max_sweeps && !hand_over_at(sw + 1)) {
+                CKS(launch(sw + 1));
+                next = sw + 2;
+                spec = true;
+            }
+            CK(cudaEventSynchronize(c.ev_sc[b]));
+            h = hs2[b];
+            const bool eval = evals[b];
+            int used = 0;
+            if (h.fail_mask) {
+                // undo the speculative sweep, then roll back and replay sweep sw with a host
+                // check after every factorisation
+                CK(cudaStreamSynchronize(c.st));
+                use_snapshot_slot(c, b);
+                CKS(restore_snapshot(c, A, lam));
+                refresh_state(c, A);
+                CKS(ctx_safe_buffers(c));
+                CKS(sweep(c, A, lam, true, eval, tol, &used));
+                CKS(read_scalars(c, &h));
+                flags |= 2;
+                next = sw + 1;
+                spec = false;
+            }
+            if (used) flags |= 1;
+            done_sweeps = sw;
+            if (opts && opts->history) {
+                opts->history[2 * (sw - 1)] = eval ? h.loss : nan("");
+                opts->history[2 * (sw - 1) + 1] = eval ? h.fit : nan("");
+            }
+            if (eval && (h.nonfinite || !isfinite(h.loss))) {
+                if (spec) {  // leave the factors as sweep sw made them
+                    CK(cudaStreamSynchronize(c.st));
+                    use_snapshot_slot(c, (sw + 1) & 1);
+                    CKS(restore_snapshot(c, A, lam));
+                    CK(cudaStreamSynchronize(c.st));
+                }
+                if (opts) opts->flags_out = flags;
+                if (sweeps_done) *sweeps_done = done_sweeps;
+                return set_err(THC_CPD_ERR_NONFINITE, "loss became non-finite at sweep %d", sw);
+            }
+            if (next == sw + 1 && sw + 1 <= max_sweeps) {
+                CKS(launch(sw + 1));
+                next = sw + 2;
+            }
+        }
+    }
+    for (int sw = 1; sw <= max_sweeps && !pipe; ++sw) {
         if (tune) tc_set_tuning(sw == 1);
         // split precision hands over to FP64 sweeps (polish) near convergence or for the
         // last polish_sweeps of a fixed-length run
@@ -670,16 +805,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
             else
                 eval = tol > 0.0 || sw == max_sweeps;
         }
-        {
-            // the state before this sweep, for a rollback: one launch
-            static_assert(sizeof(DevScalars) % sizeof(double) == 0, "DevScalars in doubles");
-            const double* src[6] = {A[0], A[1], A[2], A[3], lam, (const double*)c.sc};
-            double* dst[6] = {c.Asnap[0], c.Asnap[1], c.Asnap[2], c.Asnap[3], c.lamsnap,
-                              (double*)c.sc_snap};
-            const long len[6] = {(long)s.n[0] * R, (long)s.n[1] * R, (long)s.n[2] * R,
-                                 (long)s.n[3] * R, (long)R, (long)(sizeof(DevScalars) / sizeof(double))};
-            CK(copy_many(c.st, 6, src, dst, len));
-        }
+        CKS(take_snapshot(c, A, lam));  // the state before this sweep, for a rollback
         int used = 0;
         if (tune && sw == 1) {
             CKS(sweep(c, A, lam, false, eval, tol, &used));  // tuned on live operands
@@ -691,11 +817,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
         if (h.fail_mask) {
             // a Cholesky pivot failed somewhere in this sweep: roll back and replay the
             // sweep with a host check after every factorisation
-            for (int k = 0; k < 4; ++k)
-                CK(cudaMemcpyAsync(A[k], c.Asnap[k], sizeof(double) * s.n[k] * R,
-                                   cudaMemcpyDeviceToDevice, c.st));
-            CK(cudaMemcpyAsync(lam, c.lamsnap, sizeof(double) * R, cudaMemcpyDeviceToDevice, c.st));
-            CK(cudaMemcpyAsync(c.sc, c.sc_snap, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
+            CKS(restore_snapshot(c, A, lam));
             refresh_state(c, A);
             CKS(ctx_safe_buffers(c));
             CKS(sweep(c, A, lam, true, eval, tol, &used));

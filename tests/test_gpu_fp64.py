@@ -148,6 +148,30 @@ def test_pinv_fallback_rollback(api, ldl, R):
     assert abs(out["loss"] - loss_ref) <= 1e-9 * nG2
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_pinv_fallback_in_a_fixed_length_run(api, prec):
+    # the same singular start point over several sweeps of a fixed-length run: every sweep
+    # fails its pivot test, while the next sweep is already queued; the queued sweep is
+    # undone, the failed one rolled back and replayed, and the run goes on
+    R, sweeps = 6, 5
+    p = make_problem(4, 9, 20, R, seed=6)
+    A = [a.copy() for a in p.A]
+    for a in A:
+        a[:, R - 1] = a[:, R - 2]
+    d = to_dev(p, torch)
+    d["A"] = [torch.from_numpy(a).cuda() for a in A]
+    lam = torch.ones(R, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, sweeps, 0.0, precision=prec,
+                          loss_every=1, history=True)
+    ref = O.als(p.Xo, p.Xv, p.Z, tuple(A), sweeps)
+    assert out["sweeps"] == sweeps
+    assert (out["flags"] & 1) and (out["flags"] & 2)
+    nG2 = ref["normG2"]
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    for got, want in zip(out["losses"], ref["losses"]):
+        assert abs(got - want) <= tol * nG2
+
+
 def test_bad_arguments_raise(api):
     from paper_2502_17683_gb300._lib import ThcCpdError
     p = make_problem(3, 4, 5, 6, seed=7)

@@ -127,6 +127,27 @@ def test_split_run_meeting_tol_ends_with_fp64_sweeps(api, prec):
     assert out["sweeps"] == 3
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_fixed_polish_sweeps_equal_split_then_fp64_calls(api, prec):
+    # a fixed-length run whose last k sweeps are FP64 (polish_sweeps; the run is pipelined,
+    # the hand-over sweep is known in advance) gives the same bits as N - k split sweeps
+    # followed by a separate k-sweep FP64 call on the result
+    N, k = 9, 3
+    p = make_problem(5, 15, 60, 80, seed=4)
+    d1, d2 = to_dev(p, torch), to_dev(p, torch)
+    lam1 = torch.ones(80, dtype=torch.float64, device="cuda")
+    lam2 = torch.ones(80, dtype=torch.float64, device="cuda")
+    out1 = api.thc_cpd_als(d1["Xo"], d1["Xv"], d1["Z"], d1["A"], lam1, N, 0.0, precision=prec,
+                           polish_sweeps=k)
+    api.thc_cpd_als(d2["Xo"], d2["Xv"], d2["Z"], d2["A"], lam2, N - k, 0.0, precision=prec)
+    out2 = api.thc_cpd_als(d2["Xo"], d2["Xv"], d2["Z"], d2["A"], lam2, k, 0.0, precision="fp64")
+    assert out1["flags"] & 4 and out1["sweeps"] == N
+    assert out1["fit"] == out2["fit"]
+    for a, b in zip(d1["A"], d2["A"]):
+        assert torch.equal(a, b)
+    assert torch.equal(lam1, lam2)
+
+
 def test_mixed_small_workload_trajectory(api):
     p = make_problem(5, 15, 60, 80, seed=0)
     d = to_dev(p, torch)

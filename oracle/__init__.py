@@ -8,5 +8,4 @@ thc_inputs/ serve both).
 Modules:
   thc_cpd  - explicit tensors, matrix-free MTTKRP, factor-form loss, CP-ALS.
   mlp      - FP64 forward/backward of the extrapolation MLP.
-  split    - bit-level reference of the BF16 / TF32 operand split.
 """

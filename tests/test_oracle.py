@@ -266,3 +266,76 @@ def test_planted_mistakes_are_caught():
     S = (Xo.T @ Xo) * (Xv.T @ Xv)
     bad_norm = float(np.sum(Z * (S @ Z.T @ S)))          # transposed core in ||G||^2
     assert abs(bad_norm - O.frobenius2(G)) > 1e-6 * O.frobenius2(G)
+
+
+# --- the extrapolated trial point of the learned step --------------------------------
+# Hand case (R = 2, dims 1, 2, 1, 2, alpha = 2): P = previous point, N = ALS point, lam on
+# the last mode. B_k = P_k + 2 (N_k - P_k) = 2 N_k - P_k, with mode 4 taken lam-absorbed:
+#   B1 = 2[3 2] - [1 2] = [5 2]                    norms (5, 2)
+#   B2 = 2[[1 1],[1 0]] - I = [[1 2],[2 -1]]       norms (sqrt5, sqrt5)
+#   B3 = 2[2 3] - [2 1] = [2 5]                    norms (2, 5)
+#   P4 lam_prev = [[2 0],[0 6]], N4 lam_new = [[0 2],[1 0]]
+#   B4 = [[-2 4],[2 -6]]                           norms (2 sqrt2, 2 sqrt13)
+# lam = product of the column norms = (5 sqrt5 2 2sqrt2, 2 sqrt5 5 2sqrt13) = (20 sqrt10, 20 sqrt65).
+_EXT_PREV = ([[1.0, 2.0]], [[1.0, 0.0], [0.0, 1.0]], [[2.0, 1.0]], [[1.0, 0.0], [0.0, 2.0]])
+_EXT_NEW = ([[3.0, 2.0]], [[1.0, 1.0], [1.0, 0.0]], [[2.0, 3.0]], [[0.0, 1.0], [1.0, 0.0]])
+_EXT_LAM_PREV = [2.0, 3.0]
+_EXT_LAM_NEW = [1.0, 2.0]
+_S5, _S2, _S13 = np.sqrt(5.0), np.sqrt(2.0), np.sqrt(13.0)
+_EXT_B = ([[1.0, 1.0]],
+          [[1 / _S5, 2 / _S5], [2 / _S5, -1 / _S5]],
+          [[1.0, 1.0]],
+          [[-1 / _S2, 2 / _S13], [1 / _S2, -3 / _S13]])
+_EXT_LAM = [20.0 * np.sqrt(10.0), 20.0 * np.sqrt(65.0)]
+
+
+def _ext_inputs():
+    a = lambda x: tuple(np.array(m, dtype=np.float64) for m in x)
+    return a(_EXT_PREV), np.array(_EXT_LAM_PREV), a(_EXT_NEW), np.array(_EXT_LAM_NEW)
+
+
+def _ext_matches(B, lam):
+    return (all(np.allclose(b, np.array(e), rtol=0, atol=1e-14) for b, e in zip(B, _EXT_B))
+            and np.allclose(lam, _EXT_LAM, rtol=1e-14, atol=0))
+
+
+def test_extrapolate_hand_case():
+    P, lp, N, ln = _ext_inputs()
+    B, lam = O.extrapolate(P, lp, N, ln, 2.0)
+    assert _ext_matches(B, lam)
+
+
+def test_extrapolate_end_points_reproduce_the_two_tensors():
+    # alpha = 0 gives back the previous point's tensor, alpha = 1 the ALS point's
+    # (the definition of the step; normalisation leaves the CPD tensor unchanged)
+    P, lp, N, ln = _ext_inputs()
+    for alpha, (A, lam) in ((0.0, (P, lp)), (1.0, (N, ln))):
+        B, lb = O.extrapolate(P, lp, N, ln, alpha)
+        np.testing.assert_allclose(O.cpd_tensor(B, lb), _brute_Gt(A, lam), rtol=1e-13, atol=1e-13)
+        for b in B:
+            np.testing.assert_allclose(np.linalg.norm(b, axis=0), 1.0, rtol=1e-14)
+
+
+def test_extrapolate_planted_mistakes_are_caught():
+    # plausible slips: lam absorbed into mode 1 instead of mode 4, lam dropped, the new
+    # point's lam used for both points; each misses the hand values
+    P, lp, N, ln = _ext_inputs()
+
+    def variant(mode_for_lam, lam_prev, lam_new):
+        Pp = [p.copy() for p in P]
+        Nn = [n.copy() for n in N]
+        if mode_for_lam is not None:
+            Pp[mode_for_lam] = Pp[mode_for_lam] * lam_prev[None, :]
+            Nn[mode_for_lam] = Nn[mode_for_lam] * lam_new[None, :]
+        B = [p + 2.0 * (n - p) for p, n in zip(Pp, Nn)]
+        out, lam = [], np.ones(2)
+        for b in B:
+            nrm = np.linalg.norm(b, axis=0)
+            out.append(b / nrm)
+            lam = lam * nrm
+        return out, lam
+
+    assert _ext_matches(*variant(3, lp, ln))           # the reading itself passes
+    assert not _ext_matches(*variant(0, lp, ln))       # lam on the first mode
+    assert not _ext_matches(*variant(None, lp, ln))    # lam dropped
+    assert not _ext_matches(*variant(3, ln, ln))       # stale lam on the previous point

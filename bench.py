@@ -1,13 +1,16 @@
 #!/usr/bin/env python
 """ALS sweeps/s of THC-driven matrix-free CP-ALS on one GB300.
 
-Workload (one step): thc_cpd_als on the o=20, v=100, R_thc=480, R_cp=720 THC block
-(synthetic THC factors, seed 0; 50 sweeps, no early stop), restarted from the same
-start factors every step. value = sweeps/s over all ranks (each rank solves its own
-independent problem: weak scaling, no collective on the data path).
+Workload (one step): thc_cpd_als on the o=50, v=250, R_thc=1200, R_cp=1800 THC block
+(synthetic THC factors with Z decay scale 240, seed 0; 100 sweeps, no early stop),
+restarted from the same start factors every step. value = sweeps/s over all ranks (each
+rank solves its own independent problem: weak scaling, no collective on the data path).
+Beside it: the plain FP64 GPU path on the same workload, and the wall-time each form
+(FP64, BF16x3, BF16x3 with the learned extrapolation) needs to reach one common fit.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16x3|tf32x3]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+  python bench.py --drift-report         # per-sweep fit differences from identical starts
 """
 from __future__ import annotations
 
@@ -22,8 +25,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-W = dict(o=20, v=100, Rt=480, R=720, sweeps=50, seed=0, decay=None)
-WORKLOAD = "THC-driven CP-ALS, o=20 v=100 R_thc=480 R_cp=720, 50 sweeps per step"
+W = dict(o=50, v=250, Rt=1200, R=1800, sweeps=100, seed=0, decay=240.0)
+WORKLOAD = "THC-driven CP-ALS, o=50 v=250 R_thc=1200 R_cp=1800 (Z decay 240), 100 sweeps per step"
 # other paper-shaped sizes, for profiling captures (the bench line uses the default)
 CONFIGS = {
     "c1": dict(o=5, v=15, Rt=60, R=80, sweeps=25),
@@ -45,9 +48,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps", type=int, default=None,
-                    help="sweeps per step (profiling captures only; the bench line uses 50)")
-    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS),
-                    help="workload size (profiling captures only; the bench line uses c2)")
+                    help="sweeps per step (profiling captures only; the bench line uses 100)")
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS),
+                    help="workload size (profiling captures only; the bench line uses c3)")
+    ap.add_argument("--no-equal-fit", action="store_true",
+                    help="skip the wall-time-to-a-common-fit comparison")
+    ap.add_argument("--drift-report", action="store_true",
+                    help="o=20 v=100 R_thc=480 R_cp=720, 50 sweeps: per-sweep |fit - fit_fp64| of "
+                         "the split precisions and of FP64 runs from perturbed starts")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the FP64 path beside the split precision")
     ap.add_argument("--learned-report", action="store_true",
@@ -71,38 +79,60 @@ def peaks():
 # nominal dense rates (TFLOP/s) used to carry the measured bf16 peak over to other dtypes
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 
-# The LDL^T and the FP64 GEMMs run on the FP64 FMA units, not on the tensor cores: their
-# roofline is 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz (the maximum SM clock)
-# = 1.259 TFLOP/s, the part's nominal 1.25 TFLOP/s.
-FP64_ALU_PEAK = 152 * 2 * 2 * 2070e6 / 1e12
+
+def fp64_peaks(dev, sm_max_mhz):
+    """FP64 roofline denominators: the FP64 FMA rate measured by the library's probe kernel,
+    cuBLAS DGEMM (torch float64 matmul, 8192^3, best of 5) and the rate derived from the unit
+    counts (SMs read from the device x 2 FP64 FMA per clock x 2 flop x the maximum SM clock)."""
+    import torch
+    from paper_2502_17683_gb300 import api
+    probe = api.thc_cpd_fp64_fma_rate()
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    best = 0.0
+    for i in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        if i:
+            best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    del a, b
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    return {"probe_tflops": probe, "dgemm_tflops": best, "nsm": nsm,
+            "derived_tflops": nsm * 2 * 2 * mhz * 1e6 / 1e12, "sm_max_mhz": mhz}
+
 
 # DRAM bytes per launch of the dataflow LDL^T kernel, from one ncu capture of one sweep of
-# the default workload (the four modes' launches averaged; ncu starts every launch from a
+# the named workload (the four modes' launches averaged; ncu starts every launch from a
 # flushed cache, so this is the cold-cache figure), and the SHA-256 of the kernel's sources
 # (concatenated in this order) it was taken on: reported only while they are unchanged.
-LDL_TRAFFIC = {"bytes_per_launch": 2764256,
-               "sha256": "dc1aa92630763b0f2fb84014295ea40e919c4ba7210fb7aebc71fc65320e95ce",
-               "sources": [os.path.join("paper_2502_17683_gb300", "csrc", f)
-                           for f in ("ldl_flow.cu", "ldl_common.cuh", "common.cuh")]}
+LDL_SOURCES = [os.path.join("paper_2502_17683_gb300", "csrc", f)
+               for f in ("ldl_flow.cu", "ldl_common.cuh", "common.cuh")]
+LDL_TRAFFIC = {}
 
 
 def ldl_sources_sha256():
     import hashlib
     h = hashlib.sha256()
-    for src in LDL_TRAFFIC["sources"]:
+    for src in LDL_SOURCES:
         with open(os.path.join(ROOT, src), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def ldl_traffic():
-    if not LDL_TRAFFIC["bytes_per_launch"]:
+def ldl_traffic(config):
+    rec = LDL_TRAFFIC.get(config)
+    if not rec:
         return None
     try:
         sha = ldl_sources_sha256()
     except OSError:
         return None
-    return LDL_TRAFFIC["bytes_per_launch"] if sha == LDL_TRAFFIC["sha256"] else None
+    return rec["bytes_per_launch"] if sha == rec["sha256"] else None
 
 
 class ClockSampler:
@@ -306,6 +336,44 @@ def batched_report(args):
     return 0
 
 
+def drift_report(args):
+    """Per-sweep |fit - fit_fp64| on o=20 v=100 R_thc=480 R_cp=720 over 50 sweeps from one
+    start: the split precisions, and FP64 runs whose start factors carry a relative
+    perturbation of 1e-9, 1e-7 and 1e-5 (how far ALS itself carries a perturbation of a given
+    size along this unconverged trajectory). All fits are exact FP64 losses."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import api
+    from thc_inputs import make_problem
+    o, v, Rt, R, sweeps = 20, 100, 480, 720, 50
+    p = make_problem(o, v, Rt, R, seed=0)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    Xo, Xv, Z = t(p.Xo), t(p.Xv), t(p.Z)
+
+    def run(prec, eps=0.0):
+        rng = np.random.default_rng(123)
+        A = [t(a * (1.0 + eps * rng.standard_normal(a.shape))) for a in p.A]
+        lam = torch.ones(R, dtype=torch.float64, device="cuda")
+        out = api.thc_cpd_als(Xo, Xv, Z, A, lam, sweeps, 0.0, precision=prec, loss_every=1,
+                              history=True)
+        return np.array(out["fits"])
+
+    ref = run("fp64")
+    rows = {}
+    for name, prec, eps in (("bf16x3", "bf16x3", 0.0), ("tf32x3", "tf32x3", 0.0),
+                            ("fp64_start_1e-9", "fp64", 1e-9), ("fp64_start_1e-7", "fp64", 1e-7),
+                            ("fp64_start_1e-5", "fp64", 1e-5)):
+        d = np.abs(run(prec, eps) - ref)
+        rows[name] = {"sweep": [1, 2, 5, 10, 20, 30, 40, 50],
+                      "abs_fit_diff": [float(d[s - 1]) for s in (1, 2, 5, 10, 20, 30, 40, 50)],
+                      "max": float(d.max())}
+    print(json.dumps({"report": "drift", "workload": "o=20 v=100 R_thc=480 R_cp=720, 50 sweeps, seed 0",
+                      "fp64_fit": [float(ref[s - 1]) for s in (1, 10, 50)], "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -314,6 +382,8 @@ def main():
         return learned_report(args)
     if args.batched:
         return batched_report(args)
+    if args.drift_report:
+        return drift_report(args)
 
     import numpy as np
     import torch
@@ -334,8 +404,9 @@ def main():
 
     precision = args.precision or "bf16x3"
     global WORKLOAD
-    if args.config != "c2":
+    if args.config != "c3":
         W.update(CONFIGS[args.config])
+        W["decay"] = CONFIGS[args.config].get("decay")
         WORKLOAD = (f"THC-driven CP-ALS, o={W['o']} v={W['v']} R_thc={W['Rt']} R_cp={W['R']}, "
                     f"{W['sweeps']} sweeps per step")
     if args.sweeps:
@@ -418,29 +489,61 @@ def main():
 
     # ---- the plain FP64 GPU path on the same workload, same protocol ----
     compare = None
+    o64 = None
+    nst = min(args.steps, 3)  # the FP64 path is timed on fewer steps (it is the slow arm)
     if precision != "fp64" and not args.no_compare:
         for _ in range(2):
             reset()
             api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64")
         torch.cuda.synchronize()
         ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for k in range(args.steps):
+               for _ in range(nst)]
+        for k in range(nst):
             flush.zero_()
             reset()
             ev3[k][0].record(stream)
             o64 = api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64")
             ev3[k][1].record(stream)
         torch.cuda.synchronize()
-        v64, ms3 = job_throughput(args.steps * W["sweeps"], sum(a.elapsed_time(b) for a, b in ev3), dev)
-        compare = {"fp64": {"value": v64, "fit": o64["fit"], "ms_per_step": ms3 / args.steps},
+        v64, ms3 = job_throughput(nst * W["sweeps"], sum(a.elapsed_time(b) for a, b in ev3), dev)
+        compare = {"fp64": {"value": v64, "fit": o64["fit"], "ms_per_step": ms3 / nst},
                    precision: {"value": value, "fit": fit, "ms_per_step": ms / args.steps},
                    "speedup_vs_fp64": value / v64,
                    "fit_diff_vs_fp64": fit - o64["fit"],
                    "note": "equal sweep count; both fits are exact FP64 losses of the returned factors"}
 
+    # ---- equal fit: wall-time of each form to the FP64 run's fit after the step's sweeps ----
+    equal_fit = None
+    if precision != "fp64" and o64 is not None and not args.no_equal_fit and world == 1:
+        from paper_2502_17683_gb300 import learned
+        target = o64["fit"]
+        rows = {"fp64": {"sweeps": W["sweeps"], "seconds": ms3 / nst / 1000.0, "fit": o64["fit"]}}
+        arms = [(precision, None, 5), (precision + "+learned", learned.load_params(), 0)]
+        for name, mlp, every in arms:
+            reset()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = api.thc_cpd_als(Xo, Xv, Z, A, lam, 4 * W["sweeps"], 0.0, precision=precision,
+                                mlp=mlp, loss_every=every, target_fit=target)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rows[name] = {"sweeps": r["sweeps"], "seconds": e0.elapsed_time(e1) / 1000.0,
+                          "fit": r["fit"], "reached": r["fit"] >= target}
+            if mlp is not None:
+                rows[name]["accepted_steps"] = r["accepted"]
+        equal_fit = {"target_fit": target,
+                     "target": f"the FP64 run's fit after {W['sweeps']} sweeps from the same start",
+                     "rows": rows,
+                     "speedup_vs_fp64": {k: rows["fp64"]["seconds"] / v["seconds"]
+                                         for k, v in rows.items() if k != "fp64"},
+                     "note": "split runs evaluate the exact FP64 loss every 5 sweeps (learned: every "
+                             "sweep, its accept rule needs it) and stop at the first evaluated sweep "
+                             "whose fit reaches the target; seconds by CUDA events around the call"}
+
     # ---- roofline: per-kernel-class CUDA events over one more profiled step ----
     pk, pk_kind = peaks()
+    f64pk = fp64_peaks(dev, clk.summary().get("sm_max_mhz"))
     # the factorisation a single problem gets (thc_cpd_opts.ldl = auto): dataflow up to R = 2048
     ldl_path = "dataflow" if W["R"] <= 2048 else "blocked"
     reset()
@@ -464,13 +567,19 @@ def main():
     elif dom == "elementwise":
         bound, peak, note = "hbm", None, pk_kind
     else:
-        bound, peak = "alu", FP64_ALU_PEAK
-        note = "FP64 FMA units: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (nominal 1.25 TF)"
-        if dom == "cholesky" and ldl_path == "dataflow" and args.config == "c2":
-            traffic = ldl_traffic()  # captured on this workload only
+        bound, peak = "alu", f64pk["probe_tflops"]
+        note = (f"measured FP64 FMA rate (library probe kernel); cuBLAS DGEMM measures "
+                f"{f64pk['dgemm_tflops']:.3f}, the unit counts give {f64pk['nsm']} SMs x 2 FMA/clk "
+                f"x 2 flop x {f64pk['sm_max_mhz']:.0f} MHz = {f64pk['derived_tflops']:.3f}")
+        if dom == "cholesky" and ldl_path == "dataflow":
+            traffic = ldl_traffic(args.config)  # the capture of this workload, if current
     roofline = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
                 "traffic": traffic, "peak_source": note,
+                "fp64_peaks": {k: (round(v, 4) if isinstance(v, float) else v)
+                               for k, v in f64pk.items()},
+                "frac_of_dgemm": (achieved / f64pk["dgemm_tflops"]) if bound == "alu" else None,
+                "frac_of_derived": (achieved / f64pk["derived_tflops"]) if bound == "alu" else None,
                 "classes_ms_per_step": {k: round(v["ms"], 3) for k, v in prof.items()}}
     tc = prof.get("tc_gemm", {"ms": 0.0})
     if tc["ms"] > 0:
@@ -502,6 +611,8 @@ def main():
     }
     if compare:
         line["compare"] = compare
+    if equal_fit:
+        line["equal_fit"] = equal_fit
     if rank == 0 and not args.no_cpu_baseline:
         v, n, dt = oracle_sweeps_per_s(args.cpu_seconds, W["seed"])
         line["cpu_baseline"] = {"value": v, "unit": "sweeps/s", "cores": os.cpu_count(),

@@ -81,6 +81,13 @@ typedef struct thc_cpd_opts {
                             (problems side by side fill the GPU better with short launches).
                             Both give the same factorisation up to rounding order; each is
                             bit-reproducible on its own. */
+    double wait_limit_s; /* limit of every device-side wait of the dataflow LDL^T and the
+                            backward solve, in seconds (0: 1 s). A wait that runs out makes
+                            the launch give up and the call return THC_CPD_ERR_TIMEOUT. */
+    double target_fit;   /* thc_cpd_als: > 0 stops after the first evaluated sweep whose
+                            FP64 fit is >= target_fit (split precision evaluates the loss
+                            every loss_every sweeps, or every sweep when loss_every is 0);
+                            0: off. Used to compare runs at equal fit. */
 } thc_cpd_opts;
 
 /* Values of thc_cpd_opts.ldl. */
@@ -189,6 +196,12 @@ thc_cpd_status thc_cpd_mlp_forward(const float* params, const float* X, int n, f
  * (host). Synchronises. */
 thc_cpd_status thc_cpd_mlp_grad(const float* params, const float* X, const float* y, int n,
                                 float* grad, float* loss_host, const thc_cpd_opts* opts);
+/* One Adam update (Kingma & Ba 2015, b1 = 0.9, b2 = 0.999, eps = 1e-8, bias-corrected with
+ * step count t >= 1) of params with gradient grad and the moments m, v (all device, FP32,
+ * THC_CPD_MLP_NPARAM each; params, m, v updated in place): the optimiser step that
+ * thc_cpd_mlp_train applies after every batch. Synchronises. */
+thc_cpd_status thc_cpd_mlp_adam(float* params, const float* grad, float* m, float* v, int t,
+                                float lr, const thc_cpd_opts* opts);
 /* Adam training (lr, batches of `batch`, reshuffled every epoch from `seed`) of the MSE on
  * (X, y); params updated in place; final loss over all rows in *final_loss_host. */
 thc_cpd_status thc_cpd_mlp_train(float* params, const float* X, const float* y, int n, int epochs,
@@ -229,6 +242,11 @@ void thc_cpd_profile(int enable);
  * filled or -1 on a CUDA error. */
 int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes);
 
+/* Measured FP64 FMA throughput of the device (TFLOP/s, 2 flop per FMA) from a probe kernel
+ * of independent FMA chains on every SM (64 warps per SM, best of three timed launches):
+ * the roofline denominator of the FP64 kernels (Gram, solve, loss). Synchronises. */
+thc_cpd_status thc_cpd_fp64_fma_rate(double* tflops_host, const thc_cpd_opts* opts);
+
 /* thc_cpd_mttkrp without any device allocation (the paper has no counterpart: this is
  * a service for callers that may not allocate device memory while they run, such as a
  * host whose own pool allocator owns all device memory, or code that must not call
@@ -238,8 +256,15 @@ int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes);
  * comes from one 32 MiB array in the library's device memory, which every GPU that loads
  * the library keeps until the process exits. Problems whose 4 * R_thc * R_cp doubles do
  * not fit in it are rejected with THC_CPD_ERR_SHAPE (message in thc_cpd_last_error()).
+ * Arguments are checked exactly as thc_cpd_mttkrp checks them (same statuses and messages).
  * The first call on a device, with that device current, looks up the array's device
- * address (cudaGetSymbolAddress); make it before any stream capture. Calls only enqueue
+ * address (cudaGetSymbolAddress); make it before any stream capture. Under CUDA's default
+ * lazy module loading that first call is also what creates the 32 MiB array on the device
+ * (with CUDA_MODULE_LOADING=EAGER, process start does): make it before another pool
+ * allocator claims the device's memory; if no memory is left then, it returns
+ * THC_CPD_ERR_CUDA with that explanation. The address is cached per device ordinal and
+ * belongs to the device's primary context: it stays valid for the process's lifetime, not
+ * across a cudaDeviceReset or in another context. Calls only enqueue
  * work on opts->stream (no synchronisation); M is ready when the stream reaches that
  * point. All calls on a device share the array, which keeps the last call's contents:
  * calls whose GPU work overlaps race on it and must be serialised by the caller. */
@@ -247,6 +272,23 @@ thc_cpd_status thc_cpd_mttkrp_noalloc(int o, int v, int Rt, int R,
                                       const double* Xo, const double* Xv, const double* Z,
                                       const double* const A[4], int mode, double* M,
                                       const thc_cpd_opts* opts);
+
+/* Normal-equation solve of one ALS mode update (Sec. 2.1, the textbook CP-ALS update the
+ * paper's ALS follows): A (n x R) with A H = M for the symmetric positive (semi)definite
+ * H (R x R, full matrix, lower triangle read) and M (n x R), by the dataflow LDL^T with the
+ * M rows carried along and the backward solve, exactly as inside thc_cpd_als. A pivot
+ * <= R * eps * max_i H_ii switches to the pseudo-inverse (symmetric eigendecomposition,
+ * eigenvalues <= R * eps * max |w| dropped); *used_pinv (host, may be NULL) says so.
+ * H, M and A are device arrays owned by the caller; H and M are not modified.
+ * tasks: NULL for the library's own schedule, or a caller-built off-path task list in the
+ * format of thc_cpd_ldl_schedule (host, 4 shorts per task, ntasks tasks). A caller list is
+ * checked for index ranges only (THC_CPD_ERR_ARG otherwise) and used as given: a list that
+ * lacks a task some other task or the pivot chain waits for makes those waits run out
+ * after opts->wait_limit_s and the call return THC_CPD_ERR_TIMEOUT; the device stays usable.
+ * Shapes: 1 <= R <= 2048, 1 <= n <= 4096. Synchronises the stream. */
+thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M, double* A,
+                                 const short* tasks, int ntasks, int* used_pinv,
+                                 const thc_cpd_opts* opts);
 
 /* Task list of the dataflow LDL^T of the normal-equation solve (host only, no device
  * work; Sec. 2.1's normal equations, solved by LDL^T with the M rows carried along).

@@ -22,7 +22,8 @@ EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_profile", "thc_cpd_profile_read", "thc_cpd_split_gemm",
            "thc_cpd_mttkrp_noalloc", "thc_cpd_als_batched", "thc_cpd_mlp_init",
            "thc_cpd_mlp_forward", "thc_cpd_mlp_grad", "thc_cpd_mlp_train", "thc_cpd_als_trajectory",
-           "thc_cpd_ldl_schedule")
+           "thc_cpd_ldl_schedule", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam",
+           "thc_cpd_fp64_fma_rate")
 MLP_NPARAM = 6849
 KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
 
@@ -48,7 +49,9 @@ class Opts(ctypes.Structure):
                 ("autotune", ctypes.c_int),
                 ("accepted_out", ctypes.c_int),
                 ("mlp", ctypes.c_void_p),
-                ("ldl", ctypes.c_int)]
+                ("ldl", ctypes.c_int),
+                ("wait_limit_s", ctypes.c_double),
+                ("target_fit", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -79,11 +82,14 @@ _SIGS = {
     "thc_cpd_mlp_init": [P, ctypes.c_ulonglong, OPTS],
     "thc_cpd_mlp_forward": [P, P, I, P, OPTS],
     "thc_cpd_mlp_grad": [P, P, P, I, P, ctypes.POINTER(ctypes.c_float), OPTS],
+    "thc_cpd_fp64_fma_rate": [DP, OPTS],
+    "thc_cpd_mlp_adam": [P, P, P, P, I, ctypes.c_float, OPTS],
     "thc_cpd_mlp_train": [P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong,
                           ctypes.POINTER(ctypes.c_float), OPTS],
     "thc_cpd_als_trajectory": [I, I, I, I, P, P, P, PTR4, P, I, DP, I,
                                ctypes.POINTER(ctypes.c_float), DP, OPTS],
     "thc_cpd_ldl_schedule": [I, I, ctypes.POINTER(ctypes.c_short), I],
+    "thc_cpd_ldl_solve": [I, I, P, P, P, ctypes.POINTER(ctypes.c_short), I, IP, OPTS],
 }
 
 _lib = None

@@ -17,7 +17,8 @@ __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_als", "thc_cpd_version", "thc_cpd_launch_count", "thc_cpd_profile",
            "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc",
            "thc_cpd_als_batched", "thc_cpd_mlp_init", "thc_cpd_mlp_forward", "thc_cpd_mlp_grad",
-           "thc_cpd_mlp_train", "thc_cpd_als_trajectory", "Opts"]
+           "thc_cpd_mlp_train", "thc_cpd_als_trajectory", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam", "thc_cpd_fp64_fma_rate",
+           "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -41,8 +42,9 @@ def _fdev(t: torch.Tensor, name: str, shape=None) -> int:
 
 
 def _opts(precision="fp64", stream=None, loss_every=0, history=None, polish_sweeps=0,
-          autotune=False, ldl="auto") -> Opts:
+          autotune=False, ldl="auto", wait_limit_s=0.0) -> Opts:
     o = Opts()
+    o.wait_limit_s = float(wait_limit_s)
     if ldl not in LDL_VARIANTS:
         raise ThcCpdError(ERR_ARG, f"unknown ldl variant {ldl!r}")
     o.ldl = LDL_VARIANTS[ldl]
@@ -71,6 +73,36 @@ def _ptr4(A, dims, R):
     if len(A) != 4:
         raise ThcCpdError(ERR_ARG, "A must hold four factor matrices")
     return PTR4(*[_dev(a, f"A[{k}]", (dims[k], R)) for k, a in enumerate(A)])
+
+
+def thc_cpd_ldl_solve(H, M, A=None, tasks=None, wait_limit_s=0.0, stream=None):
+    """A with A H = M (H: R x R SPD, M: n x R) by the library's dataflow LDL^T and backward
+    solve, pseudo-inverse on a failed pivot. tasks: None (the library's schedule) or an
+    int16 array of shape (ntasks, 4) in the format of thc_cpd_ldl_schedule. Returns
+    (A, used_pinv)."""
+    R = H.shape[0]
+    n = M.shape[0]
+    if A is None:
+        A = torch.empty(n, R, dtype=torch.float64, device=H.device)
+    opts = _opts("fp64", stream, wait_limit_s=wait_limit_s)
+    used = ctypes.c_int(0)
+    tp, nt = None, 0
+    if tasks is not None:
+        import numpy as np
+        tasks = np.ascontiguousarray(tasks, dtype=np.int16).reshape(-1, 4)
+        tp, nt = tasks.ctypes.data_as(ctypes.POINTER(ctypes.c_short)), int(tasks.shape[0])
+    check(load().thc_cpd_ldl_solve(R, n, _dev(H, "H", (R, R)), _dev(M, "M", (n, R)),
+                                   _dev(A, "A", (n, R)), tp, nt, ctypes.byref(used),
+                                   ctypes.byref(opts)))
+    return A, bool(used.value)
+
+
+def thc_cpd_fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s (probe kernel)."""
+    out = ctypes.c_double()
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_fp64_fma_rate(ctypes.byref(out), ctypes.byref(opts)))
+    return out.value
 
 
 def thc_cpd_version() -> str:
@@ -140,7 +172,7 @@ def thc_cpd_als_sweep(Xo, Xv, Z, A, lam, normG2: float = 0.0, precision="fp64", 
 
 def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision="fp64",
                 stream=None, loss_every: int = 0, history: bool = False, polish_sweeps: int = 0,
-                autotune: bool = False, mlp=None, ldl="auto"):
+                autotune: bool = False, mlp=None, ldl="auto", target_fit: float = 0.0):
     o, v, Rt = _dims(Xo, Xv, Z)
     R = A[0].shape[1]
     loss, fit, done = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
@@ -148,6 +180,7 @@ def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision=
     opts = _opts(precision, stream, loss_every,
                  ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
                  polish_sweeps, autotune, ldl)
+    opts.target_fit = float(target_fit)
     if mlp is not None:
         opts.mlp = _fdev(mlp, "mlp", (MLP_NPARAM,))
     check(load().thc_cpd_als(o, v, Rt, R, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
@@ -260,6 +293,16 @@ def thc_cpd_mlp_grad(params, X, y, stream=None):
                                   _fdev(y, "y", (n,)), n, _fdev(grad, "grad"), ctypes.byref(loss),
                                   ctypes.byref(opts)))
     return grad, loss.value
+
+
+def thc_cpd_mlp_adam(params, grad, m, v, t: int, lr: float = 1e-3, stream=None):
+    """One Adam update of params (and the moments m, v) in place, as thc_cpd_mlp_train
+    applies it after each batch."""
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_mlp_adam(_fdev(params, "params", (MLP_NPARAM,)),
+                                  _fdev(grad, "grad", (MLP_NPARAM,)), _fdev(m, "m", (MLP_NPARAM,)),
+                                  _fdev(v, "v", (MLP_NPARAM,)), int(t), float(lr),
+                                  ctypes.byref(opts)))
 
 
 def thc_cpd_mlp_train(params, X, y, epochs: int, batch: int = 64, lr: float = 1e-3, seed: int = 0,

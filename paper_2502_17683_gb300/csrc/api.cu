@@ -94,6 +94,12 @@ thc_cpd_status check_prec(const thc_cpd_opts* opts) {
     return THC_CPD_OK;
 }
 
+// the limit of the dataflow solve's device-side waits for launches from this thread
+void set_wait_limit(const thc_cpd_opts* o) {
+    const double sec = o ? o->wait_limit_s : 0.0;
+    flow_set_wait_ns(sec > 0.0 ? (unsigned long long)std::min(sec * 1e9, 6e10) : 0ull);
+}
+
 cudaStream_t stream_of(const thc_cpd_opts* o) {
     return o ? (cudaStream_t)o->stream : (cudaStream_t)0;
 }
@@ -207,6 +213,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     c.Z = Z;
     c.st = stream_of(opts);
     c.prec = opts ? opts->precision : THC_CPD_FP64;
+    set_wait_limit(opts);
     const int Rt = s.Rt, R = s.R, nmax = s.nmax;
     size_t pc = 0;
     for (int k = 0; k < 2; ++k) {
@@ -693,6 +700,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
         loss_hist.push_back(l0);
     }
     const int loss_every = (opts && opts->loss_every > 0) ? opts->loss_every : 0;
+    const double target = (opts && opts->target_fit > 0.0) ? opts->target_fit : 0.0;
     const int polish = (opts && opts->polish_sweeps > 0 && tol <= 0.0) ? opts->polish_sweeps : 0;
     const bool split_run = c.prec != THC_CPD_FP64;
     int flags = 0;
@@ -724,7 +732,8 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
                 flags |= 4;
             }
             bool eval = true;
-            if (c.prec != THC_CPD_FP64) eval = (loss_every > 0 && sw % loss_every == 0) || sw == max_sweeps;
+            if (c.prec != THC_CPD_FP64 && !(target > 0.0 && loss_every == 0))
+                eval = (loss_every > 0 && sw % loss_every == 0) || sw == max_sweeps;
             const int b = sw & 1;
             use_snapshot_slot(c, b);
             CKS(take_snapshot(c, A, lam));
@@ -781,6 +790,14 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
                 if (sweeps_done) *sweeps_done = done_sweeps;
                 return set_err(THC_CPD_ERR_NONFINITE, "loss became non-finite at sweep %d", sw);
             }
+            if (target > 0.0 && eval && h.fit >= target) {
+                if (spec) {  // undo the queued sweep sw + 1: the run ends at sweep sw
+                    CK(cudaStreamSynchronize(c.st));
+                    use_snapshot_slot(c, (sw + 1) & 1);
+                    CKS(restore_snapshot(c, A, lam));
+                }
+                break;
+            }
             if (next == sw + 1 && sw + 1 <= max_sweeps) {
                 CKS(launch(sw + 1));
                 next = sw + 2;
@@ -803,7 +820,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
             if (loss_every > 0)
                 eval = (sw % loss_every == 0) || sw == max_sweeps;
             else
-                eval = tol > 0.0 || sw == max_sweeps;
+                eval = tol > 0.0 || target > 0.0 || sw == max_sweeps;
         }
         CKS(take_snapshot(c, A, lam));  // the state before this sweep, for a rollback
         int used = 0;
@@ -906,6 +923,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
             if (sweeps_done) *sweeps_done = done_sweeps;
             return set_err(THC_CPD_ERR_NONFINITE, "loss became non-finite at sweep %d", sw);
         }
+        if (target > 0.0 && eval && h.fit >= target) break;
         // a split-precision run that meets tol (|dfit| fell below 10 tol and tol in one
         // sweep) still ends with FP64 sweeps: the hand-over above fires next sweep
         if (h.done && !(split_run && c.prec != THC_CPD_FP64)) break;
@@ -1107,6 +1125,17 @@ int set_error(int s, const char* msg) {
     g_err = msg;
     return s;
 }
+
+int check_mttkrp_args(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                      const double* Z, const double* const* A, int mode, const double* M) {
+    Shape s;
+    CKS(check_shape(o, v, Rt, R, &s));
+    if (!A) return set_err(THC_CPD_ERR_ARG, "A must be non-null");
+    CKS(check_ptrs(Xo, Xv, Z, A));
+    if (mode < 0 || mode > 3) return set_err(THC_CPD_ERR_ARG, "mode must be 0..3, got %d", mode);
+    if (!M) return set_err(THC_CPD_ERR_ARG, "M must be non-null");
+    return THC_CPD_OK;
+}
 }  // namespace thc
 
 extern "C" {
@@ -1132,11 +1161,9 @@ thc_cpd_status thc_cpd_mttkrp(int o, int v, int Rt, int R, const double* Xo, con
                               const double* Z, const double* const A[4], int mode, double* M,
                               const thc_cpd_opts* opts) {
     Shape s;
+    CKS((thc_cpd_status)check_mttkrp_args(o, v, Rt, R, Xo, Xv, Z, A, mode, M));
     CKS(check_shape(o, v, Rt, R, &s));
-    CKS(check_ptrs(Xo, Xv, Z, A));
     CKS(check_prec(opts));
-    if (mode < 0 || mode > 3) return set_err(THC_CPD_ERR_ARG, "mode must be 0..3, got %d", mode);
-    if (!M) return set_err(THC_CPD_ERR_ARG, "M must be non-null");
     Ctx c;
     CKS(ctx_init(c, s, Xo, Xv, Z, opts, 0));
     if (c.prec == THC_CPD_FP64) {
@@ -1267,7 +1294,82 @@ thc_cpd_status thc_cpd_als_trajectory(int o, int v, int Rt, int R, const double*
 
 }  // extern "C"
 
-extern "C" thc_cpd_status thc_cpd_als_batched(int nprob, thc_cpd_problem* probs, int max_sweeps,
+extern "C" thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M, double* A,
+                                 const short* tasks, int ntasks, int* used_pinv,
+                                 const thc_cpd_opts* opts) {
+    if (R < 1 || R > 2048 || n < 1 || n > 4096)
+        return set_err(THC_CPD_ERR_SHAPE, "need 1 <= R <= 2048 and 1 <= n <= 4096 (R=%d n=%d)", R, n);
+    if (!H || !M || !A) return set_err(THC_CPD_ERR_ARG, "H, M and A must be non-null");
+    if (tasks && ntasks < 0) return set_err(THC_CPD_ERR_ARG, "ntasks must be >= 0");
+    if (tasks) {
+        const int bad = flow_task_check(R, n, tasks, ntasks);
+        if (bad >= 0) return set_err(THC_CPD_ERR_ARG, "task %d has an out-of-range type or tile index", bad);
+    }
+    if (used_pinv) *used_pinv = 0;
+    if (!flow_prepare(R, n)) return set_err(THC_CPD_ERR_UNSUPPORTED, "no dataflow schedule for R=%d n=%d", R, n);
+    set_wait_limit(opts);
+    cudaStream_t st = stream_of(opts);
+    const size_t RR = (size_t)R * R, nR = (size_t)n * R;
+    size_t bytes = Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
+                   Arena::need<double>(std::max(RR, nR)) + Arena::need<double>(R) +
+                   Arena::need<int>(flow_sync_ints(R, n)) + Arena::need<int>(bsolve_sync_ints(n)) +
+                   Arena::need<DevScalars>(1) + Arena::need<short>(4 * (size_t)std::max(ntasks, 1));
+    struct Ws {
+        void* p = nullptr;
+        cudaStream_t st;
+        ~Ws() {
+            if (p) cudaFreeAsync(p, st);
+        }
+    } ws;
+    ws.st = st;
+    CK(cudaMallocAsync(&ws.p, bytes, st));
+    Arena ar;
+    ar.base = (char*)ws.p;
+    ar.cap = bytes;
+    double* Haug = ar.take<double>(RR + nR);
+    double* P = ar.take<double>(RR);
+    double* Hsave = ar.take<double>(RR);
+    double* V = ar.take<double>(RR);
+    double* dinv = ar.take<double>(R);
+    double* T = ar.take<double>(std::max(RR, nR));
+    double* w = ar.take<double>(R);
+    int* fsync = ar.take<int>(flow_sync_ints(R, n));
+    int* bsync = ar.take<int>(bsolve_sync_ints(n));
+    DevScalars* sc = ar.take<DevScalars>(1);
+    void* dtasks = ar.take<short>(4 * (size_t)std::max(ntasks, 1));
+    CK(cudaMemsetAsync(fsync, 0, sizeof(int) * flow_sync_ints(R, n), st));
+    CK(cudaMemsetAsync(bsync, 0, sizeof(int) * bsolve_sync_ints(n), st));
+    scalars_init(st, sc, 0.0);
+    copy_with_maxdiag(st, R, H, Haug, sc);
+    CK(cudaMemcpyAsync(Hsave, H, sizeof(double) * RR, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(Haug + RR, M, sizeof(double) * nR, cudaMemcpyDeviceToDevice, st));
+    {
+        ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
+        if (tasks)
+            CK(ldl_flow_tasks(st, R, n, Haug, P, dinv, sc, 0, fsync, tasks, ntasks, dtasks));
+        else
+            CK(ldl_flow(st, R, n, Haug, P, dinv, sc, 0, fsync));
+    }
+    {
+        ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
+        CK(bsolve_slices(st, R, n, Haug + RR, A, Haug, bsync));
+    }
+    DevScalars* h = host_scalars();
+    if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
+    CK(cudaMemcpyAsync(h, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (int e = flow_take_error())
+        return set_err(THC_CPD_ERR_TIMEOUT, "LDL^T dataflow wait gave up (code %d)", e);
+    if (h->fail_mask) {
+        int sweeps = 0;
+        CK(pinv_solve(st, R, n, Hsave, M, A, V, w, T, &sweeps));
+        CK(cudaStreamSynchronize(st));
+        if (used_pinv) *used_pinv = 1;
+    }
+    return THC_CPD_OK;
+}
+
+thc_cpd_status thc_cpd_als_batched(int nprob, thc_cpd_problem* probs, int max_sweeps,
                                               double tol, thc_cpd_opts* opts) {
     return run_batched(nprob, probs, max_sweeps, tol, opts);
 }

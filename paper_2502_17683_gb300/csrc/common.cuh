@@ -49,4 +49,10 @@ inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 // Record the message returned by thc_cpd_last_error() for this host thread; returns s.
 int set_error(int s, const char* msg);
 
+// The argument checks of thc_cpd_mttkrp (shapes, null pointers, mode), shared by every
+// MTTKRP entry point so that they accept and reject the same arguments with the same
+// messages. Returns a thc_cpd_status; the message is set on failure.
+int check_mttkrp_args(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                      const double* Z, const double* const* A, int mode, const double* M);
+
 }  // namespace thc

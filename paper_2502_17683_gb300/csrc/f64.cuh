@@ -45,6 +45,20 @@ bool flow_prepare(int R, int n);
 cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
                      DevScalars* sc, int mode, int* sync, int max_ctas = 0);
 int flow_take_error();
+// The same launch with a caller-provided task list (host, 4 shorts per task as
+// thc_cpd_ldl_schedule writes them; dev_tasks: 8 * ntasks bytes of device memory). The list
+// is used as given: an incomplete or misordered one ends in bounded waits that give up.
+cudaError_t ldl_flow_tasks(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
+                           DevScalars* sc, int mode, int* sync, const short* host_tasks,
+                           int ntasks, void* dev_tasks);
+// Index of the first task whose type or tile indices are out of range, or -1.
+int flow_task_check(int R, int n, const short* tasks, int ntasks);
+// Limit of every wait of the dataflow LDL^T and the backward solve launched afterwards from
+// this host thread (0: the default, 1 s).
+void flow_set_wait_ns(unsigned long long ns);
+
+// H_out = H (R x R) and sc->maxdiag = max_i H_ii.
+void copy_with_maxdiag(cudaStream_t st, int R, const double* H, double* H_out, DevScalars* sc);
 
 // Backward solve A L = Y (unit lower L in the strictly-lower part of H, R x R; Y and A n x R)
 // by column slices claimed from a ticket (ldl_flow.cu); sync: bsolve_sync_ints(n) ints.

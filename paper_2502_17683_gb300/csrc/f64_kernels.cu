@@ -347,6 +347,28 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
     k_hadamard3<<<blocks, 256, 0, st>>>(R, Ga, Gb, Gc, H, sc);
 }
 
+__global__ void k_copy_maxdiag(int R, const double* __restrict__ H, double* __restrict__ out,
+                               DevScalars* sc) {
+    const long n = (long)R * R;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x)
+        out[i] = H[i];
+    if (blockIdx.x == 0) {
+        __shared__ double sh[32];
+        double mx = 0.0;
+        for (int i = threadIdx.x; i < R; i += blockDim.x) mx = fmax(mx, H[(size_t)i * R + i]);
+        mx = block_reduce_max(mx, sh);
+        if (threadIdx.x == 0) sc->maxdiag = mx;
+    }
+}
+
+void copy_with_maxdiag(cudaStream_t st, int R, const double* H, double* H_out, DevScalars* sc) {
+    const long n = (long)R * R;
+    int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    count_launch();
+    k_copy_maxdiag<<<blocks, 256, 0, st>>>(R, H, H_out, sc);
+}
+
 // ------------------------------------------------------------------------------------
 // Solve of the ALS normal equations A H = M: blocked right-looking LDL^T factorisation
 // of H (the square-root-free form of the Cholesky factorisation, same pivots) with the

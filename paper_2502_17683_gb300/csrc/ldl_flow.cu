@@ -58,7 +58,7 @@ constexpr int FB = 16;
 constexpr int kGroups = 4;                 // worker groups (128 threads) per CTA
 constexpr int kFlowThreads = 128 * kGroups;
 constexpr int kFlowSmem = 120 * 1024;      // more than half an SM: one CTA per SM
-constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // default limit of every wait (1 s)
 constexpr int kSyncHead = 6;  // ticket, arrivals, fdone, abort, critical ticket, CTAs done
 constexpr int kMaxTiles = 256;             // largest schedule the host builds
 // Up to 128 tiles (R <= 2048) the dataflow kernel is at least as fast as the blocked
@@ -131,7 +131,8 @@ __device__ __forceinline__ void group_sync(int id) {
 // *p[i] >= v[i] for every i (true), or the launch is aborting / this wait gave up (false).
 // The counters are read together: one round trip per poll.
 template <int N>
-__device__ bool flow_wait(const int* const (&p)[N], const int (&v)[N], int* abort_flag) {
+__device__ bool flow_wait(const int* const (&p)[N], const int (&v)[N], int* abort_flag,
+                          unsigned long long limit_ns) {
     auto ready = [&]() {
         int x[N];
 #pragma unroll
@@ -148,7 +149,7 @@ __device__ bool flow_wait(const int* const (&p)[N], const int (&v)[N], int* abor
         if (ready()) return true;
         if ((it & 31) == 31) {
             if (ld_acquire(abort_flag)) return false;
-            if (global_ns() - t0 > kWaitNs) {
+            if (global_ns() - t0 > limit_ns) {
                 atomicExch(abort_flag, 1);
                 atomicExch(&g_flow_error, 1);
                 return false;
@@ -171,12 +172,12 @@ __device__ __forceinline__ void chain_arrive_factor() { asm volatile("bar.arrive
 
 // Bounded wait for a shared-memory step counter written by the other half of the chain
 // CTA: *p >= v (true), or the launch aborts / the wait gives up (false).
-__device__ bool smem_wait(const volatile int* p, int v, int* abort_flag) {
+__device__ bool smem_wait(const volatile int* p, int v, int* abort_flag, unsigned long long limit_ns) {
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; *p < v; ++it) {
         if ((it & 63) == 63) {
             if (ld_acquire(abort_flag)) return false;
-            if (global_ns() - t0 > kWaitNs) {
+            if (global_ns() - t0 > limit_ns) {
                 atomicExch(abort_flag, 1);
                 atomicExch(&g_flow_error, 1);
                 return false;
@@ -278,10 +279,12 @@ __device__ void factor_tile(ChainSmem& S, int jb, double tau) {
 }
 
 struct FlowArgs {
-    double* H;
-    double* P;
-    double* dinv;
-    int R, nrows, nT, nM;
+    double* H;              // element (0, 0) of the factorised block; rows ld doubles apart
+    double* P;              // X = L D of the block's H rows, same indexing as H
+    double* dinv;           // D^-1 of the block's R columns
+    int R, nrows, nT, nM;   // columns (and H rows) of the block, all its rows, tile counts
+    int ld;                 // row pitch of H and P (R for a whole solve)
+    int R_tau;              // order of the whole normal matrix (the pivot threshold's R)
     const FlowTask* tasks;  // [0, nmain): served by the worker CTAs; [nmain, ntasks): the
     int ntasks, nmain;      // critical tasks, served by the critical CTAs
     int ncrit;              // critical CTAs (one group each), roles 1..ncrit
@@ -289,6 +292,7 @@ struct FlowArgs {
     int nsync;
     DevScalars* sc;
     int mode;
+    unsigned long long wait_ns;  // limit of every wait
 };
 
 __device__ __forceinline__ int* sdone_of(const FlowArgs& a) { return a.sync + kSyncHead; }
@@ -302,16 +306,17 @@ __device__ __forceinline__ int* cnt_of(const FlowArgs& a) {
 // has taken its previous content out.
 __device__ void flow_producer(const FlowArgs& a, ChainSmem& S) {
     const int t2 = threadIdx.x - 256, R = a.R, nT = a.nT;  // 0 .. kProducerThreads - 1
+    const size_t ld = a.ld;
     int* abort_flag = a.sync + 3;
     int* cnt = cnt_of(a);
     for (int sn = 1; sn < nT; ++sn) {
         const int b = sn & 1;
         if (t2 == 0) {
-            bool ok = sn < 3 || smem_wait(&S.empty[b], sn - 2, abort_flag);
+            bool ok = sn < 3 || smem_wait(&S.empty[b], sn - 2, abort_flag, a.wait_ns);
             if (ok) {
                 const int* const pc[2] = {&cnt[sn * nT + sn - 1], &cnt[sn * nT + sn]};
                 const int vc[2] = {sn - 1, sn - 1};
-                ok = flow_wait(pc, vc, abort_flag);
+                ok = flow_wait(pc, vc, abort_flag, a.wait_ns);
             }
             S.pstat = ok;
         }
@@ -321,9 +326,9 @@ __device__ void flow_producer(const FlowArgs& a, ChainSmem& S) {
             const int n0 = sn * FB, nb = min(FB, R - n0);
             for (int e = t2; e < FB * FB; e += kProducerThreads) {
                 const int rr = e >> 4, cc = e & 15;
-                S.Bn[b][rr][cc] = rr < nb ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 - FB + cc) : 0.0;
+                S.Bn[b][rr][cc] = rr < nb ? __ldcg(a.H + (size_t)(n0 + rr) * ld + n0 - FB + cc) : 0.0;
                 S.Dn[b][rr][cc] =
-                    (rr < nb && cc <= rr) ? __ldcg(a.H + (size_t)(n0 + rr) * R + n0 + cc) : 0.0;
+                    (rr < nb && cc <= rr) ? __ldcg(a.H + (size_t)(n0 + rr) * ld + n0 + cc) : 0.0;
             }
         }
         producer_sync();
@@ -339,8 +344,9 @@ __device__ void flow_producer(const FlowArgs& a, ChainSmem& S) {
 // The critical path (threads 0..255): for s = 0..T-1, S(s, s-1), U(s, s, s-1), F(s).
 __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
     const int tid = threadIdx.x, R = a.R, nT = a.nT;
+    const size_t ld = a.ld;
     int* abort_flag = a.sync + 3;
-    const double tau = (double)R * DBL_EPSILON * a.sc->maxdiag;
+    const double tau = (double)a.R_tau * DBL_EPSILON * a.sc->maxdiag;
     const int r = tid >> 4, c = tid & 15;  // element of a tile
     int bad = 0;
     int s_end = nT;  // the step the loop stopped at (nT: all done)
@@ -348,9 +354,9 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
         const int s0 = s * FB, sb = min(FB, R - s0), b = s & 1;
         double dss = 0.0, x = 0.0;
         if (s == 0) {
-            if (r < sb && c <= r) dss = __ldcg(a.H + (size_t)r * R + c);
+            if (r < sb && c <= r) dss = __ldcg(a.H + (size_t)r * ld + c);
         } else {
-            if (tid == 0) S.ok = smem_wait(&S.full[b], s, abort_flag) && S.valid[b];
+            if (tid == 0) S.ok = smem_wait(&S.full[b], s, abort_flag, a.wait_ns) && S.valid[b];
             chain_sync();
             if (!S.ok) {
                 s_end = s;
@@ -366,8 +372,8 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
             }
             const double l = x * S.dp[c];
             if (r < sb) {
-                a.H[(size_t)(s0 + r) * R + s0 - FB + c] = l;
-                a.P[(size_t)(s0 + r) * R + s0 - FB + c] = x;
+                a.H[(size_t)(s0 + r) * ld + s0 - FB + c] = l;
+                a.P[(size_t)(s0 + r) * ld + s0 - FB + c] = x;
             }
             S.Xs[r][c] = x;
             S.Ls[r][c] = l;
@@ -388,7 +394,7 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
         chain_sync();
         factor_tile(S, sb, tau);
         if (r < sb && c <= r)
-            a.H[(size_t)(s0 + r) * R + s0 + c] = (c < r) ? S.L[r][c] : S.D[r][r];
+            a.H[(size_t)(s0 + r) * ld + s0 + c] = (c < r) ? S.L[r][c] : S.D[r][r];
         if (tid < sb) a.dinv[s0 + tid] = S.dinv[tid];
         S.Lp[r][c] = (c < r && r < sb) ? S.L[r][c] : 0.0;
         if (tid < FB) S.dp[tid] = tid < sb ? S.dinv[tid] : 0.0;
@@ -442,11 +448,12 @@ __device__ __forceinline__ void tile_rows(const FlowArgs& a, int t, int& r0, int
 // S(t, k) by one worker group: thread gt owns column c of rows rr and rr + 8.
 __device__ void task_S(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t, int k) {
     const int R = a.R;
+    const size_t ld = a.ld;
     int* sdone = sdone_of(a);
     if (gt == 0) {
         const int* const pc[2] = {a.sync + 2, &cnt_of(a)[t * a.nT + k]};
         const int vc[2] = {k + 1, k};
-        W.ok = flow_wait(pc, vc, a.sync + 3);
+        W.ok = flow_wait(pc, vc, a.sync + 3, a.wait_ns);
     }
     group_sync(bar);
     if (!W.ok) return;
@@ -456,12 +463,12 @@ __device__ void task_S(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
     const int c = gt & 15, rr = gt >> 4;
     const int row0 = r0 + rr, row1 = r0 + rr + 8;
     const bool cv = c < kb;
-    double b0 = (cv && row0 < rlim) ? __ldcg(a.H + (size_t)row0 * R + k0 + c) : 0.0;
-    double b1 = (cv && row1 < rlim) ? __ldcg(a.H + (size_t)row1 * R + k0 + c) : 0.0;
+    double b0 = (cv && row0 < rlim) ? __ldcg(a.H + (size_t)row0 * ld + k0 + c) : 0.0;
+    double b1 = (cv && row1 < rlim) ? __ldcg(a.H + (size_t)row1 * ld + k0 + c) : 0.0;
     double lr[FB];
 #pragma unroll
     for (int q = 0; q < FB; ++q)
-        lr[q] = (q < c && cv) ? __ldcg(a.H + (size_t)(k0 + c) * R + k0 + q) : 0.0;
+        lr[q] = (q < c && cv) ? __ldcg(a.H + (size_t)(k0 + c) * ld + k0 + q) : 0.0;
     const double di = cv ? __ldcg(a.dinv + k0 + c) : 0.0;
     const int src = gt & 16;
 #pragma unroll
@@ -475,12 +482,12 @@ __device__ void task_S(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
     }
     const bool hrow = t < a.nT;
     if (cv && row0 < rlim) {
-        a.H[(size_t)row0 * R + k0 + c] = b0 * di;
-        if (hrow) a.P[(size_t)row0 * R + k0 + c] = b0;
+        a.H[(size_t)row0 * ld + k0 + c] = b0 * di;
+        if (hrow) a.P[(size_t)row0 * ld + k0 + c] = b0;
     }
     if (cv && row1 < rlim) {
-        a.H[(size_t)row1 * R + k0 + c] = b1 * di;
-        if (hrow) a.P[(size_t)row1 * R + k0 + c] = b1;
+        a.H[(size_t)row1 * ld + k0 + c] = b1 * di;
+        if (hrow) a.P[(size_t)row1 * ld + k0 + c] = b1;
     }
     group_sync(bar);
     if (gt == 0) {
@@ -492,12 +499,13 @@ __device__ void task_S(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
 // U(t, j, k) by one worker group: tile (t, j) -= L(t, k) X(j, k)^T.
 __device__ void task_U(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t, int j, int k) {
     const int R = a.R;
+    const size_t ld = a.ld;
     int* sdone = sdone_of(a);
     int* cnt = cnt_of(a);
     if (gt == 0) {
         const int* const pc[3] = {&sdone[t], &sdone[j], &cnt[t * a.nT + j]};
         const int vc[3] = {k + 1, k + 1, k};
-        W.ok = flow_wait(pc, vc, a.sync + 3);
+        W.ok = flow_wait(pc, vc, a.sync + 3, a.wait_ns);
     }
     group_sync(bar);
     if (!W.ok) return;
@@ -507,15 +515,15 @@ __device__ void task_U(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
     const int c = gt & 15, rr = gt >> 4;
     const int row0 = r0 + rr, row1 = r0 + rr + 8, col = c0 + c;
     const bool cv = c < kb;
-    W.A[rr][c] = (cv && row0 < rlim) ? __ldcg(a.H + (size_t)row0 * R + k0 + c) : 0.0;
-    W.A[rr + 8][c] = (cv && row1 < rlim) ? __ldcg(a.H + (size_t)row1 * R + k0 + c) : 0.0;
-    W.B[rr][c] = (cv && c0 + rr < R) ? __ldcg(a.P + (size_t)(c0 + rr) * R + k0 + c) : 0.0;
-    W.B[rr + 8][c] = (cv && c0 + rr + 8 < R) ? __ldcg(a.P + (size_t)(c0 + rr + 8) * R + k0 + c) : 0.0;
+    W.A[rr][c] = (cv && row0 < rlim) ? __ldcg(a.H + (size_t)row0 * ld + k0 + c) : 0.0;
+    W.A[rr + 8][c] = (cv && row1 < rlim) ? __ldcg(a.H + (size_t)row1 * ld + k0 + c) : 0.0;
+    W.B[rr][c] = (cv && c0 + rr < R) ? __ldcg(a.P + (size_t)(c0 + rr) * ld + k0 + c) : 0.0;
+    W.B[rr + 8][c] = (cv && c0 + rr + 8 < R) ? __ldcg(a.P + (size_t)(c0 + rr + 8) * ld + k0 + c) : 0.0;
     const bool diag = t == j;
     const bool v0 = row0 < rlim && col < R && !(diag && c > rr);
     const bool v1 = row1 < rlim && col < R && !(diag && c > rr + 8);
-    const double h0 = v0 ? __ldcg(a.H + (size_t)row0 * R + col) : 0.0;
-    const double h1 = v1 ? __ldcg(a.H + (size_t)row1 * R + col) : 0.0;
+    const double h0 = v0 ? __ldcg(a.H + (size_t)row0 * ld + col) : 0.0;
+    const double h1 = v1 ? __ldcg(a.H + (size_t)row1 * ld + col) : 0.0;
     group_sync(bar);
     double s0 = 0.0, s1 = 0.0, u0 = 0.0, u1 = 0.0;
 #pragma unroll
@@ -526,8 +534,8 @@ __device__ void task_U(const FlowArgs& a, WorkerSmem& W, int gt, int bar, int t,
         u0 = fma(W.A[rr + 8][q], b0, u0);
         u1 = fma(W.A[rr + 8][q + 1], b1, u1);
     }
-    if (v0) a.H[(size_t)row0 * R + col] = h0 - (s0 + s1);
-    if (v1) a.H[(size_t)row1 * R + col] = h1 - (u0 + u1);
+    if (v0) a.H[(size_t)row0 * ld + col] = h0 - (s0 + s1);
+    if (v1) a.H[(size_t)row1 * ld + col] = h1 - (u0 + u1);
     group_sync(bar);
     if (gt == 0) {
         __threadfence();
@@ -630,6 +638,7 @@ struct BsArgs {
     const double* H;
     int R, n, nJ, C;
     int* sync;  // [0] ticket, [1] abort, [2] CTAs done, [3 + r] prog of row r; zero at entry
+    unsigned long long wait_ns;
 };
 
 // 32-term dot product in four independent FMA chains (fixed order)
@@ -682,7 +691,7 @@ __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
                 if (tid == 0) {
                     const int* const pc[1] = {&prog[r]};
                     const int vc[1] = {a.nJ - K};
-                    ok = flow_wait(pc, vc, abort_flag);
+                    ok = flow_wait(pc, vc, abort_flag, a.wait_ns);
                     kmin = a.nJ - ld_acquire(&prog[r]);
                 }
                 __syncthreads();
@@ -842,6 +851,8 @@ struct Plan {
     bool ok = false;
 };
 
+thread_local unsigned long long t_wait_ns = kWaitNs;
+
 std::mutex g_plan_mu;
 std::map<std::tuple<int, int, int>, Plan> g_plans;  // (device, R, n) -> plan (kept)
 
@@ -905,13 +916,56 @@ cudaError_t ldl_flow(cudaStream_t st, int R, int n, double* Haug, double* P, dou
     // for the critical tasks
     const int ncrit = max_ctas > 0 ? std::min(p->ncrit, 1) : p->ncrit;
     const int grid = max_ctas > 0 ? std::max(2 + ncrit, std::min(p->grid, max_ctas)) : p->grid;
-    FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, p->tasks, p->ntasks, p->nmain, ncrit,
-               sync, nsync, sc, mode};
+    FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, R, R, p->tasks, p->ntasks, p->nmain, ncrit,
+               sync, nsync, sc, mode, t_wait_ns};
     const int smem = max_ctas > 0 ? (int)kFlowSmemUsed : kFlowSmem;
     k_ldl_flow<<<grid, kFlowThreads, smem, st>>>(a);
     count_launch();
     return cudaGetLastError();
 }
+
+cudaError_t ldl_flow_tasks(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
+                           DevScalars* sc, int mode, int* sync, const short* host_tasks,
+                           int ntasks, void* dev_tasks) {
+    const Plan* p = get_plan(R, n);  // grid, shared-memory attribute and tile counts
+    if (!p || ntasks < 0) return cudaErrorInvalidValue;
+    std::vector<FlowTask> h((size_t)ntasks);
+    for (int i = 0; i < ntasks; ++i)
+        h[i] = FlowTask{host_tasks[4 * i], host_tasks[4 * i + 1], host_tasks[4 * i + 2],
+                        host_tasks[4 * i + 3]};
+    std::stable_partition(h.begin(), h.end(),
+                          [&](const FlowTask& x) { return !critical_task(x, p->nT); });
+    int nmain = 0;
+    while (nmain < ntasks && !critical_task(h[nmain], p->nT)) ++nmain;
+    if (ntasks > 0) {
+        const cudaError_t e = cudaMemcpyAsync(dev_tasks, h.data(), sizeof(FlowTask) * h.size(),
+                                              cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        // the host vector goes out of scope: the copy must have left it
+        const cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e2 != cudaSuccess) return e2;
+    }
+    const int nsync = kSyncHead + (p->nT + p->nM) * (1 + p->nT);
+    const int ncrit = ntasks > nmain ? p->ncrit : 0;
+    FlowArgs a{Haug, P, dinv, R, R + n, p->nT, p->nM, R, R, (const FlowTask*)dev_tasks, ntasks,
+               nmain, ncrit, sync, nsync, sc, mode, t_wait_ns};
+    k_ldl_flow<<<p->grid, kFlowThreads, kFlowSmem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int flow_task_check(int R, int n, const short* tasks, int ntasks) {
+    const int nT = cdiv(R, FB), nRT = nT + cdiv(n, FB);
+    for (int i = 0; i < ntasks; ++i) {
+        const short* x = tasks + 4 * i;
+        if (x[0] != 0 && x[0] != 1) return i;
+        if (x[1] < 0 || x[1] >= nRT || x[3] < 0 || x[3] >= nT) return i;
+        if (x[0] == 1 && (x[2] < 0 || x[2] >= nT)) return i;
+    }
+    return -1;
+}
+
+void flow_set_wait_ns(unsigned long long ns) { t_wait_ns = ns ? ns : kWaitNs; }
 
 size_t bsolve_sync_ints(int nmax) { return 3 + (size_t)nmax; }
 
@@ -919,7 +973,7 @@ cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, doubl
                           const double* H, int* sync) {
     if (n <= 0) return cudaSuccess;
     const int nJ = cdiv(R, BB), C = cdiv(R, kSlice);
-    BsArgs a{Yf, A, H, R, n, nJ, C, sync};
+    BsArgs a{Yf, A, H, R, n, nJ, C, sync, t_wait_ns};
     const int grid = std::min(n * C, kNumSM * 4);
     k_bsolve_slices<<<grid, kBsThreads, 0, st>>>(a);
     count_launch();

@@ -264,6 +264,17 @@ extern "C" thc_cpd_status thc_cpd_mlp_grad(const float* params, const float* X, 
     return THC_CPD_OK;
 }
 
+extern "C" thc_cpd_status thc_cpd_mlp_adam(float* params, const float* grad, float* m, float* v,
+                                           int t, float lr, const thc_cpd_opts* opts) {
+    if (!params || !grad || !m || !v) return mlp_err(THC_CPD_ERR_ARG, "null pointer");
+    if (t < 1) return mlp_err(THC_CPD_ERR_ARG, "the step count t must be >= 1");
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : (cudaStream_t)0;
+    k_adam<<<cdiv(NPARAM, 128), 128, 0, st>>>(params, grad, m, v, t, lr);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return mlp_err(THC_CPD_ERR_CUDA, "launch failed");
+    return cudaStreamSynchronize(st) == cudaSuccess ? THC_CPD_OK : mlp_err(THC_CPD_ERR_CUDA, "sync failed");
+}
+
 extern "C" thc_cpd_status thc_cpd_mlp_train(float* params, const float* X, const float* y, int n,
                                             int epochs, int batch, float lr,
                                             unsigned long long seed, float* final_loss_host,

@@ -8,9 +8,20 @@
 // synchronise the device) is not allowed, and real-time loops that must not touch the
 // allocator at all. They pass inputs and outputs as usual; the scratch comes from here.
 //
+// Where the 32 MiB come from: the array lives in this file's own device module. Under
+// CUDA's default lazy module loading that module, and so the array, is created on a device
+// by the first call there (its address lookup loads the module); with
+// CUDA_MODULE_LOADING=EAGER it is created when the process first initialises the device.
+// Either way the reservation happens once, before any work of that call is enqueued: a
+// caller whose own pool will claim the device should make one call first. If the device
+// has no room left at that moment the call fails with THC_CPD_ERR_CUDA and says so.
+//
 // Set-up: the first call on a device (with that device current) looks up the device
-// address of the array with cudaGetSymbolAddress and caches it per device; make that
-// first call before any stream capture begins. Every later call reuses the address.
+// address of the array with cudaGetSymbolAddress and caches it per device ordinal; make
+// that first call before any stream capture begins. The cached address belongs to the
+// device's primary context and stays valid for the life of the process; a caller that
+// resets the device (cudaDeviceReset) or drives the library from another context must not
+// use this entry point afterwards.
 //
 // Sharing: all calls on a device use the same array and it keeps the contents of the
 // last call. Calls whose GPU work overlaps (different streams, or different host threads
@@ -46,19 +57,14 @@ extern "C" thc_cpd_status thc_cpd_mttkrp_noalloc(int o, int v, int Rt, int R, co
                                                  const thc_cpd_opts* opts) {
     using namespace thc;
     char msg[256];
-    if (o < 1 || v < 1 || Rt < 1 || R < 1) {
-        snprintf(msg, sizeof msg, "dimensions must be >= 1 (o=%d v=%d Rt=%d R=%d)", o, v, Rt, R);
-        return (thc_cpd_status)set_error(THC_CPD_ERR_SHAPE, msg);
-    }
-    if (!Xo || !Xv || !Z || !A || !M) return (thc_cpd_status)set_error(THC_CPD_ERR_ARG, "null pointer argument");
-    for (int k = 0; k < 4; ++k)
-        if (!A[k]) return (thc_cpd_status)set_error(THC_CPD_ERR_ARG, "null factor pointer");
-    if (mode < 0 || mode > 3) return (thc_cpd_status)set_error(THC_CPD_ERR_ARG, "mode must be 0..3");
+    // the same checks, in the same order and with the same messages, as thc_cpd_mttkrp
+    const int chk = check_mttkrp_args(o, v, Rt, R, Xo, Xv, Z, A, mode, M);
+    if (chk != THC_CPD_OK) return (thc_cpd_status)chk;
     if (opts && opts->precision != THC_CPD_FP64)
         return (thc_cpd_status)set_error(THC_CPD_ERR_UNSUPPORTED, "the allocation-free MTTKRP is FP64 only");
     const size_t RtR = round256((size_t)Rt * R);
     const size_t need = 4 * RtR;  // three projections W_k and the Z product Y
-    if ((long)Rt * R >= 0x7fffffffL || need > kScratchDoubles) {
+    if (need > kScratchDoubles) {
         snprintf(msg, sizeof msg,
                  "R_thc * R_cp = %d * %d needs %zu bytes of scratch; the allocation-free "
                  "MTTKRP has %zu (use thc_cpd_mttkrp)",
@@ -75,7 +81,17 @@ extern "C" thc_cpd_status thc_cpd_mttkrp_noalloc(int o, int v, int Rt, int R, co
         if (!g_scratch_ptr[dev]) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e == cudaErrorMemoryAllocation) {
+                cudaGetLastError();
+                snprintf(msg, sizeof msg,
+                         "the 32 MiB scratch array could not be created on device %d (its module "
+                         "is loaded by the first call there): no device memory left; make the "
+                         "first call before another allocator claims the device",
+                         dev);
+                return (thc_cpd_status)set_error(THC_CPD_ERR_CUDA, msg);
+            }
             if (e != cudaSuccess || !p) {
+                cudaGetLastError();
                 snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the scratch array failed: %s",
                          cudaGetErrorString(e));
                 return (thc_cpd_status)set_error(THC_CPD_ERR_CUDA, msg);

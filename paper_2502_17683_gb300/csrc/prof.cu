@@ -1,7 +1,9 @@
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
 
+#include "common.cuh"
 #include "prof.cuh"
 #include "thc_cpd.h"
 
@@ -85,3 +87,59 @@ int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes) {
 }
 
 }  // extern "C"
+
+// ---- FP64 FMA throughput probe (the roofline denominator of the FP64 kernels) ----------
+namespace {
+constexpr int kProbeChains = 8;   // independent FMA chains per thread (covers the latency)
+constexpr int kProbeIters = 4096;
+
+__global__ void __launch_bounds__(256) k_fp64_fma_probe(double* out, double a, double b) {
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = (double)(threadIdx.x + c) * 1e-3;
+    for (int i = 0; i < kProbeIters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) s += x[c];
+    if (s == 12345.678) out[0] = s;  // keeps the chains live; never true for these inputs
+}
+}  // namespace
+
+extern "C" thc_cpd_status thc_cpd_fp64_fma_rate(double* tflops_host, const thc_cpd_opts* opts) {
+    using namespace thc;
+    if (!tflops_host) return (thc_cpd_status)set_error(THC_CPD_ERR_ARG, "tflops_host must be non-null");
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : (cudaStream_t)0;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+        return (thc_cpd_status)set_error(THC_CPD_ERR_CUDA, "no CUDA device");
+    const int grid = 8 * nsm, threads = 256;  // 64 warps per SM
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double best = 0.0;
+    double* sink = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMallocAsync((void**)&sink, sizeof(double), st) != cudaSuccess)
+        return (thc_cpd_status)set_error(THC_CPD_ERR_CUDA, "probe set-up failed");
+    for (int rep = 0; rep < 4; ++rep) {  // the first run warms up; best of the rest
+        cudaEventRecord(e0, st);
+        k_fp64_fma_probe<<<grid, threads, 0, st>>>(sink, 0.999999, 1e-9);
+        cudaEventRecord(e1, st);
+        count_launch();
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 2.0 * grid * threads * (double)kProbeChains * kProbeIters;
+        if (rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    cudaFreeAsync(sink, st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || best <= 0.0)
+        return (thc_cpd_status)set_error(THC_CPD_ERR_CUDA, "probe failed");
+    *tflops_host = best;
+    return THC_CPD_OK;
+}

@@ -71,6 +71,23 @@ def test_argument_validation_happens_before_device_work(lib):
     assert lib.thc_cpd_thc_norm2(3, 4, 5, 1, 1, 1, None, None) == _lib.ERR_ARG
 
 
+def test_ldl_solve_checks_its_arguments_before_device_work(lib):
+    import numpy as np
+    from paper_2502_17683_gb300 import _lib
+    sp = ctypes.POINTER(ctypes.c_short)
+    f = lib.thc_cpd_ldl_solve
+    assert f(0, 5, 1, 1, 1, None, 0, None, None) == _lib.ERR_SHAPE
+    assert f(4096, 5, 1, 1, 1, None, 0, None, None) == _lib.ERR_SHAPE
+    assert f(64, 0, 1, 1, 1, None, 0, None, None) == _lib.ERR_SHAPE
+    assert f(64, 5, None, 1, 1, None, 0, None, None) == _lib.ERR_ARG
+    # a task list with an out-of-range tile index (R = 64: 4 column tiles, n = 5: 1 row tile)
+    bad = np.array([[1, 2, 1, 0], [1, 3, 2, 7]], dtype=np.int16)
+    assert f(64, 5, 1, 1, 1, bad.ctypes.data_as(sp), 2, None, None) == _lib.ERR_ARG
+    assert b"task 1" in lib.thc_cpd_last_error()
+    bad = np.array([[2, 2, 1, 0]], dtype=np.int16)  # unknown task type
+    assert f(64, 5, 1, 1, 1, bad.ctypes.data_as(sp), 1, None, None) == _lib.ERR_ARG
+
+
 def test_no_cpu_fallback_when_library_missing(tmp_path):
     from paper_2502_17683_gb300 import _lib
     with pytest.raises(_lib.ThcCpdError):

@@ -58,6 +58,33 @@ def test_forward_and_gradient_match_oracle(api):
     assert np.max(np.abs(g - g_64)) <= 2e-2 * np.max(np.abs(g_64))
 
 
+def test_adam_step_matches_oracle(api):
+    # the optimiser kernel that training applies after every batch, from nonzero moments at
+    # step t = 7 (bias corrections and both decay rates matter), element by element
+    rng = np.random.default_rng(5)
+    theta = rng.standard_normal(N.NPARAM).astype(np.float32)
+    grad = (rng.standard_normal(N.NPARAM) * 10.0 ** rng.uniform(-4, 0, N.NPARAM)).astype(np.float32)
+    m = (0.1 * rng.standard_normal(N.NPARAM)).astype(np.float32)
+    v = (0.01 * rng.uniform(0, 1, N.NPARAM)).astype(np.float32)
+    t, lr = 7, 3e-3
+    # the kernel holds lr, b1, b2 and eps as FP32 constants (1 - b2 is then 1 - fl32(0.999),
+    # 1.3e-5 away from 0.001): the oracle step is taken with those values
+    f = lambda x: float(np.float32(x))
+    th_ref, m_ref, v_ref = N.adam_step(theta.astype(np.float64), grad.astype(np.float64),
+                                       m.astype(np.float64), v.astype(np.float64), t, f(lr),
+                                       b1=f(0.9), b2=f(0.999), eps=f(1e-8))
+    d = lambda x: torch.from_numpy(x.copy()).cuda()
+    P, G, Md, Vd = d(theta), d(grad), d(m), d(v)
+    api.thc_cpd_mlp_adam(P, G, Md, Vd, t, lr)
+    P, Md, Vd = (x.cpu().numpy().astype(np.float64) for x in (P, Md, Vd))
+    # FP32 arithmetic: a few ulps of each quantity
+    assert np.max(np.abs(Md - m_ref)) <= 1e-6 * np.max(np.abs(m_ref))
+    assert np.max(np.abs(Vd - v_ref) / np.maximum(v_ref, 1e-30)) <= 1e-6
+    assert np.max(np.abs(P - th_ref)) <= 1e-6 * np.max(np.abs(th_ref))
+    # and the step is not the identity (lr * mh / (sqrt(vh) + eps) is well above rounding)
+    assert np.max(np.abs(P - theta)) > 1e-3 * lr
+
+
 def test_training_fits_a_teacher(api):
     rng = np.random.default_rng(1)
     teacher = N.init(7) * 2.0
@@ -146,3 +173,32 @@ def test_trained_network_gains_over_plain_als(api):
                      res["learned"]["fit"]))
     print("sweeps to |dfit| < 1e-6 (plain, learned, fit plain, fit learned):", rows)
     assert sum(r[1] for r in rows) < sum(r[0] for r in rows)
+
+
+def test_trained_network_reaches_a_common_fit_in_less_wall_time(api):
+    # o=30 v=150 R_thc=720 R_cp=1080 (the learned-extrapolation workload), split precision:
+    # plain ALS runs 250 sweeps; its fit is the target the learned run must reach sooner
+    import time
+    from paper_2502_17683_gb300 import learned
+    P = learned.load_params()
+    p = make_problem(30, 150, 720, 1080, seed=904)
+    R = 1080
+
+    def run(mlp, sweeps, target=0.0):
+        d = to_dev(p, torch)
+        lam = torch.ones(R, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, sweeps, 0.0,
+                              precision="bf16x3", mlp=mlp, target_fit=target)
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    run(None, 3)  # warm-up (graphs, plans)
+    plain, t_plain = run(None, 250)
+    learned_out, t_learned = run(P, 250, target=plain["fit"])
+    print(f"plain {plain['sweeps']} sweeps {t_plain:.2f} s fit {plain['fit']:.9f}; learned "
+          f"{learned_out['sweeps']} sweeps {t_learned:.2f} s fit {learned_out['fit']:.9f}")
+    assert learned_out["fit"] >= plain["fit"]
+    assert learned_out["sweeps"] < plain["sweeps"]
+    assert t_learned < t_plain

@@ -109,6 +109,33 @@ def make_planted(o: int, v: int, rank: int, R: int, seed: int = 0,
     return THCProblem(o, v, Rt, R, Xo, Xv, Z, A), planted
 
 
+def make_planted_noisy(o: int, v: int, rank: int, noise_rank: int = 24, noise_scale: float = 10.0,
+                       seed: int = 0, start_perturb: float = 0.3) -> tuple[THCProblem, tuple]:
+    """A planted rank-`rank` CPD plus a THC-shaped perturbation, so that the best rank-`rank`
+    CPD is a fixed point of ALS that is not exact (fit below 1):
+
+      Xo = [A1*|A3*|Eo], Xv = [A2*|A4*|Ev], Z = blockdiag([[0, I], [0, 0]], s L L^T / m)
+
+    with Eo, Ev, L ~ N(0,1)/sqrt(m) (m = noise_rank, L m x m) and s = noise_scale. The start
+    factors are the planted ones with each entry scaled by (1 + start_perturb N(0,1)), so
+    that ALS converges to the fixed point near the planted CPD. R_cp = rank.
+    Returns the problem and the planted factors."""
+    base, planted = make_planted(o, v, rank, rank, seed=seed, independent=True)
+    rng = np.random.default_rng([seed, 0x5E])
+    m = noise_rank
+    Eo = rng.standard_normal((o, m)) / math.sqrt(m)
+    Ev = rng.standard_normal((v, m)) / math.sqrt(m)
+    L = rng.standard_normal((m, m))
+    Xo = np.concatenate([base.Xo, Eo], axis=1)
+    Xv = np.concatenate([base.Xv, Ev], axis=1)
+    Rt = Xo.shape[1]
+    Z = np.zeros((Rt, Rt))
+    Z[:base.Rt, :base.Rt] = base.Z
+    Z[base.Rt:, base.Rt:] = noise_scale * (L @ L.T) / m
+    A = tuple(a * (1.0 + start_perturb * rng.standard_normal(a.shape)) for a in planted)
+    return THCProblem(o, v, Rt, rank, Xo, Xv, Z, A), planted
+
+
 def round_up(x: int, m: int) -> int:
     return ((x + m - 1) // m) * m
 

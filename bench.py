@@ -51,6 +51,8 @@ def parse():
                     help="sweeps per step (profiling captures only; the bench line uses 100)")
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS),
                     help="workload size (profiling captures only; the bench line uses c3)")
+    ap.add_argument("--ldl", default="auto", choices=["auto", "dataflow", "blocked", "emulated"],
+                    help="factorisation of the normal equations (thc_cpd_opts.ldl)")
     ap.add_argument("--no-equal-fit", action="store_true",
                     help="skip the wall-time-to-a-common-fit comparison")
     ap.add_argument("--drift-report", action="store_true",
@@ -421,7 +423,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        return api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision=precision)
+        return api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision=precision, ldl=args.ldl)
 
     def reset():
         for a, a0 in zip(A, A0):
@@ -470,7 +472,7 @@ def main():
         dZ.copy_(hZ, non_blocking=True)
         for a, h in zip(A, hA):
             a.copy_(h, non_blocking=True)
-        api.thc_cpd_als(dXo, dXv, dZ, A, lam, W["sweeps"], 0.0, precision=precision)
+        api.thc_cpd_als(dXo, dXv, dZ, A, lam, W["sweeps"], 0.0, precision=precision, ldl=args.ldl)
         for o_, a in zip(oA, A):
             o_.copy_(a, non_blocking=True)
         olam.copy_(lam, non_blocking=True)
@@ -494,7 +496,7 @@ def main():
     if precision != "fp64" and not args.no_compare:
         for _ in range(2):
             reset()
-            api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64")
+            api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64", ldl=args.ldl)
         torch.cuda.synchronize()
         ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(nst)]
@@ -502,7 +504,7 @@ def main():
             flush.zero_()
             reset()
             ev3[k][0].record(stream)
-            o64 = api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64")
+            o64 = api.thc_cpd_als(Xo, Xv, Z, A, lam, W["sweeps"], 0.0, precision="fp64", ldl=args.ldl)
             ev3[k][1].record(stream)
         torch.cuda.synchronize()
         v64, ms3 = job_throughput(nst * W["sweeps"], sum(a.elapsed_time(b) for a, b in ev3), dev)
@@ -525,7 +527,7 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             r = api.thc_cpd_als(Xo, Xv, Z, A, lam, 4 * W["sweeps"], 0.0, precision=precision,
-                                mlp=mlp, loss_every=every, target_fit=target)
+                                mlp=mlp, loss_every=every, target_fit=target, ldl=args.ldl)
             e1.record(stream)
             torch.cuda.synchronize()
             rows[name] = {"sweeps": r["sweeps"], "seconds": e0.elapsed_time(e1) / 1000.0,

@@ -94,7 +94,12 @@ typedef struct thc_cpd_opts {
 typedef enum {
     THC_CPD_LDL_AUTO = 0,
     THC_CPD_LDL_BLOCKED = 1,   /* one launch per 32-column block step */
-    THC_CPD_LDL_DATAFLOW = 2   /* one persistent launch (R <= 2048; blocked beyond) */
+    THC_CPD_LDL_DATAFLOW = 2,  /* one persistent launch (R <= 2048; blocked beyond) */
+    THC_CPD_LDL_EMULATED = 3   /* two-level: 128-column panels by the dataflow kernel, each
+                                  trailing update as an FP64-accurate product on the BF16
+                                  tensor cores (exact integer slices, see
+                                  thc_cpd_emulated_gemm); the factorisation stays FP64 in
+                                  every value it stores (R <= 4096; dataflow otherwise) */
 } thc_cpd_ldl;
 
 /* One independent problem of a batched run (thc_cpd_als_batched). Inputs as for
@@ -224,8 +229,10 @@ long thc_cpd_launch_count(void);
 
 /* Per kernel class: summed CUDA-event time of the launch groups, their algorithmic
  * FLOPs and bytes, and the number of groups. Classes: 0 FP64 GEMM, 1 Cholesky
- * (factorisation with the fused forward solve), 2 backward solve, 3 element-wise and
- * reduction kernels, 4 tensor-core GEMM. */
+ * (factorisation with the fused forward solve; on the emulated path its FP64 panels),
+ * 2 backward solve, 3 element-wise and reduction kernels, 4 split tensor-core GEMM,
+ * 5 FP64-accurate emulated products on the tensor cores (digit split and product; FLOPs
+ * counted as the FP64 work they replace). */
 typedef struct thc_cpd_kstat {
     double ms;
     double flops;
@@ -238,9 +245,21 @@ typedef struct thc_cpd_kstat {
  * timed runs whose throughput is reported. */
 void thc_cpd_profile(int enable);
 
-/* Fills out[0..min(max_classes,5)) (waits for the recorded events); returns the count
+/* Fills out[0..min(max_classes,6)) (waits for the recorded events); returns the count
  * filled or -1 on a CUDA error. */
 int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes);
+
+/* C (M x N) = A (M x K) B (N x K)^T to FP64 accuracy on the BF16 tensor cores (the
+ * contraction behind THC_CPD_LDL_EMULATED, exposed for testing and reuse; the paper's
+ * solves are FP64, Sec. 2.1 and 3). Every row of A and of B is scaled by a power of two and
+ * cut into 7 signed 8-bit integer digits (an error-free splitting after Ozaki, Ogita, Oishi
+ * and Rump, Numer. Algorithms 59, 2012); the digit products are exact on the tensor cores
+ * (FP32 accumulation of integers below 2^24, K in chunks of 128) and are recombined exactly
+ * in 64-bit integers, then rounded once to FP64. Error: about 2^-53 |C| + 2^-55 K
+ * max_k |A_ik| max_k |B_jk|. Row-major FP64 device arrays (lda, ldb, ldc in elements).
+ * Shapes: 1 <= M, N <= 4096, K >= 1. Synchronises. */
+thc_cpd_status thc_cpd_emulated_gemm(int M, int N, int K, const double* A, int lda, const double* B,
+                                     int ldb, double* C, int ldc, const thc_cpd_opts* opts);
 
 /* Measured FP64 FMA throughput of the device (TFLOP/s, 2 flop per FMA) from a probe kernel
  * of independent FMA chains on every SM (64 warps per SM, best of three timed launches):

@@ -14,7 +14,7 @@ OK, ERR_ARG, ERR_SHAPE, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_ALLOC, ERR_UNS
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
                 5: "ERR_TIMEOUT", 6: "ERR_ALLOC", 7: "ERR_UNSUPPORTED"}
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
-LDL_VARIANTS = {"auto": 0, "blocked": 1, "dataflow": 2}
+LDL_VARIANTS = {"auto": 0, "blocked": 1, "dataflow": 2, "emulated": 3}
 
 # every symbol include/thc_cpd.h declares
 EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_sweep",
@@ -23,9 +23,9 @@ EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_mttkrp_noalloc", "thc_cpd_als_batched", "thc_cpd_mlp_init",
            "thc_cpd_mlp_forward", "thc_cpd_mlp_grad", "thc_cpd_mlp_train", "thc_cpd_als_trajectory",
            "thc_cpd_ldl_schedule", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam",
-           "thc_cpd_fp64_fma_rate")
+           "thc_cpd_fp64_fma_rate", "thc_cpd_emulated_gemm")
 MLP_NPARAM = 6849
-KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm")
+KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm", "tc_emulated")
 
 
 class ThcCpdError(RuntimeError):
@@ -83,6 +83,7 @@ _SIGS = {
     "thc_cpd_mlp_forward": [P, P, I, P, OPTS],
     "thc_cpd_mlp_grad": [P, P, P, I, P, ctypes.POINTER(ctypes.c_float), OPTS],
     "thc_cpd_fp64_fma_rate": [DP, OPTS],
+    "thc_cpd_emulated_gemm": [I, I, I, P, I, P, I, P, I, OPTS],
     "thc_cpd_mlp_adam": [P, P, P, P, I, ctypes.c_float, OPTS],
     "thc_cpd_mlp_train": [P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong,
                           ctypes.POINTER(ctypes.c_float), OPTS],

@@ -18,7 +18,7 @@ __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc",
            "thc_cpd_als_batched", "thc_cpd_mlp_init", "thc_cpd_mlp_forward", "thc_cpd_mlp_grad",
            "thc_cpd_mlp_train", "thc_cpd_als_trajectory", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam", "thc_cpd_fp64_fma_rate",
-           "Opts"]
+           "thc_cpd_emulated_gemm", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -75,7 +75,19 @@ def _ptr4(A, dims, R):
     return PTR4(*[_dev(a, f"A[{k}]", (dims[k], R)) for k, a in enumerate(A)])
 
 
-def thc_cpd_ldl_solve(H, M, A=None, tasks=None, wait_limit_s=0.0, stream=None):
+def thc_cpd_emulated_gemm(A, B, C=None, stream=None):
+    """C = A @ B.T to FP64 accuracy on the BF16 tensor cores (exact integer slices)."""
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.empty(M, N, dtype=torch.float64, device=A.device)
+    opts = _opts("fp64", stream)
+    check(load().thc_cpd_emulated_gemm(M, N, K, _dev(A, "A"), K, _dev(B, "B", (N, K)), K,
+                                       _dev(C, "C", (M, N)), N, ctypes.byref(opts)))
+    return C
+
+
+def thc_cpd_ldl_solve(H, M, A=None, tasks=None, wait_limit_s=0.0, stream=None, ldl="auto"):
     """A with A H = M (H: R x R SPD, M: n x R) by the library's dataflow LDL^T and backward
     solve, pseudo-inverse on a failed pivot. tasks: None (the library's schedule) or an
     int16 array of shape (ntasks, 4) in the format of thc_cpd_ldl_schedule. Returns
@@ -84,7 +96,7 @@ def thc_cpd_ldl_solve(H, M, A=None, tasks=None, wait_limit_s=0.0, stream=None):
     n = M.shape[0]
     if A is None:
         A = torch.empty(n, R, dtype=torch.float64, device=H.device)
-    opts = _opts("fp64", stream, wait_limit_s=wait_limit_s)
+    opts = _opts("fp64", stream, wait_limit_s=wait_limit_s, ldl=ldl)
     used = ctypes.c_int(0)
     tp, nt = None, 0
     if tasks is not None:

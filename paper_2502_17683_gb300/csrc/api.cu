@@ -15,6 +15,7 @@
 #include "thc_cpd.h"
 #include "f64.cuh"
 #include "mixed.cuh"
+#include "oz.cuh"
 #include "prof.cuh"
 
 namespace {
@@ -89,7 +90,8 @@ thc_cpd_status check_prec(const thc_cpd_opts* opts) {
     if (p != THC_CPD_FP64 && !mixed_supported())
         return set_err(THC_CPD_ERR_UNSUPPORTED, "split tensor-core precision needs an sm_103 device");
     const int l = opts ? opts->ldl : THC_CPD_LDL_AUTO;
-    if (l != THC_CPD_LDL_AUTO && l != THC_CPD_LDL_BLOCKED && l != THC_CPD_LDL_DATAFLOW)
+    if (l != THC_CPD_LDL_AUTO && l != THC_CPD_LDL_BLOCKED && l != THC_CPD_LDL_DATAFLOW &&
+        l != THC_CPD_LDL_EMULATED)
         return set_err(THC_CPD_ERR_ARG, "unknown ldl variant %d", l);
     return THC_CPD_OK;
 }
@@ -109,6 +111,8 @@ cudaStream_t stream_of(const thc_cpd_opts* o) {
 thc_cpd_status kernel_errors(bool mixed) {
     if (int e = flow_take_error())
         return set_err(THC_CPD_ERR_TIMEOUT, "LDL^T dataflow wait gave up (code %d)", e);
+    if (int e = oz_take_error())
+        return set_err(THC_CPD_ERR_TIMEOUT, "emulated-product kernel wait gave up (code %d)", e);
     if (mixed) {
         if (int e = mixed_take_error())
             return set_err(THC_CPD_ERR_TIMEOUT, "tensor-core kernel wait gave up (code %d)", e);
@@ -154,6 +158,9 @@ struct Ctx {
     // for the batched driver, where problems share the GPU.
     bool dataflow = true;
     int flow_ctas = 0;
+    // two-level factorisation with emulated FP64 tensor-core trailing updates
+    bool emulated = false;
+    OzWs oz;
     double* part = nullptr;
     size_t part_cap = 0;
     double* red = nullptr;
@@ -199,6 +206,13 @@ struct Ctx {
 };
 
 enum : unsigned { NEED_ALS = 1, NEED_NORM = 2, NEED_SAFE = 4, NEED_BATCHED = 8 };
+
+// Whether a single problem's LDL^T runs in panels with emulated tensor-core updates: on
+// request (R above one panel and within the panel plans' range), never otherwise yet.
+bool use_emulated_ldl(int ldl, int R, int nmax) {
+    const bool fits = R > kOzPanel && R <= 4096 && cdiv((long)R + nmax - kOzPanel, 16) <= 256;
+    return ldl == THC_CPD_LDL_EMULATED && fits;
+}
 
 // grid cap of the dataflow factorisation when the batched driver is asked for it
 constexpr int kBatchedFlowCtas = 32;
@@ -250,6 +264,12 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     const bool mixed = c.prec != THC_CPD_FP64;
     const bool tf32 = c.prec == THC_CPD_TF32X3;
     if (mixed) bytes += mixed_ws_bytes(tf32, s.o, s.v, Rt, R);
+    // the factorisation: plans (host task lists, uploaded once per shape) are prepared here,
+    // never inside a capture
+    const int ldl = opts ? opts->ldl : THC_CPD_LDL_AUTO;
+    c.emulated = !(need & NEED_BATCHED) && use_emulated_ldl(ldl, R, nmax) && oz_prepare(R, s.o) &&
+                 oz_prepare(R, s.v);
+    if (c.emulated) bytes += oz_ws_bytes(R + nmax, R);
     CK(cudaMallocAsync(&c.block, bytes, c.st));
     Arena ar;
     ar.base = (char*)c.block;
@@ -289,10 +309,10 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
         mixed_ws_carve(c.mx, ar, tf32, s.o, s.v, Rt, R);
         CK(mixed_setup(c.mx, c.st, Xo, Xv, Z));
     }
+    if (c.emulated) oz_ws_carve(c.oz, ar, R + nmax, R);
     fill(c.st, c.ones, R, 1.0);
-    // dataflow task lists (allocated and uploaded once per shape, never inside a capture)
-    const int ldl = opts ? opts->ldl : THC_CPD_LDL_AUTO;
-    c.dataflow = ldl == THC_CPD_LDL_DATAFLOW || (ldl == THC_CPD_LDL_AUTO && !(need & NEED_BATCHED));
+    c.dataflow = c.emulated || ldl == THC_CPD_LDL_DATAFLOW ||
+                 (ldl == THC_CPD_LDL_AUTO && !(need & NEED_BATCHED));
     c.flow_ctas = (need & NEED_BATCHED) ? kBatchedFlowCtas : 0;
     if (c.dataflow) {
         flow_prepare(R, s.o);
@@ -399,7 +419,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
         CK(cudaMemcpyAsync(c.Haug, c.Hsave, sizeof(double) * R * R, cudaMemcpyDeviceToDevice, c.st));
     }
     chol_solve(c.st, R, n, c.Haug, A[k], c.LinvD, c.LinvD + (size_t)R * R, c.sc, k, c.counters,
-               c.dataflow ? c.flow_sync : nullptr, c.flow_ctas, c.bs_sync);
+               c.dataflow ? c.flow_sync : nullptr, c.flow_ctas, c.bs_sync, c.emulated ? &c.oz : nullptr);
     if (safe) {
         DevScalars* h = host_scalars();
         if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
@@ -1294,7 +1314,39 @@ thc_cpd_status thc_cpd_als_trajectory(int o, int v, int Rt, int R, const double*
 
 }  // extern "C"
 
-extern "C" thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M, double* A,
+extern "C" thc_cpd_status thc_cpd_emulated_gemm(int M, int N, int K, const double* A, int lda, const double* B,
+                                     int ldb, double* C, int ldc, const thc_cpd_opts* opts) {
+    if (M < 1 || N < 1 || K < 1 || M > 4096 || N > 4096 || lda < K || ldb < K || ldc < N)
+        return set_err(THC_CPD_ERR_SHAPE, "bad emulated GEMM shape %d x %d x %d (lda %d ldb %d ldc %d)",
+                       M, N, K, lda, ldb, ldc);
+    if (!A || !B || !C) return set_err(THC_CPD_ERR_ARG, "A, B and C must be non-null");
+    if (!oz_available())
+        return set_err(THC_CPD_ERR_UNSUPPORTED, "the emulated product needs an sm_103 device");
+    cudaStream_t st = stream_of(opts);
+    const size_t bytes = oz_ws_bytes(M, N);
+    struct Ws {
+        void* p = nullptr;
+        cudaStream_t st;
+        ~Ws() {
+            if (p) cudaFreeAsync(p, st);
+        }
+    } ws;
+    ws.st = st;
+    CK(cudaMallocAsync(&ws.p, bytes, st));
+    Arena ar;
+    ar.base = (char*)ws.p;
+    ar.cap = bytes;
+    OzWs oz;
+    oz_ws_carve(oz, ar, M, N);
+    CK(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * N, M, st));
+    CK(oz_gemm(st, M, N, K, A, lda, B, ldb, C, ldc, 1.0, false, oz));
+    CK(cudaStreamSynchronize(st));
+    if (int e = oz_take_error())
+        return set_err(THC_CPD_ERR_TIMEOUT, "emulated-product kernel wait gave up (code %d)", e);
+    return THC_CPD_OK;
+}
+
+thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M, double* A,
                                  const short* tasks, int ntasks, int* used_pinv,
                                  const thc_cpd_opts* opts) {
     if (R < 1 || R > 2048 || n < 1 || n > 4096)
@@ -1310,7 +1362,9 @@ extern "C" thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const
     set_wait_limit(opts);
     cudaStream_t st = stream_of(opts);
     const size_t RR = (size_t)R * R, nR = (size_t)n * R;
-    size_t bytes = Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
+    const bool emu = use_emulated_ldl(opts ? opts->ldl : THC_CPD_LDL_AUTO, R, n) && !tasks &&
+                     oz_prepare(R, n);
+    size_t bytes = (emu ? oz_ws_bytes(R + n, R) : 0) + Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
                    Arena::need<double>(std::max(RR, nR)) + Arena::need<double>(R) +
                    Arena::need<int>(flow_sync_ints(R, n)) + Arena::need<int>(bsolve_sync_ints(n)) +
                    Arena::need<DevScalars>(1) + Arena::need<short>(4 * (size_t)std::max(ntasks, 1));
@@ -1337,6 +1391,8 @@ extern "C" thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const
     int* bsync = ar.take<int>(bsolve_sync_ints(n));
     DevScalars* sc = ar.take<DevScalars>(1);
     void* dtasks = ar.take<short>(4 * (size_t)std::max(ntasks, 1));
+    OzWs oz;
+    if (emu) oz_ws_carve(oz, ar, R + n, R);
     CK(cudaMemsetAsync(fsync, 0, sizeof(int) * flow_sync_ints(R, n), st));
     CK(cudaMemsetAsync(bsync, 0, sizeof(int) * bsolve_sync_ints(n), st));
     scalars_init(st, sc, 0.0);
@@ -1347,6 +1403,8 @@ extern "C" thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const
         ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
         if (tasks)
             CK(ldl_flow_tasks(st, R, n, Haug, P, dinv, sc, 0, fsync, tasks, ntasks, dtasks));
+        else if (emu)
+            CK(ldl_oz(st, R, n, Haug, P, dinv, sc, 0, fsync, oz));
         else
             CK(ldl_flow(st, R, n, Haug, P, dinv, sc, 0, fsync));
     }
@@ -1360,6 +1418,8 @@ extern "C" thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const
     CK(cudaStreamSynchronize(st));
     if (int e = flow_take_error())
         return set_err(THC_CPD_ERR_TIMEOUT, "LDL^T dataflow wait gave up (code %d)", e);
+    if (int e = oz_take_error())
+        return set_err(THC_CPD_ERR_TIMEOUT, "emulated-product kernel wait gave up (code %d)", e);
     if (h->fail_mask) {
         int sweeps = 0;
         CK(pinv_solve(st, R, n, Hsave, M, A, V, w, T, &sweeps));

@@ -33,9 +33,12 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   with only the shared memory they use (problems running side by side).
 //   bs_sync: bsolve_sync_ints(n) ints, the progress counters of the backward solve (by
 //   column slices, ldl_flow.cu); zero before the first use, left zero by each launch.
+//   oz: with it (and flow_sync) the factorisation runs in 128-column panels with emulated
+//   FP64 tensor-core trailing updates (ldl_oz, oz.cuh).
+struct OzWs;
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
-                int* bs_sync);
+                int* bs_sync, const OzWs* oz = nullptr);
 
 // Dataflow LDL^T (ldl_flow.cu): ints of progress state for R and n <= nmax; plan set-up
 // for (R, n) (false: too large or the task order failed its check; use the blocked path);
@@ -51,6 +54,13 @@ int flow_take_error();
 cudaError_t ldl_flow_tasks(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
                            DevScalars* sc, int mode, int* sync, const short* host_tasks,
                            int ntasks, void* dev_tasks);
+// One panel of the two-level factorisation: columns [j0, j0 + bw) of the (R + n) x R matrix
+// Haug (ld R), all rows from j0 down, as one dataflow launch whose "appended rows" are every
+// row below the panel's diagonal block (their L, or Y for the M rows, in the panel columns).
+// The trailing update is the caller's. A plan for (bw, R + n - j0 - bw) must exist
+// (flow_prepare); the pivot threshold uses the whole order R.
+cudaError_t ldl_flow_panel(cudaStream_t st, int R, int n, int j0, int bw, double* Haug, double* P,
+                           double* dinv, DevScalars* sc, int mode, int* sync);
 // Index of the first task whose type or tile indices are out of range, or -1.
 int flow_task_check(int R, int n, const short* tasks, int ntasks);
 // Limit of every wait of the dataflow LDL^T and the backward solve launched afterwards from

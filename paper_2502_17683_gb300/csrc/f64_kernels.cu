@@ -11,6 +11,7 @@
 #include <algorithm>
 
 #include "f64.cuh"
+#include "oz.cuh"
 #include "ldl_common.cuh"
 #include "prof.cuh"
 
@@ -563,10 +564,12 @@ k_ldl_update(double* __restrict__ H, const double* __restrict__ P, double* __res
 
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
-                int* bs_sync) {
+                int* bs_sync, const OzWs* oz) {
     const int nrows = R + n;
     const int nJ = cdiv(R, NB);
-    if (flow_sync && flow_prepare(R, n)) {
+    if (oz && flow_sync) {
+        ldl_oz(st, R, n, Haug, P, dinv, sc, mode, flow_sync, *oz);
+    } else if (flow_sync && flow_prepare(R, n)) {
         ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
         ldl_flow(st, R, n, Haug, P, dinv, sc, mode, flow_sync, flow_ctas);
     } else {

@@ -99,6 +99,7 @@ struct ChainSmem {
     volatile int full[2];    // last step written to buffer b
     volatile int empty[2];   // last step the chain has taken out of buffer b
     volatile int live;       // 0 once the chain is aborting: the publisher releases nothing
+    volatile int pub;        // steps whose two barriers (7 and 8) the publisher has passed
 };
 
 struct WorkerSmem {
@@ -163,6 +164,23 @@ constexpr int kProducerThreads = 224;  // warps 8-14 prefetch the chain's tiles
 // Warp 15 publishes the chain's progress: after bar.arrive 7 / 8 by the 256 chain threads
 // (tile (s, s-1) substituted; tile (s, s) factorised) it fences and releases sdone[s] /
 // fdone, so that the fence's latency is not on the chain's path.
+
+// The chain arrives at barriers 7 and 8 without waiting, so before its arrivals of step s
+// it makes sure that the publisher has passed both barriers of step s - 1 (S.pub >= s):
+// arriving again at a named barrier whose previous phase the publisher has not yet joined
+// would complete that phase without the publisher and leave it waiting on a later one.
+// The publisher gets there within a fence and a store once the chain has arrived, so the
+// wait is normally over at once; it is bounded all the same (error code 2 when it gives
+// up).
+template <class S_t>
+__device__ __forceinline__ void wait_publisher(S_t& S, int s) {
+    for (unsigned it = 0; S.pub < s; ++it) {
+        if (it == (1u << 26)) {
+            atomicExch(&g_flow_error, 2);
+            break;
+        }
+    }
+}
 
 // Barrier of the chain's compute threads 0..255 (producer and publisher warps run apart).
 __device__ __forceinline__ void chain_sync() { asm volatile("bar.sync 5, 256;" ::: "memory"); }
@@ -377,6 +395,7 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
             }
             S.Xs[r][c] = x;
             S.Ls[r][c] = l;
+            if (tid == 0) wait_publisher(S, s);
             chain_sync();
             if (tid == 0) S.empty[b] = s;  // buffer b read out (before the barrier above)
             chain_arrive_subst();          // the publisher warp releases sdone[s]
@@ -406,7 +425,11 @@ __device__ void flow_chain(const FlowArgs& a, ChainSmem& S) {
         // aborting (a wait gave up): run out the publisher's barriers, releasing nothing
         if (tid == 0) S.live = 0;
         for (int s2 = s_end; s2 < nT; ++s2) {
-            if (s2 > 0) chain_arrive_subst();
+            if (s2 > 0) {
+                if (tid == 0) wait_publisher(S, s2);
+                chain_sync();
+                chain_arrive_subst();
+            }
             chain_arrive_factor();
         }
     }
@@ -431,6 +454,7 @@ __device__ void flow_publisher(const FlowArgs& a, ChainSmem& S) {
             __threadfence();
             st_release(fdone, s + 1);
         }
+        if (lane == 0) S.pub = s + 1;  // both barriers of step s passed
     }
 }
 
@@ -575,7 +599,10 @@ __global__ void __launch_bounds__(kFlowThreads, 1) k_ldl_flow(FlowArgs a) {
         ChainSmem& S = *reinterpret_cast<ChainSmem*>(smem);
         for (int e = threadIdx.x; e < FB * (FB + 1) / 2; e += blockDim.x) S.pairs[e] = pair_code<FB>(e);
         if (threadIdx.x < FB * FB) S.L[threadIdx.x >> 4][threadIdx.x & 15] = 0.0;
-        if (threadIdx.x == 0) S.live = 1;
+        if (threadIdx.x == 0) {
+            S.live = 1;
+            S.pub = 0;
+        }
         if (threadIdx.x < 2) {
             S.full[threadIdx.x] = 0;
             S.empty[threadIdx.x] = 0;
@@ -966,6 +993,20 @@ int flow_task_check(int R, int n, const short* tasks, int ntasks) {
 }
 
 void flow_set_wait_ns(unsigned long long ns) { t_wait_ns = ns ? ns : kWaitNs; }
+
+cudaError_t ldl_flow_panel(cudaStream_t st, int R, int n, int j0, int bw, double* Haug, double* P,
+                           double* dinv, DevScalars* sc, int mode, int* sync) {
+    const int below = R + n - j0 - bw;
+    const Plan* p = get_plan(bw, below);
+    if (!p) return cudaErrorInvalidValue;
+    const int nsync = kSyncHead + (p->nT + p->nM) * (1 + p->nT);
+    const size_t off = (size_t)j0 * R + j0;
+    FlowArgs a{Haug + off, P + off, dinv + j0, bw, bw + below, p->nT, p->nM, R, R, p->tasks,
+               p->ntasks, p->nmain, p->ncrit, sync, nsync, sc, mode, t_wait_ns};
+    k_ldl_flow<<<p->grid, kFlowThreads, kFlowSmem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
 
 size_t bsolve_sync_ints(int nmax) { return 3 + (size_t)nmax; }
 

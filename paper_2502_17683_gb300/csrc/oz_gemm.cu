@@ -1,0 +1,392 @@
+// FP64-accurate emulated products on the BF16 tensor cores and the two-level LDL^T built
+// on them (see oz.cuh for the arithmetic).
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "f64.cuh"
+#include "oz.cuh"
+#include "prof.cuh"
+#include "tcgen05.cuh"
+
+namespace thc {
+
+__device__ int g_oz_error = 0;
+
+namespace {
+
+constexpr int S = kOzSlices;
+constexpr int KP = kOzPanel;                 // K elements per operand row (2 x 64)
+constexpr int BM = 128;                      // MMA M: rows of the left operand per tile
+constexpr int BN = 64;                       // MMA N: rows of the right operand per tile
+constexpr int A_TILE = BM * 128;             // bytes of one 128 x 64 BF16 box
+constexpr int B_TILE = BN * 128;             // bytes of one 64 x 64 BF16 box
+constexpr int A_STAGES = 4;
+constexpr int B_BYTES = 2 * S * B_TILE;      // both K halves of all right-operand slices
+constexpr int SMEM_BYTES = 1024 + B_BYTES + A_STAGES * A_TILE + 256;
+constexpr int TMEM_COLS = 512;               // S accumulators of BN columns (448 used)
+constexpr int NTHREADS = 192;                // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity, int code) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(&g_oz_error, code);
+    return false;
+}
+
+__device__ __forceinline__ double pow2(int e) {
+    return __longlong_as_double((long long)(e + 1023) << 52);  // e in [-1022, 1023]
+}
+
+// Exponent E of a normal double, |x| in [2^(E-1), 2^E); -2000 for zero, subnormal, inf, NaN.
+__device__ __forceinline__ int exp_of(double x) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    return (ex == 0 || ex == 0x7FF) ? -2000 : ex - 1022;
+}
+
+// The S digits of x relative to the row exponent erow: x ~ 2^erow sum_a d_a 2^(-7-8a),
+// formed exactly in integer arithmetic from the bits of x (X = round(x 2^(55 - erow)),
+// then signed base-256 digits from the least significant one up).
+__device__ __forceinline__ void digits_of(double x, int erow, int (&d)[S]) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    long long X = 0;
+    if (ex != 0 && ex != 0x7FF) {
+        const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+        const int sh = (ex - 1022) - erow + 2;  // <= 2
+        if (sh >= 0)
+            X = m * (1LL << sh);
+        else if (sh > -54)
+            X = (m + (1LL << (-sh - 1))) >> (-sh);
+        if (b < 0) X = -X;
+    }
+#pragma unroll
+    for (int a = S - 1; a > 0; --a) {
+        const long long da = ((X + 128) & 255) - 128;
+        d[a] = (int)da;
+        X = (X - da) / 256;  // exact: X - da is a multiple of 256
+    }
+    d[0] = (int)X;
+}
+
+__device__ __forceinline__ uint16_t bf16_int(int d) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
+}
+
+// One warp per row r < rows: the values src[r * ld + k] (k < K, zero beyond) times the
+// column scale, their row exponent and their S digit slices out[a][r][k] (k < KP).
+// Column scales (which: 0 = none, 1 = D_k 2^-m_k, 2 = 2^m_k with m_k = floor(E(D_k) / 2)
+// and D_k = diag[k * (ldd + 1)]) balance the LDL^T update L D L^T between its two operands
+// with exact powers of two.
+__global__ void __launch_bounds__(256)
+k_oz_split(const double* __restrict__ src, int ld, int rows, int K, const double* __restrict__ diag,
+           int ldd, int which, uint16_t* __restrict__ out, int rows_alloc, int* __restrict__ exps) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= rows) return;
+    const int r = warp;
+    double x[KP / 32];
+    int emax = -2000;
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) {
+        const int k = lane + 32 * q;
+        double v = 0.0;
+        if (k < K) {
+            v = src[(size_t)r * ld + k];
+            if (which) {
+                const double dk = diag[(size_t)k * (ldd + 1)];
+                const int Ek = exp_of(dk);
+                const int mk = (Ek == -2000) ? 0 : (Ek >> 1);
+                v = (which == 1) ? v * (dk * pow2(-mk)) : v * pow2(mk);
+            }
+        }
+        x[q] = v;
+        emax = max(emax, exp_of(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    const int erow = emax == -2000 ? 0 : emax;
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) {
+        const int k = lane + 32 * q;
+        int d[S];
+        digits_of(x[q], erow, d);
+#pragma unroll
+        for (int a = 0; a < S; ++a) out[((size_t)a * rows_alloc + r) * KP + k] = bf16_int(d[a]);
+    }
+    if (lane == 0) exps[r] = erow;
+}
+
+struct UpdArgs {
+    double* C;     // C[i][j] at C[i * ldc + j]
+    int ldc;
+    int mA, mB;    // rows of C (left operand rows) and columns (right operand rows)
+    const int* eA;
+    const int* eB;
+    int tiles_n;   // tiles along mB
+    int lower;     // 1: rows i < mB only on and below the diagonal (LDL^T trailing block)
+    double sign;   // C += sign * A B^T
+};
+
+// C -= A B^T on one 128 x 64 tile from the digit slices: warp 0 loads the right operand's
+// 2 x S boxes once and streams the left operand's 2 x S boxes through a 4-stage ring;
+// warp 1 issues, per left slice a, the MMAs with every right slice b <= S - 1 - a into
+// accumulator a + b (TMEM columns 64 (a + b) ..); warps 2-5 (one row per thread) turn the S
+// integer accumulators into one FP64 value per element and apply it to C. Rows of C below
+// mB (the H part of the LDL^T trailing block) are updated on and below the diagonal only;
+// tiles entirely above it exit at once. Every wait is bounded.
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+            const UpdArgs args) {
+    const int tm = blockIdx.x / args.tiles_n, tn = blockIdx.x % args.tiles_n;
+    const int m0 = tm * BM, n0 = tn * BN;
+    if (args.lower && m0 + BM - 1 < args.mB && n0 > m0 + BM - 1) return;  // above the diagonal
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* bsm = smem;                       // [2][S] boxes of B_TILE
+    uint8_t* asm_ = smem + B_BYTES;            // [A_STAGES] boxes of A_TILE
+    uint64_t* bfull = (uint64_t*)(asm_ + A_STAGES * A_TILE);
+    uint64_t* afull = bfull + 1;
+    uint64_t* aempty = afull + A_STAGES;
+    uint64_t* accfull = aempty + A_STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(accfull + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bfull, 1);
+        for (int s = 0; s < A_STAGES; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 1);
+        }
+        mbar_init(accfull, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr int NA = 2 * S;  // left-operand boxes: (K half, slice)
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        mbar_expect_tx(bfull, (uint32_t)B_BYTES);
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < S; ++b) tma_load_3d(bsm + (c * S + b) * B_TILE, &mapB, bfull, 64 * c, n0, b);
+        int it = 0;
+        for (; it < NA; ++it) {
+            const int st = it % A_STAGES;
+            if (!oz_wait(&aempty[st], ((it / A_STAGES) & 1) ^ 1, 1)) break;
+            mbar_expect_tx(&afull[st], (uint32_t)A_TILE);
+            tma_load_3d(asm_ + st * A_TILE, &mapA, &afull[st], 64 * (it / S), m0, it % S);
+        }
+        // every copy issued has landed before the CTA may leave
+        oz_wait(bfull, 0, 2);
+        for (int j = max(0, it - A_STAGES); j < it; ++j) oz_wait(&afull[j % A_STAGES], (j / A_STAGES) & 1, 2);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = make_idesc(false, BM, BN);
+        bool ok = oz_wait(bfull, 0, 3);
+        tc_fence_after();
+        for (int it = 0; it < NA && ok; ++it) {
+            const int st = it % A_STAGES, c = it / S, a = it % S;
+            if (!oz_wait(&afull[st], (it / A_STAGES) & 1, 4)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint64_t ad = sw128_desc(smem_u32(asm_ + st * A_TILE));
+            for (int b = 0; b + a < S; ++b) {
+                const uint64_t bd = sw128_desc(smem_u32(bsm + (c * S + b) * B_TILE));
+                const uint32_t acc = tmem + (uint32_t)((a + b) * BN);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {  // 4 x 16 elements (32 bytes) per 64-wide box
+                    const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                    tc_mma<false>(acc, ad + o, bd + o, idesc, (c | a | kk) ? 1u : 0u);
+                }
+            }
+            tc_commit(&aempty[st]);
+        }
+        tc_commit(accfull);  // also on a failed wait: arrives once the issued MMAs are done
+    } else if (warp >= 2) {
+        // ---- epilogue: one row of the tile per thread ----
+        const int q = warp & 3;  // TMEM lane quarter of this warp
+        const int i = m0 + 32 * q + lane;
+        const bool ok = oz_wait(accfull, 0, 5);
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16);
+        const int ea = (i < args.mA) ? args.eA[i] : 0;
+        double* crow = args.C + (size_t)i * args.ldc;
+#pragma unroll 1
+        for (int cc = 0; cc < BN && ok; cc += 16) {
+            float v[S][16];
+#pragma unroll
+            for (int g = 0; g < S; ++g) tmem_ld16(tbase + (uint32_t)(g * BN + cc), v[g]);
+            if (i >= args.mA) continue;
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+                const int j = n0 + cc + jj;
+                if (j >= args.mB || (args.lower && i < args.mB && j > i)) continue;
+                long long acc[S];
+#pragma unroll
+                for (int g = 0; g < S; ++g) acc[g] = (long long)__float2int_rn(v[g][jj]);
+                // V = sum_g acc_g 2^(8 (S - 1 - g)) = hi 2^32 + lo, exact in 64-bit parts
+                const long long hi = acc[0] * 65536 + acc[1] * 256 + acc[2];
+                const long long lo = acc[3] * 16777216 + acc[4] * 65536 + acc[5] * 256 + acc[6];
+                const int sh = (hi >= (1LL << 29) || hi <= -(1LL << 29)) ? 8 : 0;
+                const long long vs = hi * (1LL << (32 - sh)) + (lo >> sh);
+                // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48); below 2^-1022 it is dropped
+                const int e = ea + args.eB[j] - 62 + sh;
+                const double scale = e < -1022 ? 0.0 : pow2(min(e, 1023));
+                crow[j] = fma(args.sign * (double)vs, scale, crow[j]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---- host ----------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_once;
+bool g_ready = false;
+
+bool oz_init() {
+    std::call_once(g_once, [] {
+        int dev = 0;
+        cudaDeviceProp p;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return;
+        if (!(p.major == 10 && p.minor == 3) || (int)p.sharedMemPerBlockOptin < SMEM_BYTES) return;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return;
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        if (cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+            cudaSuccess)
+            return;
+        g_ready = true;
+    });
+    return g_ready;
+}
+
+// 3-D map over the digit slices [S][rows_alloc][KP] (BF16): box 64 (K) x box_rows x 1.
+bool slice_map(CUtensorMap* m, const uint16_t* base, int rows, int rows_alloc, int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)KP, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)KP * 2, (cuuint64_t)rows_alloc * KP * 2};
+    cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void split(cudaStream_t st, const double* src, int ld, int rows, int K, const double* diag, int ldd,
+           int which, uint16_t* out, int rows_alloc, int* exps) {
+    if (rows <= 0) return;
+    k_oz_split<<<cdiv((long)rows * 32, 256), 256, 0, st>>>(src, ld, rows, K, diag, ldd, which, out,
+                                                           rows_alloc, exps);
+    count_launch();
+}
+
+cudaError_t update(cudaStream_t st, int mA, int mB, double* C, int ldc, const OzWs& ws, bool lower,
+                   double sign) {
+    if (mA <= 0 || mB <= 0) return cudaSuccess;
+    CUtensorMap ma, mb;
+    if (!slice_map(&ma, ws.sA, mA, ws.rowsA, BM) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN))
+        return cudaErrorInvalidValue;
+    UpdArgs a{C, ldc, mA, mB, ws.eA, ws.eB, cdiv(mB, BN), lower ? 1 : 0, sign};
+    const int grid = cdiv(mA, BM) * a.tiles_n;
+    k_oz_update<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t oz_ws_bytes(int rowsA, int rowsB) {
+    return Arena::need<uint16_t>((size_t)S * rowsA * KP) + Arena::need<uint16_t>((size_t)S * rowsB * KP) +
+           Arena::need<int>(rowsA) + Arena::need<int>(rowsB);
+}
+
+bool oz_available() { return oz_init(); }
+
+void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB) {
+    w.rowsA = rowsA;
+    w.rowsB = rowsB;
+    w.sA = ar.take<uint16_t>((size_t)S * w.rowsA * KP);
+    w.sB = ar.take<uint16_t>((size_t)S * w.rowsB * KP);
+    w.eA = ar.take<int>(w.rowsA);
+    w.eB = ar.take<int>(w.rowsB);
+}
+
+bool oz_prepare(int R, int n) {
+    if (!oz_init()) return false;
+    for (int j0 = 0; j0 < R; j0 += KP) {
+        const int bw = std::min(KP, R - j0);
+        if (!flow_prepare(bw, R + n - j0 - bw)) return false;
+    }
+    return true;
+}
+
+cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
+                   DevScalars* sc, int mode, int* sync, const OzWs& ws) {
+    for (int j0 = 0; j0 < R; j0 += KP) {
+        const int bw = std::min(KP, R - j0);
+        const int j1 = j0 + bw;
+        const int mA = R + n - j1, mB = R - j1;
+        cudaError_t e;
+        {
+            // the panel's LDL^T and the substitution of every row below it
+            ProfScope prof(st, KC_CHOL, (double)bw * bw * bw / 3.0 + (double)mA * bw * bw);
+            e = ldl_flow_panel(st, R, n, j0, bw, Haug, P, dinv, sc, mode, sync);
+        }
+        if (e != cudaSuccess) return e;
+        if (j1 >= R) break;
+        const double* below = Haug + (size_t)j1 * R + j0;   // rows j1.., panel columns
+        const double* diag = Haug + (size_t)j0 * R + j0;
+        {
+            ProfScope prof(st, KC_OZ, (double)mB * (mB + 1) * bw + 2.0 * (mA - mB) * mB * bw);
+            split(st, below, R, mA, bw, diag, R, 1, ws.sA, ws.rowsA, ws.eA);
+            split(st, below, R, mB, bw, diag, R, 2, ws.sB, ws.rowsB, ws.eB);
+            e = update(st, mA, mB, Haug + (size_t)j1 * R + j1, R, ws, true, -1.0);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int lda, const double* B,
+                    int ldb, double* C, int ldc, double sign, bool lower, const OzWs& ws) {
+    if (!oz_init()) return cudaErrorNotSupported;
+    if (M > ws.rowsA || N > ws.rowsB) return cudaErrorInvalidValue;
+    for (int k0 = 0; k0 < K; k0 += KP) {
+        const int kb = std::min(KP, K - k0);
+        split(st, A + k0, lda, M, kb, nullptr, 0, 0, ws.sA, ws.rowsA, ws.eA);
+        split(st, B + k0, ldb, N, kb, nullptr, 0, 0, ws.sB, ws.rowsB, ws.eB);
+        const cudaError_t e = update(st, M, N, C, ldc, ws, lower, sign);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+int oz_take_error() {
+    int h = 0, z = 0;
+    cudaMemcpyFromSymbol(&h, g_oz_error, sizeof(int));
+    if (h) cudaMemcpyToSymbol(g_oz_error, &z, sizeof(int));
+    return h;
+}
+
+}  // namespace thc

@@ -64,7 +64,7 @@ def test_argument_validation_happens_before_device_work(lib):
     assert _call_mttkrp(lib, 5, 5, 5, 5, 0, M=None) == _lib.ERR_ARG
     assert _call_mttkrp(lib, 5, 5, 5, 5, 0, prec=9) == _lib.ERR_ARG
     assert b"mode" in lib.thc_cpd_last_error() or b"precision" in lib.thc_cpd_last_error()
-    assert _call_mttkrp(lib, 5, 5, 5, 5, 0, ldl=3) == _lib.ERR_ARG
+    assert _call_mttkrp(lib, 5, 5, 5, 5, 0, ldl=4) == _lib.ERR_ARG
     assert b"ldl" in lib.thc_cpd_last_error()
     out = ctypes.c_double()
     assert lib.thc_cpd_thc_norm2(3, 4, 5, None, 1, 1, ctypes.byref(out), None) == _lib.ERR_ARG

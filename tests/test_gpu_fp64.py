@@ -84,7 +84,7 @@ def test_one_sweep_identical_inputs(api, shape):
     assert rel(got, ref) <= 1e-9
 
 
-@pytest.mark.parametrize("ldl", ["dataflow", "blocked"])
+@pytest.mark.parametrize("ldl", ["dataflow", "blocked", "emulated"])
 @pytest.mark.parametrize("name,shape,sweeps", [("c1", (5, 15, 60, 80), 25),
                                                ("c2", (20, 100, 480, 720), 50)])
 def test_trajectory(api, name, shape, sweeps, ldl):
@@ -129,11 +129,13 @@ def test_planted_recovery_gpu(api):
     assert relerr < 1e-10
 
 
-@pytest.mark.parametrize("ldl,R", [("dataflow", 6), ("blocked", 6), ("dataflow", 40)])
+@pytest.mark.parametrize("ldl,R", [("dataflow", 6), ("blocked", 6), ("dataflow", 40),
+                                   ("emulated", 200)])
 def test_pinv_fallback_rollback(api, ldl, R):
     # two identical columns in every start factor make each H singular: the optimistic
     # sweep fails its LDL^T pivot test, is rolled back, and is replayed with the
-    # pseudo-inverse (R = 40: the failing pivot sits in the dataflow kernel's third tile)
+    # pseudo-inverse (R = 40: the failing pivot sits in the dataflow kernel's third tile;
+    # R = 200: in the second 128-column panel of the emulated two-level factorisation)
     p = make_problem(4, 9, 20, R, seed=6)
     A = [a.copy() for a in p.A]
     for a in A:

@@ -36,7 +36,7 @@ def case():
     return p, nG2, A_ref, lam_ref, loss_ref, fit_ref
 
 
-@pytest.mark.parametrize("ldl", ["auto", "blocked"])
+@pytest.mark.parametrize("ldl", ["auto", "blocked", "emulated"])
 def test_fp64_sweep_at_full_size(api, case, ldl):
     p, nG2, A_ref, lam_ref, loss_ref, fit_ref = case
     o, v, Rt, R = SHAPE

@@ -158,7 +158,9 @@ struct Ctx {
     // for the batched driver, where problems share the GPU.
     bool dataflow = true;
     int flow_ctas = 0;
-    // two-level factorisation with emulated FP64 tensor-core trailing updates
+    // two-level factorisation with emulated FP64 tensor-core trailing updates; with it the
+    // Grams and the FP64-accuracy products of the split path (its loss, the learned step's
+    // trial losses) also run as emulated FP64 products
     bool emulated = false;
     OzWs oz;
     double* part = nullptr;
@@ -269,7 +271,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     const int ldl = opts ? opts->ldl : THC_CPD_LDL_AUTO;
     c.emulated = !(need & NEED_BATCHED) && use_emulated_ldl(ldl, R, nmax) && oz_prepare(R, s.o) &&
                  oz_prepare(R, s.v);
-    if (c.emulated) bytes += oz_ws_bytes(R + nmax, R);
+    if (c.emulated) bytes += oz_ws_bytes(std::max(R + nmax, Rt), R);
     CK(cudaMallocAsync(&c.block, bytes, c.st));
     Arena ar;
     ar.base = (char*)c.block;
@@ -309,7 +311,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
         mixed_ws_carve(c.mx, ar, tf32, s.o, s.v, Rt, R);
         CK(mixed_setup(c.mx, c.st, Xo, Xv, Z));
     }
-    if (c.emulated) oz_ws_carve(c.oz, ar, R + nmax, R);
+    if (c.emulated) oz_ws_carve(c.oz, ar, std::max(R + nmax, Rt), R);
     fill(c.st, c.ones, R, 1.0);
     c.dataflow = c.emulated || ldl == THC_CPD_LDL_DATAFLOW ||
                  (ldl == THC_CPD_LDL_AUTO && !(need & NEED_BATCHED));
@@ -355,19 +357,46 @@ void compute_normG2(Ctx& c) {
     sum_hadamard_normG2(c.st, (long)Rt * Rt, c.Z, c.U, c.red, c.sc);
 }
 
-void project_fp64(Ctx& c, int k, const double* Ak) {
+// An FP64-accuracy product: emulated on the tensor cores when the context has the
+// emulated path (same result up to rounding), else on the FP64 pipes.
+void gemm64(Ctx& c, bool trans_a, int M, int N, int K, const double* A, int lda, const double* B,
+            const double* B2, int ldb, double* C, int ldc, bool symm) {
+    if (c.emulated && M <= c.oz.rowsA && N <= c.oz.rowsB)
+        oz_dgemm(c.st, trans_a, M, N, K, A, lda, B, B2, ldb, C, ldc, nullptr, symm, c.oz);
+    else
+        dgemm(c.st, trans_a, M, N, K, A, lda, B, B2, ldb, C, ldc, nullptr, symm, c.part, c.part_cap);
+}
+
+// W_k = X_k^T A_k; emu: as an emulated product (the split path's FP64 loss), else on the
+// FP64 pipes (the FP64 path's MTTKRP)
+void project_fp64(Ctx& c, int k, const double* Ak, bool emu = false) {
+    if (emu) {
+        gemm64(c, true, c.s.Rt, c.s.R, c.s.n[k], c.X[k], c.s.Rt, Ak, nullptr, c.s.R, c.W[k], c.s.R, false);
+        return;
+    }
     dgemm(c.st, true, c.s.Rt, c.s.R, c.s.n[k], c.X[k], c.s.Rt, Ak, nullptr, c.s.R, c.W[k], c.s.R,
           nullptr, false, c.part, c.part_cap);
 }
 
 void gram_fp64(Ctx& c, int k, const double* Ak) {
+    if (c.emulated) {
+        gemm64(c, true, c.s.R, c.s.R, c.s.n[k], Ak, c.s.R, Ak, nullptr, c.s.R, c.G[k], c.s.R, true);
+        return;
+    }
     dgemm(c.st, true, c.s.R, c.s.R, c.s.n[k], Ak, c.s.R, Ak, nullptr, c.s.R, c.G[k], c.s.R, nullptr,
           true, c.part, c.part_cap);
 }
 
 // Y = Z (W3 o W4) for modes 0,1 and Y = Z^T (W1 o W2) for modes 2,3
-void zgemm_fp64(Ctx& c, int half) {
+void zgemm_fp64(Ctx& c, int half, bool emu = false) {
     const int Rt = c.s.Rt, R = c.s.R;
+    if (emu) {
+        if (half == 0)
+            gemm64(c, false, Rt, R, Rt, c.Z, Rt, c.W[2], c.W[3], R, c.Y, R, false);
+        else
+            gemm64(c, true, Rt, R, Rt, c.Z, Rt, c.W[0], c.W[1], R, c.Y, R, false);
+        return;
+    }
     if (half == 0)
         dgemm(c.st, false, Rt, R, Rt, c.Z, Rt, c.W[2], c.W[3], R, c.Y, R, nullptr, false, c.part, c.part_cap);
     else
@@ -461,8 +490,8 @@ thc_cpd_status sweep(Ctx& c, double* const A[4], double* lam, bool safe, bool ev
             loss_eval(c.st, c.s.Rt, c.s.R, c.Y, c.W[2], c.W[3], lam, c.G, c.red, c.sc, tol);
         } else {
             // the loss is a cancelling difference: FP64 projections and Z product
-            for (int k = 0; k < 4; ++k) project_fp64(c, k, A[k]);
-            zgemm_fp64(c, 1);
+            for (int k = 0; k < 4; ++k) project_fp64(c, k, A[k], true);
+            zgemm_fp64(c, 1, true);
             loss_eval(c.st, c.s.Rt, c.s.R, c.Y, c.W[2], c.W[3], lam, c.G, c.red, c.sc, tol);
         }
     }
@@ -632,12 +661,10 @@ void make_features(const std::vector<double>& loss_hist, const std::vector<std::
 thc_cpd_status trial_loss(Ctx& c, LearnWs& L, double* loss) {
     const int Rt = c.s.Rt, R = c.s.R;
     for (int k = 0; k < 4; ++k) {
-        dgemm(c.st, true, Rt, R, c.s.n[k], c.X[k], Rt, L.T[k], nullptr, R, L.Wtr[k], R, nullptr, false,
-              c.part, c.part_cap);
-        dgemm(c.st, true, R, R, c.s.n[k], L.T[k], R, L.T[k], nullptr, R, L.Gtr[k], R, nullptr, true,
-              c.part, c.part_cap);
+        gemm64(c, true, Rt, R, c.s.n[k], c.X[k], Rt, L.T[k], nullptr, R, L.Wtr[k], R, false);
+        gemm64(c, true, R, R, c.s.n[k], L.T[k], R, L.T[k], nullptr, R, L.Gtr[k], R, true);
     }
-    dgemm(c.st, true, Rt, R, Rt, c.Z, Rt, L.Wtr[0], L.Wtr[1], R, L.Ytr, R, nullptr, false, c.part, c.part_cap);
+    gemm64(c, true, Rt, R, Rt, c.Z, Rt, L.Wtr[0], L.Wtr[1], R, L.Ytr, R, false);
     CK(cudaMemcpyAsync(L.sc, c.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c.st));
     loss_eval(c.st, Rt, R, L.Ytr, L.Wtr[2], L.Wtr[3], L.lamT, L.Gtr, c.red, L.sc, 0.0);
     DevScalars* h = host_scalars();

@@ -65,6 +65,15 @@ cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, doubl
 cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int lda, const double* B,
                     int ldb, double* C, int ldc, double sign, bool lower, const OzWs& ws);
 
+// The FP64 GEMM of f64.cuh (dgemm) emulated on the tensor cores, same semantics:
+//   C[M x N] = op(A)[M x K] (B o B2)[K x N], or E o that product when E is given;
+//   op(A)[m][k] = trans_a ? A[k * lda + m] : A[m * lda + k]; B, B2 row-major (ldb);
+//   symm: C symmetric (M == N); the lower triangle is computed and mirrored.
+// ws must hold M (rowsA) and N (rowsB) rows.
+cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, int lda,
+                     const double* B, const double* B2, int ldb, double* C, int ldc, const double* E,
+                     bool symm, const OzWs& ws);
+
 // Device error word of the emulated-product kernel (bounded waits that gave up); read and
 // clear.
 int oz_take_error();

@@ -18,6 +18,7 @@ __device__ int g_oz_error = 0;
 namespace {
 
 constexpr int S = kOzSlices;
+constexpr int S_ = kOzSlices;
 constexpr int KP = kOzPanel;                 // K elements per operand row (2 x 64)
 constexpr int BM = 128;                      // MMA M: rows of the left operand per tile
 constexpr int BN = 64;                       // MMA N: rows of the right operand per tile
@@ -120,6 +121,68 @@ k_oz_split(const double* __restrict__ src, int ld, int rows, int K, const double
     if (lane == 0) exps[r] = erow;
 }
 
+// Transposed source: output row n < N takes the K chunk [k0, k0 + kb) of column n of the
+// K x N row-major matrix S (ld), times S2 element by element when given (a Hadamard
+// operand): values S[(k0 + k) * ld + n] (* S2[...]). A 128 x 32 slab is staged in shared
+// memory with coalesced reads, then each warp forms four output rows as k_oz_split does.
+__global__ void __launch_bounds__(256)
+k_oz_split_t(const double* __restrict__ S, const double* __restrict__ S2, int ld, int N, int k0,
+             int kb, uint16_t* __restrict__ out, int rows_alloc, int* __restrict__ exps) {
+    __shared__ double tile[KP][33];
+    const int n0 = blockIdx.x * 32, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int kk = warp; kk < KP; kk += 8) {
+        const int n = n0 + lane;
+        double v = 0.0;
+        if (kk < kb && n < N) {
+            const size_t o = (size_t)(k0 + kk) * ld + n;
+            v = S[o];
+            if (S2) v *= S2[o];
+        }
+        tile[kk][lane] = v;
+    }
+    __syncthreads();
+    for (int nn = warp * 4; nn < warp * 4 + 4; ++nn) {
+        const int n = n0 + nn;
+        if (n >= N) break;
+        double x[KP / 32];
+        int emax = -2000;
+#pragma unroll
+        for (int q = 0; q < KP / 32; ++q) {
+            x[q] = tile[lane + 32 * q][nn];
+            emax = max(emax, exp_of(x[q]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        const int erow = emax == -2000 ? 0 : emax;
+#pragma unroll
+        for (int q = 0; q < KP / 32; ++q) {
+            int d[S_];
+            digits_of(x[q], erow, d);
+#pragma unroll
+            for (int a = 0; a < S_; ++a)
+                out[((size_t)a * rows_alloc + n) * KP + lane + 32 * q] = bf16_int(d[a]);
+        }
+        if (lane == 0) exps[n] = erow;
+    }
+}
+
+// C[j][i] = C[i][j] for j > i (the upper triangle of a symmetric result from its lower one)
+__global__ void k_oz_mirror(int n, double* __restrict__ C, int ldc) {
+    __shared__ double t[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;  // tile row, tile column (bj > bi mirrored)
+    if (bj < bi) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bj * 32 + r, j = bi * 32 + tx;  // lower element (i, j), i >= j
+        t[r][tx] = (i < n && j < n) ? C[(size_t)i * ldc + j] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bi * 32 + r, j = bj * 32 + tx;  // upper element (i, j) = lower (j, i)
+        if (i < n && j < n && j > i) C[(size_t)i * ldc + j] = t[tx][r];
+    }
+}
+
 struct UpdArgs {
     double* C;     // C[i][j] at C[i * ldc + j]
     int ldc;
@@ -128,7 +191,9 @@ struct UpdArgs {
     const int* eB;
     int tiles_n;   // tiles along mB
     int lower;     // 1: rows i < mB only on and below the diagonal (LDL^T trailing block)
-    double sign;   // C += sign * A B^T
+    double sign;   // C (+)= sign * E o (A B^T)
+    int accumulate;  // 0: C is overwritten
+    const double* E;  // optional Hadamard factor of the product, indexed like C
 };
 
 // C -= A B^T on one 128 x 64 tile from the digit slices: warp 0 loads the right operand's
@@ -243,8 +308,9 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                 const long long vs = hi * (1LL << (32 - sh)) + (lo >> sh);
                 // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48); below 2^-1022 it is dropped
                 const int e = ea + args.eB[j] - 62 + sh;
-                const double scale = e < -1022 ? 0.0 : pow2(min(e, 1023));
-                crow[j] = fma(args.sign * (double)vs, scale, crow[j]);
+                const double t = (double)vs * (e < -1022 ? 0.0 : pow2(min(e, 1023)));  // exact scaling
+                const double f = args.E ? args.sign * args.E[(size_t)i * args.ldc + j] : args.sign;
+                crow[j] = args.accumulate ? fma(f, t, crow[j]) : f * t;
             }
         }
     }
@@ -302,12 +368,12 @@ void split(cudaStream_t st, const double* src, int ld, int rows, int K, const do
 }
 
 cudaError_t update(cudaStream_t st, int mA, int mB, double* C, int ldc, const OzWs& ws, bool lower,
-                   double sign) {
+                   double sign, bool accumulate = true, const double* E = nullptr) {
     if (mA <= 0 || mB <= 0) return cudaSuccess;
     CUtensorMap ma, mb;
     if (!slice_map(&ma, ws.sA, mA, ws.rowsA, BM) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN))
         return cudaErrorInvalidValue;
-    UpdArgs a{C, ldc, mA, mB, ws.eA, ws.eB, cdiv(mB, BN), lower ? 1 : 0, sign};
+    UpdArgs a{C, ldc, mA, mB, ws.eA, ws.eB, cdiv(mB, BN), lower ? 1 : 0, sign, accumulate ? 1 : 0, E};
     const int grid = cdiv(mA, BM) * a.tiles_n;
     k_oz_update<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, a);
     count_launch();
@@ -378,6 +444,35 @@ cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int l
         split(st, B + k0, ldb, N, kb, nullptr, 0, 0, ws.sB, ws.rowsB, ws.eB);
         const cudaError_t e = update(st, M, N, C, ldc, ws, lower, sign);
         if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, int lda,
+                     const double* B, const double* B2, int ldb, double* C, int ldc, const double* E,
+                     bool symm, const OzWs& ws) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (!oz_init()) return cudaErrorNotSupported;
+    if (M > ws.rowsA || N > ws.rowsB || (symm && M != N)) return cudaErrorInvalidValue;
+    if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * N, M, st);
+    ProfScope prof(st, KC_OZ, (symm ? 1.0 : 2.0) * M * (double)N * K);
+    for (int k0 = 0; k0 < K; k0 += KP) {
+        const int kb = std::min(KP, K - k0);
+        if (trans_a) {
+            k_oz_split_t<<<cdiv(M, 32), 256, 0, st>>>(A, nullptr, lda, M, k0, kb, ws.sA, ws.rowsA, ws.eA);
+            count_launch();
+        } else {
+            split(st, A + k0, lda, M, kb, nullptr, 0, 0, ws.sA, ws.rowsA, ws.eA);
+        }
+        k_oz_split_t<<<cdiv(N, 32), 256, 0, st>>>(B, B2, ldb, N, k0, kb, ws.sB, ws.rowsB, ws.eB);
+        count_launch();
+        const cudaError_t e = update(st, M, N, C, ldc, ws, symm, 1.0, k0 > 0, E);
+        if (e != cudaSuccess) return e;
+    }
+    if (symm && N > 1) {
+        const int nt = cdiv(N, 32);
+        k_oz_mirror<<<dim3(nt, nt), 256, 0, st>>>(N, C, ldc);
+        count_launch();
     }
     return cudaGetLastError();
 }

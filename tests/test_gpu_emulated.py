@@ -110,3 +110,24 @@ def test_emulated_and_dataflow_ldl_agree_in_als(api):
     assert abs(fits[0] - fits[2]) <= 1e-12
     for a, b in zip(facs[0], facs[2]):
         assert rel(a, b) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_split_path_fp64_loss_through_emulated_products(api, prec):
+    # with the emulated path the split-precision run takes its FP64 loss (projections and
+    # the Z product) and the Grams from emulated products: the reported fit must be the
+    # exact FP64 fit of the returned factors, as computed by the FP64-pipe loss entry point
+    from tests._util import to_dev
+    from thc_inputs import make_problem
+    p = make_problem(20, 100, 480, 720, seed=12)
+    d = to_dev(p, torch)
+    lam = torch.ones(720, dtype=torch.float64, device="cuda")
+    out = api.thc_cpd_als(d["Xo"], d["Xv"], d["Z"], d["A"], lam, 3, 0.0, precision=prec,
+                          ldl="emulated")
+    loss, fit = api.thc_cpd_loss(d["Xo"], d["Xv"], d["Z"], d["A"], lam)
+    nG2 = O.thc_norm2(p.Xo, p.Xv, p.Z)
+    assert abs(out["loss"] - loss) <= 1e-12 * nG2
+    assert abs(out["fit"] - fit) <= 1e-12
+    # and the run itself matches the oracle's sweeps to the split path's per-sweep bound
+    ref = O.als(p.Xo, p.Xv, p.Z, p.A, 3)
+    assert abs(out["fit"] - ref["fits"][-1]) <= 1e-5

@@ -103,6 +103,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without its wait: several can be in flight; tmem_ld_wait() completes them
+// all and pins the destination registers after the wait.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[N][16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int g = 0; g < N; ++g)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) asm volatile("" : "+r"(r[g][k]));
+}
+
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA with the
 // 128-byte swizzle: 8-row x 128-byte atoms, 1024 bytes apart (stride byte offset);
 // the leading byte offset is unused for this layout; descriptor version 1.

@@ -1,6 +1,7 @@
 """The FP64-accurate product on the BF16 tensor cores (thc_cpd_emulated_gemm: exact integer
 digit slices, exact tensor-core digit products, exact 64-bit recombination, one rounding)
-and the normal-equation solve whose trailing updates run on it (THC_CPD_LDL_EMULATED),
+and the normal-equation solve whose trailing updates run on it (THC_CPD_LDL_EMULATED; with
+128 or more right-hand sides the backward solve too runs in blocks with emulated updates),
 against FP64 references.
 
 Bounds. Each row of A and of B keeps its digits down to 2^-55 of its largest entry, so the
@@ -81,7 +82,7 @@ def _normal_equations(R, n, seed, dims=(9, 40, 9)):
     return H, rng.standard_normal((n, R))
 
 
-@pytest.mark.parametrize("R,n", [(129, 3), (300, 50), (720, 100), (1800, 250)])
+@pytest.mark.parametrize("R,n", [(129, 3), (300, 50), (300, 200), (720, 100), (1800, 250)])
 def test_emulated_ldl_solve_matches_oracle(api, R, n):
     H, M = _normal_equations(R, n, seed=R)
     Aref, used_ref = O.solve_normal_equations(M, H)

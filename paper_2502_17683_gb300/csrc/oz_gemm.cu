@@ -21,14 +21,16 @@ constexpr int S = kOzSlices;
 constexpr int S_ = kOzSlices;
 constexpr int KP = kOzPanel;                 // K elements per operand row (2 x 64)
 constexpr int BM = 128;                      // MMA M: rows of the left operand per tile
-constexpr int BN = 64;                       // MMA N: rows of the right operand per tile
-constexpr int A_TILE = BM * 128;             // bytes of one 128 x 64 BF16 box
-constexpr int B_TILE = BN * 128;             // bytes of one 64 x 64 BF16 box
-constexpr int A_STAGES = 4;
-constexpr int B_BYTES = 2 * S * B_TILE;      // both K halves of all right-operand slices
-constexpr int SMEM_BYTES = 1024 + B_BYTES + A_STAGES * A_TILE + 256;
-constexpr int TMEM_COLS = 512;               // S accumulators of BN columns (448 used)
-constexpr int NTHREADS = 192;                // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
+constexpr int BN = 32;                       // MMA N: rows of the right operand per tile
+constexpr int A_TILE = BM * 128;             // bytes of one 128 x 64 BF16 box (one slice, one K half)
+constexpr int B_HALF = S * BN * 128;         // all right-operand slices of one K half (28 KB)
+constexpr int A_STAGES = 6;
+constexpr int B_STAGES = 2;
+constexpr int SMEM_BYTES = 1024 + A_STAGES * A_TILE + B_STAGES * B_HALF + 256;
+constexpr int ACC_SET = S * BN;              // TMEM columns of one set of S accumulators (224)
+constexpr int TMEM_COLS = 512;               // two sets: the epilogue drains one, the MMAs fill the other
+constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 16 columns each
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 MMA + TMEM, then the epilogue
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity, int code) {
@@ -189,6 +191,7 @@ struct UpdArgs {
     int mA, mB;    // rows of C (left operand rows) and columns (right operand rows)
     const int* eA;
     const int* eB;
+    int tiles_m;   // tiles along mA
     int tiles_n;   // tiles along mB
     int lower;     // 1: rows i < mB only on and below the diagonal (LDL^T trailing block)
     double sign;   // C (+)= sign * E o (A B^T)
@@ -196,37 +199,54 @@ struct UpdArgs {
     const double* E;  // optional Hadamard factor of the product, indexed like C
 };
 
-// C -= A B^T on one 128 x 64 tile from the digit slices: warp 0 loads the right operand's
-// 2 x S boxes once and streams the left operand's 2 x S boxes through a 4-stage ring;
-// warp 1 issues, per left slice a, the MMAs with every right slice b <= S - 1 - a into
-// accumulator a + b (TMEM columns 64 (a + b) ..); warps 2-5 (one row per thread) turn the S
-// integer accumulators into one FP64 value per element and apply it to C. Rows of C below
-// mB (the H part of the LDL^T trailing block) are updated on and below the diagonal only;
-// tiles entirely above it exit at once. Every wait is bounded.
+// Tile (tm, tn) of the update is skipped when it lies entirely above the diagonal of a
+// lower-only (symmetric or LDL^T trailing) block.
+__device__ __forceinline__ bool tile_active(const UpdArgs& a, int t, int& m0, int& n0) {
+    m0 = (t / a.tiles_n) * BM;
+    n0 = (t % a.tiles_n) * BN;
+    return !(a.lower && m0 + BM - 1 < a.mB && n0 > m0 + BM - 1);
+}
+
+// C (+)= sign * E o (A B^T) from the digit slices, one 128 x 32 output tile at a time, each
+// CTA (one per SM) walking tiles blockIdx.x, blockIdx.x + gridDim.x, ...: warp 0 streams,
+// per tile and K half, the right operand's S boxes (one 28 KB stage) and the left
+// operand's S boxes (16 KB stages) by 3-D TMA; warp 1 issues, per left slice a, the BF16
+// MMAs with the right slices b <= S - 1 - a into accumulator a + b of the tile's set (two
+// sets of S x 32 TMEM columns alternate between tiles); eight epilogue warps (a lane
+// quarter and 16 columns each) turn the previous tile's S integer accumulators into one
+// FP64 value per element and apply it, overlapping the MMAs of the next tile. Rows of C
+// below mB on a lower-only block are updated on and below the diagonal only. Every wait is
+// bounded.
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
             const UpdArgs args) {
-    const int tm = blockIdx.x / args.tiles_n, tn = blockIdx.x % args.tiles_n;
-    const int m0 = tm * BM, n0 = tn * BN;
-    if (args.lower && m0 + BM - 1 < args.mB && n0 > m0 + BM - 1) return;  // above the diagonal
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* bsm = smem;                       // [2][S] boxes of B_TILE
-    uint8_t* asm_ = smem + B_BYTES;            // [A_STAGES] boxes of A_TILE
-    uint64_t* bfull = (uint64_t*)(asm_ + A_STAGES * A_TILE);
-    uint64_t* afull = bfull + 1;
+    uint8_t* asm_ = smem;                               // [A_STAGES] x A_TILE
+    uint8_t* bsm = smem + A_STAGES * A_TILE;            // [B_STAGES] x B_HALF
+    uint64_t* afull = (uint64_t*)(bsm + B_STAGES * B_HALF);
     uint64_t* aempty = afull + A_STAGES;
-    uint64_t* accfull = aempty + A_STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(accfull + 1);
+    uint64_t* bfull = aempty + A_STAGES;
+    uint64_t* bempty = bfull + B_STAGES;
+    uint64_t* accfull = bempty + B_STAGES;              // [2]
+    uint64_t* accempty = accfull + 2;                   // [2]
+    uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = args.tiles_m * args.tiles_n;
 
     if (threadIdx.x == 0) {
-        mbar_init(bfull, 1);
-        for (int s = 0; s < A_STAGES; ++s) {
-            mbar_init(&afull[s], 1);
-            mbar_init(&aempty[s], 1);
+        for (int i = 0; i < A_STAGES; ++i) {
+            mbar_init(&afull[i], 1);
+            mbar_init(&aempty[i], 1);
         }
-        mbar_init(accfull, 1);
+        for (int i = 0; i < B_STAGES; ++i) {
+            mbar_init(&bfull[i], 1);
+            mbar_init(&bempty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accempty[i], EPI_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -237,93 +257,126 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr int NA = 2 * S;  // left-operand boxes: (K half, slice)
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer ----
-        mbar_expect_tx(bfull, (uint32_t)B_BYTES);
-        for (int c = 0; c < 2; ++c)
-            for (int b = 0; b < S; ++b) tma_load_3d(bsm + (c * S + b) * B_TILE, &mapB, bfull, 64 * c, n0, b);
-        int it = 0;
-        for (; it < NA; ++it) {
-            const int st = it % A_STAGES;
-            if (!oz_wait(&aempty[st], ((it / A_STAGES) & 1) ^ 1, 1)) break;
-            mbar_expect_tx(&afull[st], (uint32_t)A_TILE);
-            tma_load_3d(asm_ + st * A_TILE, &mapA, &afull[st], 64 * (it / S), m0, it % S);
+        int ia = 0, ib = 0;  // positions in the two rings, over all tiles of this CTA
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int m0, n0;
+            if (!tile_active(args, t, m0, n0)) continue;
+            for (int c = 0; c < 2 && ok; ++c) {
+                const int sb = ib % B_STAGES;
+                if (!oz_wait(&bempty[sb], ((ib / B_STAGES) & 1) ^ 1, 1)) { ok = false; break; }
+                mbar_expect_tx(&bfull[sb], (uint32_t)B_HALF);
+                for (int b = 0; b < S; ++b)
+                    tma_load_3d(bsm + sb * B_HALF + b * (BN * 128), &mapB, &bfull[sb], 64 * c, n0, b);
+                ++ib;
+                for (int a = 0; a < S; ++a, ++ia) {
+                    const int sa = ia % A_STAGES;
+                    if (!oz_wait(&aempty[sa], ((ia / A_STAGES) & 1) ^ 1, 1)) { ok = false; break; }
+                    mbar_expect_tx(&afull[sa], (uint32_t)A_TILE);
+                    tma_load_3d(asm_ + sa * A_TILE, &mapA, &afull[sa], 64 * c, m0, a);
+                }
+            }
         }
         // every copy issued has landed before the CTA may leave
-        oz_wait(bfull, 0, 2);
-        for (int j = max(0, it - A_STAGES); j < it; ++j) oz_wait(&afull[j % A_STAGES], (j / A_STAGES) & 1, 2);
+        for (int j = max(0, ia - A_STAGES); j < ia; ++j) oz_wait(&afull[j % A_STAGES], (j / A_STAGES) & 1, 2);
+        for (int j = max(0, ib - B_STAGES); j < ib; ++j) oz_wait(&bfull[j % B_STAGES], (j / B_STAGES) & 1, 2);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
         const uint32_t idesc = make_idesc(false, BM, BN);
-        bool ok = oz_wait(bfull, 0, 3);
-        tc_fence_after();
-        for (int it = 0; it < NA && ok; ++it) {
-            const int st = it % A_STAGES, c = it / S, a = it % S;
-            if (!oz_wait(&afull[st], (it / A_STAGES) & 1, 4)) {
-                ok = false;
-                break;
-            }
+        int ia = 0, ib = 0, i = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int m0, n0;
+            if (!tile_active(args, t, m0, n0)) continue;
+            const int set = i & 1;
+            // accumulator set `set` is free once the epilogue has drained tile i - 2
+            if (i >= 2 && !oz_wait(&accempty[set], ((i >> 1) - 1) & 1, 5)) { ok = false; break; }
             tc_fence_after();
-            const uint64_t ad = sw128_desc(smem_u32(asm_ + st * A_TILE));
-            for (int b = 0; b + a < S; ++b) {
-                const uint64_t bd = sw128_desc(smem_u32(bsm + (c * S + b) * B_TILE));
-                const uint32_t acc = tmem + (uint32_t)((a + b) * BN);
+            const uint32_t acc0 = tmem + (uint32_t)(set * ACC_SET);
+            for (int c = 0; c < 2 && ok; ++c) {
+                const int sb = ib % B_STAGES;
+                if (!oz_wait(&bfull[sb], (ib / B_STAGES) & 1, 3)) { ok = false; break; }
+                for (int a = 0; a < S; ++a, ++ia) {
+                    const int sa = ia % A_STAGES;
+                    if (!oz_wait(&afull[sa], (ia / A_STAGES) & 1, 4)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t ad = sw128_desc(smem_u32(asm_ + sa * A_TILE));
+                    for (int b = 0; b + a < S; ++b) {
+                        const uint64_t bd = sw128_desc(smem_u32(bsm + sb * B_HALF + b * (BN * 128)));
+                        const uint32_t acc = acc0 + (uint32_t)((a + b) * BN);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {  // 4 x 16 elements (32 bytes) per 64-wide box
-                    const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                    tc_mma<false>(acc, ad + o, bd + o, idesc, (c | a | kk) ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk) {  // 4 x 16 elements (32 bytes) per 64-wide box
+                            const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                            tc_mma<false>(acc, ad + o, bd + o, idesc, (c | a | kk) ? 1u : 0u);
+                        }
+                    }
+                    tc_commit(&aempty[sa]);
+                }
+                tc_commit(&bempty[sb]);
+                ++ib;
+            }
+            tc_commit(&accfull[set]);  // also after a failed wait: arrives once the issued MMAs are done
+            ++i;
+        }
+    } else if (warp >= 2) {
+        // ---- epilogue: a lane quarter q and 16 columns h of each tile ----
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int m0, n0;
+            if (!tile_active(args, t, m0, n0)) continue;
+            const int set = i & 1;
+            const bool ok = oz_wait(&accfull[set], (i >> 1) & 1, 6);
+            tc_fence_after();
+            const int row = m0 + 32 * q + lane;
+            const bool rowok = row < args.mA;
+            const int ea = rowok ? args.eA[row] : 0;
+            double* crow = args.C + (size_t)row * args.ldc;
+            const uint32_t tbase = tmem + (uint32_t)(set * ACC_SET + 16 * h) + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+            for (int half = 0; half < 2 && ok; ++half) {
+                uint32_t r[S][8];
+#pragma unroll
+                for (int g = 0; g < S; ++g) tmem_ld8_nowait(tbase + (uint32_t)(g * BN + 8 * half), r[g]);
+                // the row's 8 outputs and the column exponents are fetched while the
+                // tensor-memory loads are in flight
+                double cv[8];
+                int eb[8];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = n0 + 16 * h + 8 * half + jj;
+                    cv[jj] = (rowok && j < args.mB && args.accumulate) ? crow[j] : 0.0;
+                    eb[jj] = j < args.mB ? __ldg(args.eB + j) : 0;
+                }
+                tmem_ld_wait(r);
+                if (!rowok) continue;
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = n0 + 16 * h + 8 * half + jj;
+                    if (j >= args.mB || (args.lower && row < args.mB && j > row)) continue;
+                    long long acc[S];
+#pragma unroll
+                    for (int g = 0; g < S; ++g) acc[g] = (long long)__float2int_rn(__uint_as_float(r[g][jj]));
+                    // V = sum_g acc_g 2^(8 (S - 1 - g)) = hi 2^32 + lo, exact in 64-bit parts
+                    const long long hi = acc[0] * 65536 + acc[1] * 256 + acc[2];
+                    const long long lo = acc[3] * 16777216 + acc[4] * 65536 + acc[5] * 256 + acc[6];
+                    const int sh = (hi >= (1LL << 29) || hi <= -(1LL << 29)) ? 8 : 0;
+                    const long long vs = hi * (1LL << (32 - sh)) + (lo >> sh);
+                    // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48); below 2^-1022 it is dropped
+                    const int e = ea + eb[jj] - 62 + sh;
+                    const double tv = (double)vs * (e < -1022 ? 0.0 : pow2(min(e, 1023)));  // exact scaling
+                    const double f = args.E ? args.sign * args.E[(size_t)row * args.ldc + j] : args.sign;
+                    crow[j] = args.accumulate ? fma(f, tv, cv[jj]) : f * tv;
                 }
             }
-            tc_commit(&aempty[st]);
-        }
-        tc_commit(accfull);  // also on a failed wait: arrives once the issued MMAs are done
-    } else if (warp >= 2) {
-        // ---- epilogue: one row of the tile per thread ----
-        const int q = warp & 3;  // TMEM lane quarter of this warp
-        const int i = m0 + 32 * q + lane;
-        const bool ok = oz_wait(accfull, 0, 5);
-        tc_fence_after();
-        const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16);
-        const int ea = (i < args.mA) ? args.eA[i] : 0;
-        double* crow = args.C + (size_t)i * args.ldc;
-        const bool rowok = i < args.mA;
-#pragma unroll 1
-        for (int cc = 0; cc < BN && ok; cc += 16) {
-            uint32_t r[S][16];
-#pragma unroll
-            for (int g = 0; g < S; ++g) tmem_ld16_nowait(tbase + (uint32_t)(g * BN + cc), r[g]);
-            // the row's 16 outputs and the column exponents are fetched while the tensor-memory
-            // loads are in flight (independent loads, one latency for all)
-            double cv[16];
-            int eb[16];
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-                const int j = n0 + cc + jj;
-                cv[jj] = (rowok && j < args.mB && args.accumulate) ? crow[j] : 0.0;
-                eb[jj] = j < args.mB ? __ldg(args.eB + j) : 0;
-            }
-            tmem_ld_wait(r);
-            if (!rowok) continue;
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-                const int j = n0 + cc + jj;
-                if (j >= args.mB || (args.lower && i < args.mB && j > i)) continue;
-                long long acc[S];
-#pragma unroll
-                for (int g = 0; g < S; ++g) acc[g] = (long long)__float2int_rn(__uint_as_float(r[g][jj]));
-                // V = sum_g acc_g 2^(8 (S - 1 - g)) = hi 2^32 + lo, exact in 64-bit parts
-                const long long hi = acc[0] * 65536 + acc[1] * 256 + acc[2];
-                const long long lo = acc[3] * 16777216 + acc[4] * 65536 + acc[5] * 256 + acc[6];
-                const int sh = (hi >= (1LL << 29) || hi <= -(1LL << 29)) ? 8 : 0;
-                const long long vs = hi * (1LL << (32 - sh)) + (lo >> sh);
-                // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48); below 2^-1022 it is dropped
-                const int e = ea + eb[jj] - 62 + sh;
-                const double t = (double)vs * (e < -1022 ? 0.0 : pow2(min(e, 1023)));  // exact scaling
-                const double f = args.E ? args.sign * args.E[(size_t)i * args.ldc + j] : args.sign;
-                crow[j] = args.accumulate ? fma(f, t, cv[jj]) : f * t;
-            }
+            // every TMEM read of this tile has completed (tcgen05.wait::ld)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[set]);
+            ++i;
         }
     }
     tc_fence_before();
@@ -338,6 +391,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
 bool g_ready = false;
+int g_num_sm = 148;
 
 bool oz_init() {
     std::call_once(g_once, [] {
@@ -345,6 +399,7 @@ bool oz_init() {
         cudaDeviceProp p;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return;
         if (!(p.major == 10 && p.minor == 3) || (int)p.sharedMemPerBlockOptin < SMEM_BYTES) return;
+        g_num_sm = p.multiProcessorCount;
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
@@ -385,8 +440,15 @@ cudaError_t update(cudaStream_t st, int mA, int mB, double* C, int ldc, const Oz
     CUtensorMap ma, mb;
     if (!slice_map(&ma, ws.sA, mA, ws.rowsA, BM) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN))
         return cudaErrorInvalidValue;
-    UpdArgs a{C, ldc, mA, mB, ws.eA, ws.eB, cdiv(mB, BN), lower ? 1 : 0, sign, accumulate ? 1 : 0, E};
-    const int grid = cdiv(mA, BM) * a.tiles_n;
+    UpdArgs a{C, ldc, mA, mB, ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0, sign,
+              accumulate ? 1 : 0, E};
+    // persistent: one CTA per SM, at most one per active tile
+    long active = 0;
+    for (int tm = 0; tm < a.tiles_m; ++tm) {
+        const int m0 = tm * BM;
+        active += (lower && m0 + BM - 1 < mB) ? std::min<long>(a.tiles_n, (m0 + BM - 1) / BN + 1) : a.tiles_n;
+    }
+    const int grid = (int)std::max<long>(1, std::min<long>(active, g_num_sm));
     k_oz_update<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, a);
     count_launch();
     return cudaGetLastError();

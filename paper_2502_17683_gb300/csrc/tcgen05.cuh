@@ -115,13 +115,21 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
         : "r"(taddr));
 }
 
-template <int N>
-__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[N][16]) {
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+}
+
+template <int N, int C>
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[N][C]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int g = 0; g < N; ++g)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) asm volatile("" : "+r"(r[g][k]));
+        for (int k = 0; k < C; ++k) asm volatile("" : "+r"(r[g][k]));
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA with the

@@ -136,6 +136,26 @@ def make_planted_noisy(o: int, v: int, rank: int, noise_rank: int = 24, noise_sc
     return THCProblem(o, v, Rt, rank, Xo, Xv, Z, A), planted
 
 
+def make_lt(o: int, v: int, n_alpha: int = 12, seed: int = 0):
+    """Synthetic orbital energies and a Laplace quadrature for the LT-MP2 exchange energy
+    (Eq. lt_D): occupied eps ~ U(-2, -0.5), virtual eps ~ U(0.2, 3); n_alpha Gauss-Legendre
+    points x on [-1, 1] mapped to [0, inf) by s = tau (1 + x) / (1 - x), weights times the
+    Jacobian 2 tau / (1 - x)^2, tau = 1 / (2 gap), gap = min eps_vir - max eps_occ, so that
+    sum w exp(-D s) ~ 1/D. The Gamma / Lambda factors of the paper carry exp(+-eps t / 2), so
+    the four of them multiply to exp(-D t / 2): the points are returned as t = 2 s (weights
+    unchanged). Returns (eps_occ, eps_vir, t, w). (The paper uses 12 Legendre points; the
+    mapping is this build's choice.)"""
+    rng = np.random.default_rng([seed, 0x17])
+    eps_occ = np.sort(rng.uniform(-2.0, -0.5, size=o))
+    eps_vir = np.sort(rng.uniform(0.2, 3.0, size=v))
+    gap = float(np.min(eps_vir) - np.max(eps_occ))
+    tau = 1.0 / (2.0 * gap)
+    x, om = np.polynomial.legendre.leggauss(n_alpha)
+    s_pts = tau * (1.0 + x) / (1.0 - x)
+    w = om * 2.0 * tau / (1.0 - x) ** 2
+    return eps_occ, eps_vir, 2.0 * s_pts, w
+
+
 def round_up(x: int, m: int) -> int:
     return ((x + m - 1) // m) * m
 

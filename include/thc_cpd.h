@@ -261,6 +261,24 @@ int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes);
 thc_cpd_status thc_cpd_emulated_gemm(int M, int N, int K, const double* A, int lda, const double* B,
                                      int ldb, double* C, int ldc, const thc_cpd_opts* opts);
 
+/* The CPD+THC LT-MP2 exchange energy (Sec. 2.2), the consumer of the CP factors: with
+ * the Laplace quadrature factors Lam (nalpha x o, occupied) and Gam (nalpha x v, virtual)
+ * of Eq. mp1_t, amplitudes t[i,a,j,b] = Lam_i Gam_a Lam_j Gam_b X[i,a,j,b] and the
+ * exchange pairing K(T, Y) = -sum_alpha sum_iajb t(T)[i,a,j,b] Y[i,b,j,a]:
+ *   e_single = K(G, Gt)  (Eq. cpd_single_k, factor form O(R_thc^2 R) per point),
+ *   e_double = K(Gt, Gt) (the double-CPD term, O((o + v) R^2) per point),
+ *   e_robust = 2 e_single - e_double (Eq. rob_K; no error of first order in G - Gt),
+ * G the THC block (Eq. THC) and Gt = sum_r lam_r A1 A2 A3 A4 (Eq. cp4). Device inputs as for
+ * thc_cpd_loss (lam may not be NULL); the three energies are returned in host memory (each
+ * pointer may be NULL). The contractions are FP64 GEMMs on the FP64 pipes, or with
+ * opts->ldl = THC_CPD_LDL_EMULATED the FP64-accurate emulated products of the tensor cores;
+ * the reductions run in a fixed order. 1 <= nalpha <= 1024. Synchronises. */
+thc_cpd_status thc_cpd_exchange(int o, int v, int Rt, int R, int nalpha, const double* Xo,
+                                const double* Xv, const double* Z, const double* const A[4],
+                                const double* lam, const double* Lam, const double* Gam,
+                                double* e_single, double* e_double, double* e_robust,
+                                const thc_cpd_opts* opts);
+
 /* Measured FP64 FMA throughput of the device (TFLOP/s, 2 flop per FMA) from a probe kernel
  * of independent FMA chains on every SM (64 warps per SM, best of three timed launches):
  * the roofline denominator of the FP64 kernels (Gram, solve, loss). Synchronises. */

@@ -18,7 +18,7 @@ __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc",
            "thc_cpd_als_batched", "thc_cpd_mlp_init", "thc_cpd_mlp_forward", "thc_cpd_mlp_grad",
            "thc_cpd_mlp_train", "thc_cpd_als_trajectory", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam", "thc_cpd_fp64_fma_rate",
-           "thc_cpd_emulated_gemm", "Opts"]
+           "thc_cpd_emulated_gemm", "thc_cpd_exchange", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -73,6 +73,22 @@ def _ptr4(A, dims, R):
     if len(A) != 4:
         raise ThcCpdError(ERR_ARG, "A must hold four factor matrices")
     return PTR4(*[_dev(a, f"A[{k}]", (dims[k], R)) for k, a in enumerate(A)])
+
+
+def thc_cpd_exchange(Xo, Xv, Z, A, lam, Lam, Gam, emulated=False, stream=None):
+    """CPD+THC LT-MP2 exchange energies (single, double, robust) for the Laplace factors Lam
+    (n_alpha x o) and Gam (n_alpha x v); emulated: FP64-accurate tensor-core products."""
+    o, v, Rt = _dims(Xo, Xv, Z)
+    R = A[0].shape[1]
+    na = Lam.shape[0]
+    opts = _opts("fp64", stream, ldl="emulated" if emulated else "auto")
+    e1, e2, er = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(load().thc_cpd_exchange(o, v, Rt, R, na, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                                  _dev(Z, "Z", (Rt, Rt)), _ptr4(A, (o, v, o, v), R),
+                                  _dev(lam, "lam", (R,)), _dev(Lam, "Lam", (na, o)),
+                                  _dev(Gam, "Gam", (na, v)), ctypes.byref(e1), ctypes.byref(e2),
+                                  ctypes.byref(er), ctypes.byref(opts)))
+    return e1.value, e2.value, er.value
 
 
 def thc_cpd_emulated_gemm(A, B, C=None, stream=None):

@@ -1173,6 +1173,15 @@ int set_error(int s, const char* msg) {
     return s;
 }
 
+int check_problem_args(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                       const double* Z, const double* const* A) {
+    Shape s;
+    CKS(check_shape(o, v, Rt, R, &s));
+    if (!A) return set_err(THC_CPD_ERR_ARG, "A must be non-null");
+    CKS(check_ptrs(Xo, Xv, Z, A));
+    return THC_CPD_OK;
+}
+
 int check_mttkrp_args(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
                       const double* Z, const double* const* A, int mode, const double* M) {
     Shape s;

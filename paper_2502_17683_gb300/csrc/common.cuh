@@ -54,5 +54,8 @@ int set_error(int s, const char* msg);
 // messages. Returns a thc_cpd_status; the message is set on failure.
 int check_mttkrp_args(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
                       const double* Z, const double* const* A, int mode, const double* M);
+// The shape and pointer checks alone (THC factors and the four CP factors).
+int check_problem_args(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
+                       const double* Z, const double* const* A);
 
 }  // namespace thc

@@ -210,9 +210,10 @@ __device__ __forceinline__ bool tile_active(const UpdArgs& a, int t, int& m0, in
 // C (+)= sign * E o (A B^T) from the digit slices, one 128 x 32 output tile at a time, each
 // CTA (one per SM) walking tiles blockIdx.x, blockIdx.x + gridDim.x, ...: warp 0 streams,
 // per tile and K half, the right operand's S boxes (one 28 KB stage) and the left
-// operand's S boxes (16 KB stages) by 3-D TMA; warp 1 issues, per left slice a, the BF16
-// MMAs with the right slices b <= S - 1 - a into accumulator a + b of the tile's set (two
-// sets of S x 32 TMEM columns alternate between tiles); eight epilogue warps (a lane
+// operand's S boxes (16 KB stages) by 3-D TMA; warp 1 issues, per left slice a and K step,
+// one BF16 MMA against the stacked right slices b <= S - 1 - a whose result columns fall
+// into accumulators a + b of the tile's set (two sets of S x 32 TMEM columns alternate
+// between tiles): 7 MMAs of N = 32 (S - a) per K step instead of 28; eight epilogue warps (a lane
 // quarter and 16 columns each) turn the previous tile's S integer accumulators into one
 // FP64 value per element and apply it, overlapping the MMAs of the next tile. Rows of C
 // below mB on a lower-only block are updated on and below the diagonal only. Every wait is
@@ -285,7 +286,6 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int j = max(0, ib - B_STAGES); j < ib; ++j) oz_wait(&bfull[j % B_STAGES], (j / B_STAGES) & 1, 2);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
-        const uint32_t idesc = make_idesc(false, BM, BN);
         int ia = 0, ib = 0, i = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -303,15 +303,17 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                     const int sa = ia % A_STAGES;
                     if (!oz_wait(&afull[sa], (ia / A_STAGES) & 1, 4)) { ok = false; break; }
                     tc_fence_after();
+                    // the right slices b = 0..S-1-a lie stacked in the stage (rows 32 b ..), so
+                    // one MMA of N = 32 (S - a) with its accumulator base at column 32 a puts
+                    // A_a B_b^T at columns 32 (a + b): accumulator a + b, for every b at once
                     const uint64_t ad = sw128_desc(smem_u32(asm_ + sa * A_TILE));
-                    for (int b = 0; b + a < S; ++b) {
-                        const uint64_t bd = sw128_desc(smem_u32(bsm + sb * B_HALF + b * (BN * 128)));
-                        const uint32_t acc = acc0 + (uint32_t)((a + b) * BN);
+                    const uint64_t bd = sw128_desc(smem_u32(bsm + sb * B_HALF));
+                    const uint32_t idesc_a = make_idesc(false, BM, BN * (S - a));
+                    const uint32_t acc = acc0 + (uint32_t)(a * BN);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {  // 4 x 16 elements (32 bytes) per 64-wide box
-                            const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                            tc_mma<false>(acc, ad + o, bd + o, idesc, (c | a | kk) ? 1u : 0u);
-                        }
+                    for (int kk = 0; kk < 4; ++kk) {  // 4 x 16 elements (32 bytes) per 64-wide box
+                        const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                        tc_mma<false>(acc, ad + o, bd + o, idesc_a, (c | a | kk) ? 1u : 0u);
                     }
                     tc_commit(&aempty[sa]);
                 }

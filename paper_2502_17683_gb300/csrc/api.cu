@@ -210,10 +210,13 @@ struct Ctx {
 enum : unsigned { NEED_ALS = 1, NEED_NORM = 2, NEED_SAFE = 4, NEED_BATCHED = 8 };
 
 // Whether a single problem's LDL^T runs in panels with emulated tensor-core updates: on
-// request (R above one panel and within the panel plans' range), never otherwise yet.
+// request, and by default from R = 1024 on (measured on GB300, BF16x3 sweeps: emulated vs
+// dataflow 334 vs 395 sweeps/s at R = 720, 211 vs 207 at 1080, 104 vs 59 at 1800), within
+// the panel plans' range.
+constexpr int kEmulatedMinR = 1024;
 bool use_emulated_ldl(int ldl, int R, int nmax) {
     const bool fits = R > kOzPanel && R <= 4096 && cdiv((long)R + nmax - kOzPanel, 16) <= 256;
-    return ldl == THC_CPD_LDL_EMULATED && fits;
+    return fits && (ldl == THC_CPD_LDL_EMULATED || (ldl == THC_CPD_LDL_AUTO && R >= kEmulatedMinR));
 }
 
 // grid cap of the dataflow factorisation when the batched driver is asked for it
@@ -1444,7 +1447,9 @@ thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M,
         else
             CK(ldl_flow(st, R, n, Haug, P, dinv, sc, 0, fsync));
     }
-    {
+    if (emu && n >= kOzBsolveMinRows) {
+        CK(bsolve_oz(st, R, n, Haug + RR, A, Haug, oz));
+    } else {
         ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
         CK(bsolve_slices(st, R, n, Haug + RR, A, Haug, bsync));
     }

@@ -29,7 +29,7 @@ constexpr int B_STAGES = 2;
 constexpr int SMEM_BYTES = 1024 + A_STAGES * A_TILE + B_STAGES * B_HALF + 256;
 constexpr int ACC_SET = S * BN;              // TMEM columns of one set of S accumulators (224)
 constexpr int TMEM_COLS = 512;               // two sets: the epilogue drains one, the MMAs fill the other
-constexpr int EPI_WARPS = 8;                 // two per TMEM lane quarter, 16 columns each
+constexpr int EPI_WARPS = 16;                // four per TMEM lane quarter, 8 columns each
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 MMA + TMEM, then the epilogue
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
@@ -80,14 +80,11 @@ __device__ __forceinline__ uint16_t bf16_int(int d) {
     return __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
 }
 
-// One warp per row r < rows: the values src[r * ld + k] (k < K, zero beyond) times the
-// column scale, their row exponent and their S digit slices out[a][r][k] (k < KP).
-// Column scales (which: 0 = none, 1 = D_k 2^-m_k, 2 = 2^m_k with m_k = floor(E(D_k) / 2)
-// and D_k = diag[k * (ldd + 1)]) balance the LDL^T update L D L^T between its two operands
-// with exact powers of two.
+// One warp per row r < rows: the values src[r * ld + k] (k < K, zero beyond), their row
+// exponent and their S digit slices out[a][r][k] (k < KP).
 __global__ void __launch_bounds__(256)
-k_oz_split(const double* __restrict__ src, int ld, int rows, int K, const double* __restrict__ diag,
-           int ldd, int which, uint16_t* __restrict__ out, int rows_alloc, int* __restrict__ exps) {
+k_oz_split(const double* __restrict__ src, int ld, int rows, int K, uint16_t* __restrict__ out,
+           int rows_alloc, int* __restrict__ exps) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= rows) return;
     const int r = warp;
@@ -96,18 +93,8 @@ k_oz_split(const double* __restrict__ src, int ld, int rows, int K, const double
 #pragma unroll
     for (int q = 0; q < KP / 32; ++q) {
         const int k = lane + 32 * q;
-        double v = 0.0;
-        if (k < K) {
-            v = src[(size_t)r * ld + k];
-            if (which) {
-                const double dk = diag[(size_t)k * (ldd + 1)];
-                const int Ek = exp_of(dk);
-                const int mk = (Ek == -2000) ? 0 : (Ek >> 1);
-                v = (which == 1) ? v * (dk * pow2(-mk)) : v * pow2(mk);
-            }
-        }
-        x[q] = v;
-        emax = max(emax, exp_of(v));
+        x[q] = k < K ? src[(size_t)r * ld + k] : 0.0;
+        emax = max(emax, exp_of(x[q]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -121,6 +108,62 @@ k_oz_split(const double* __restrict__ src, int ld, int rows, int K, const double
         for (int a = 0; a < S; ++a) out[((size_t)a * rows_alloc + r) * KP + k] = bf16_int(d[a]);
     }
     if (lane == 0) exps[r] = erow;
+}
+
+// The two operands of an LDL^T trailing update from one read of the rows below the panel:
+// row r < mA of src (its first K entries) gives the left-operand row r, scaled per column k
+// by D_k 2^-m_k, and, for r < mB, the right-operand row r, scaled by 2^m_k (m_k =
+// floor(E(D_k) / 2), D_k = diag[k * (ldd + 1)]), each cut into its S digit slices.
+__global__ void __launch_bounds__(256)
+k_oz_split_ldl(const double* __restrict__ src, int ld, int mA, int mB, int K,
+               const double* __restrict__ diag, int ldd, uint16_t* __restrict__ outA, int rowsA,
+               int* __restrict__ expsA, uint16_t* __restrict__ outB, int rowsB, int* __restrict__ expsB) {
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= mA) return;
+    double xa[KP / 32], xb[KP / 32];
+    int ea = -2000, eb = -2000;
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) {
+        const int k = lane + 32 * q;
+        double a = 0.0, b = 0.0;
+        if (k < K) {
+            const double v = src[(size_t)r * ld + k];
+            const double dk = diag[(size_t)k * (ldd + 1)];
+            const int Ek = exp_of(dk);
+            const int mk = (Ek == -2000) ? 0 : (Ek >> 1);
+            a = v * (dk * pow2(-mk));
+            b = v * pow2(mk);
+        }
+        xa[q] = a;
+        xb[q] = b;
+        ea = max(ea, exp_of(a));
+        eb = max(eb, exp_of(b));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+        eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+    }
+    ea = ea == -2000 ? 0 : ea;
+    eb = eb == -2000 ? 0 : eb;
+    const bool hasB = r < mB;
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) {
+        const int k = lane + 32 * q;
+        int d[S];
+        digits_of(xa[q], ea, d);
+#pragma unroll
+        for (int a = 0; a < S; ++a) outA[((size_t)a * rowsA + r) * KP + k] = bf16_int(d[a]);
+        if (hasB) {
+            digits_of(xb[q], eb, d);
+#pragma unroll
+            for (int a = 0; a < S; ++a) outB[((size_t)a * rowsB + r) * KP + k] = bf16_int(d[a]);
+        }
+    }
+    if (lane == 0) {
+        expsA[r] = ea;
+        if (hasB) expsB[r] = eb;
+    }
 }
 
 // Transposed source: output row n < N takes the K chunk [k0, k0 + kb) of column n of the
@@ -185,6 +228,64 @@ __global__ void k_oz_mirror(int n, double* __restrict__ C, int ldc) {
     }
 }
 
+// One 128-column block J of the backward solve A L = Y (L unit lower, strictly-lower part
+// of H): rows i < n, one warp per row, lane l holding columns j0 + l + 32 q. The block's L
+// (bw x bw) is staged in shared memory; columns are solved from the last to the first,
+// a_c = y_c broadcast from its lane, then y_c' -= a_c L[c][c'] for c' < c. The solved a
+// are written to A and, when a trailing update follows (slices != null), cut into the
+// digit slices of the update's left operand like k_oz_split.
+__global__ void __launch_bounds__(256)
+k_oz_bsolve_block(double* __restrict__ Y, double* __restrict__ A, const double* __restrict__ H, int R,
+                  int n, int j0, int bw, uint16_t* __restrict__ slices, int rows_alloc,
+                  int* __restrict__ exps) {
+    extern __shared__ double Ls[];  // [bw][KP]
+    for (int e = threadIdx.x; e < bw * KP; e += blockDim.x) {
+        const int c = e / KP, cc = e % KP;
+        Ls[e] = (cc < c) ? H[(size_t)(j0 + c) * R + j0 + cc] : 0.0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= n) return;
+    double y[KP / 32];
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) {
+        const int col = lane + 32 * q;
+        y[q] = col < bw ? Y[(size_t)i * R + j0 + col] : 0.0;
+    }
+    for (int c = bw - 1; c >= 0; --c) {
+        const int qc = c >> 5;
+        const double yc = qc == 0 ? y[0] : qc == 1 ? y[1] : qc == 2 ? y[2] : y[3];
+        const double a = __shfl_sync(0xffffffffu, yc, c & 31);
+        const double* lrow = Ls + (size_t)c * KP;
+#pragma unroll
+        for (int q = 0; q < KP / 32; ++q) {
+            const int col = lane + 32 * q;
+            if (col < c) y[q] = fma(-a, lrow[col], y[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) {
+        const int col = lane + 32 * q;
+        if (col < bw) A[(size_t)i * R + j0 + col] = y[q];
+    }
+    if (!slices) return;
+    int emax = -2000;
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) emax = max(emax, exp_of(lane + 32 * q < bw ? y[q] : 0.0));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    const int erow = emax == -2000 ? 0 : emax;
+#pragma unroll
+    for (int q = 0; q < KP / 32; ++q) {
+        const int k = lane + 32 * q;
+        int d[S_];
+        digits_of(k < bw ? y[q] : 0.0, erow, d);
+#pragma unroll
+        for (int a = 0; a < S_; ++a) slices[((size_t)a * rows_alloc + i) * KP + k] = bf16_int(d[a]);
+    }
+    if (lane == 0) exps[i] = erow;
+}
+
 struct UpdArgs {
     double* C;     // C[i][j] at C[i * ldc + j]
     int ldc;
@@ -194,7 +295,7 @@ struct UpdArgs {
     int tiles_m;   // tiles along mA
     int tiles_n;   // tiles along mB
     int lower;     // 1: rows i < mB only on and below the diagonal (LDL^T trailing block)
-    double sign;   // C (+)= sign * E o (A B^T)
+    double sign;   // C (+)= sign * E o (A B^T); +1 or -1
     int accumulate;  // 0: C is overwritten
     const double* E;  // optional Hadamard factor of the product, indexed like C
 };
@@ -324,8 +425,9 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             ++i;
         }
     } else if (warp >= 2) {
-        // ---- epilogue: a lane quarter q and 16 columns h of each tile ----
-        const int q = warp & 3, h = (warp - 2) >> 2;
+        // ---- epilogue: a lane quarter q and 8 columns h of each tile ----
+        const int q = warp & 3, h = (warp - 2) >> 2;  // h = 0..3
+        const long long sign_bit = args.sign < 0.0 ? (long long)0x8000000000000000ULL : 0LL;
         int i = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int m0, n0;
@@ -337,28 +439,28 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             const bool rowok = row < args.mA;
             const int ea = rowok ? args.eA[row] : 0;
             double* crow = args.C + (size_t)row * args.ldc;
-            const uint32_t tbase = tmem + (uint32_t)(set * ACC_SET + 16 * h) + ((uint32_t)(32 * q) << 16);
-#pragma unroll 1
-            for (int half = 0; half < 2 && ok; ++half) {
+            const uint32_t tbase = tmem + (uint32_t)(set * ACC_SET + 8 * h) + ((uint32_t)(32 * q) << 16);
+            {
                 uint32_t r[S][8];
 #pragma unroll
-                for (int g = 0; g < S; ++g) tmem_ld8_nowait(tbase + (uint32_t)(g * BN + 8 * half), r[g]);
+                for (int g = 0; g < S; ++g) tmem_ld8_nowait(tbase + (uint32_t)(g * BN), r[g]);
                 // the row's 8 outputs and the column exponents are fetched while the
                 // tensor-memory loads are in flight
                 double cv[8];
                 int eb[8];
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
-                    const int j = n0 + 16 * h + 8 * half + jj;
-                    cv[jj] = (rowok && j < args.mB && args.accumulate) ? crow[j] : 0.0;
+                    const int j = n0 + 8 * h + jj;
+                    cv[jj] = (ok && rowok && j < args.mB && args.accumulate) ? crow[j] : 0.0;
                     eb[jj] = j < args.mB ? __ldg(args.eB + j) : 0;
                 }
                 tmem_ld_wait(r);
-                if (!rowok) continue;
+                if (!rowok || !ok) goto done_tile;
+                // the 8 elements side by side, without branches, so that their conversions and
+                // FP64 operations overlap; only the stores are masked
+                double tv[8], sc[8];
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
-                    const int j = n0 + 16 * h + 8 * half + jj;
-                    if (j >= args.mB || (args.lower && row < args.mB && j > row)) continue;
                     long long acc[S];
 #pragma unroll
                     for (int g = 0; g < S; ++g) acc[g] = (long long)__float2int_rn(__uint_as_float(r[g][jj]));
@@ -366,14 +468,22 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                     const long long hi = acc[0] * 65536 + acc[1] * 256 + acc[2];
                     const long long lo = acc[3] * 16777216 + acc[4] * 65536 + acc[5] * 256 + acc[6];
                     const int sh = (hi >= (1LL << 29) || hi <= -(1LL << 29)) ? 8 : 0;
-                    const long long vs = hi * (1LL << (32 - sh)) + (lo >> sh);
-                    // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48); below 2^-1022 it is dropped
-                    const int e = ea + eb[jj] - 62 + sh;
-                    const double tv = (double)vs * (e < -1022 ? 0.0 : pow2(min(e, 1023)));  // exact scaling
-                    const double f = args.E ? args.sign * args.E[(size_t)row * args.ldc + j] : args.sign;
-                    crow[j] = args.accumulate ? fma(f, tv, cv[jj]) : f * tv;
+                    tv[jj] = (double)(hi * (1LL << (32 - sh)) + (lo >> sh));
+                    // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48), times the sign, as an exact
+                    // power of two built from its bits (below 2^-1022 the term is dropped)
+                    const int e = min(ea + eb[jj] - 62 + sh, 1023);
+                    const long long bits = e < -1022 ? 0LL : ((long long)(e + 1023) << 52) | sign_bit;
+                    sc[jj] = __longlong_as_double(bits);
+                }
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = n0 + 8 * h + jj;
+                    const double f = args.E ? args.E[(size_t)row * args.ldc + min(j, args.mB - 1)] * sc[jj] : sc[jj];
+                    const double out = args.accumulate ? fma(f, tv[jj], cv[jj]) : f * tv[jj];
+                    if (j < args.mB && !(args.lower && row < args.mB && j > row)) crow[j] = out;
                 }
             }
+        done_tile:
             // every TMEM read of this tile has completed (tcgen05.wait::ld)
             tc_fence_before();
             __syncwarp();
@@ -410,7 +520,9 @@ bool oz_init() {
             return;
         g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
         if (cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-            cudaSuccess)
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_oz_bsolve_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 KP * KP * (int)sizeof(double)) != cudaSuccess)
             return;
         g_ready = true;
     });
@@ -428,11 +540,10 @@ bool slice_map(CUtensorMap* m, const uint16_t* base, int rows, int rows_alloc, i
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-void split(cudaStream_t st, const double* src, int ld, int rows, int K, const double* diag, int ldd,
-           int which, uint16_t* out, int rows_alloc, int* exps) {
+void split(cudaStream_t st, const double* src, int ld, int rows, int K, uint16_t* out, int rows_alloc,
+           int* exps) {
     if (rows <= 0) return;
-    k_oz_split<<<cdiv((long)rows * 32, 256), 256, 0, st>>>(src, ld, rows, K, diag, ldd, which, out,
-                                                           rows_alloc, exps);
+    k_oz_split<<<cdiv((long)rows * 32, 256), 256, 0, st>>>(src, ld, rows, K, out, rows_alloc, exps);
     count_launch();
 }
 
@@ -501,8 +612,9 @@ cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, doubl
         const double* diag = Haug + (size_t)j0 * R + j0;
         {
             ProfScope prof(st, KC_OZ, (double)mB * (mB + 1) * bw + 2.0 * (mA - mB) * mB * bw);
-            split(st, below, R, mA, bw, diag, R, 1, ws.sA, ws.rowsA, ws.eA);
-            split(st, below, R, mB, bw, diag, R, 2, ws.sB, ws.rowsB, ws.eB);
+            k_oz_split_ldl<<<cdiv((long)mA * 32, 256), 256, 0, st>>>(below, R, mA, mB, bw, diag, R, ws.sA,
+                                                                   ws.rowsA, ws.eA, ws.sB, ws.rowsB, ws.eB);
+            count_launch();
             e = update(st, mA, mB, Haug + (size_t)j1 * R + j1, R, ws, true, -1.0);
         }
         if (e != cudaSuccess) return e;
@@ -516,8 +628,8 @@ cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int l
     if (M > ws.rowsA || N > ws.rowsB) return cudaErrorInvalidValue;
     for (int k0 = 0; k0 < K; k0 += KP) {
         const int kb = std::min(KP, K - k0);
-        split(st, A + k0, lda, M, kb, nullptr, 0, 0, ws.sA, ws.rowsA, ws.eA);
-        split(st, B + k0, ldb, N, kb, nullptr, 0, 0, ws.sB, ws.rowsB, ws.eB);
+        split(st, A + k0, lda, M, kb, ws.sA, ws.rowsA, ws.eA);
+        split(st, B + k0, ldb, N, kb, ws.sB, ws.rowsB, ws.eB);
         const cudaError_t e = update(st, M, N, C, ldc, ws, lower, sign);
         if (e != cudaSuccess) return e;
     }
@@ -538,7 +650,7 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
             k_oz_split_t<<<cdiv(M, 32), 256, 0, st>>>(A, nullptr, lda, M, k0, kb, ws.sA, ws.rowsA, ws.eA);
             count_launch();
         } else {
-            split(st, A + k0, lda, M, kb, nullptr, 0, 0, ws.sA, ws.rowsA, ws.eA);
+            split(st, A + k0, lda, M, kb, ws.sA, ws.rowsA, ws.eA);
         }
         k_oz_split_t<<<cdiv(N, 32), 256, 0, st>>>(B, B2, ldb, N, k0, kb, ws.sB, ws.rowsB, ws.eB);
         count_launch();
@@ -549,6 +661,32 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
         const int nt = cdiv(N, 32);
         k_oz_mirror<<<dim3(nt, nt), 256, 0, st>>>(N, C, ldc);
         count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t bsolve_oz(cudaStream_t st, int R, int n, double* Y, double* A, const double* H,
+                      const OzWs& ws) {
+    if (n <= 0) return cudaSuccess;
+    if (n > ws.rowsA || R > ws.rowsB + KP) return cudaErrorInvalidValue;
+    const int nb = cdiv(R, KP);
+    for (int J = nb - 1; J >= 0; --J) {
+        const int j0 = J * KP, bw = std::min(KP, R - j0);
+        {
+            ProfScope prof(st, KC_BSOLVE, (double)n * bw * bw);
+            k_oz_bsolve_block<<<cdiv(n, 8), 256, (size_t)bw * KP * sizeof(double), st>>>(
+                Y, A, H, R, n, j0, bw, J > 0 ? ws.sA : nullptr, ws.rowsA, ws.eA);
+            count_launch();
+        }
+        if (J == 0) break;
+        // y[:, 0:j0] -= a_J L[j0:j0+bw, 0:j0]: right-operand rows c' < j0 are column c' of
+        // L's block row J
+        ProfScope prof(st, KC_OZ, 2.0 * n * (double)j0 * bw);
+        k_oz_split_t<<<cdiv(j0, 32), 256, 0, st>>>(H + (size_t)j0 * R, nullptr, R, j0, 0, bw, ws.sB,
+                                                     ws.rowsB, ws.eB);
+        count_launch();
+        const cudaError_t e = update(st, n, j0, Y, R, ws, false, -1.0);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -1447,9 +1447,7 @@ thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M,
         else
             CK(ldl_flow(st, R, n, Haug, P, dinv, sc, 0, fsync));
     }
-    if (emu && n >= kOzBsolveMinRows) {
-        CK(bsolve_oz(st, R, n, Haug + RR, A, Haug, oz));
-    } else {
+    {
         ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
         CK(bsolve_slices(st, R, n, Haug + RR, A, Haug, bsync));
     }

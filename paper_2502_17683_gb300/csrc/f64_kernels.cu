@@ -594,11 +594,6 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
         }
     }
     if (n <= 0) return;
-    if (oz && flow_sync && n >= kOzBsolveMinRows && R > kOzPanel) {
-        // blocks of 128 columns, the updates between them on the tensor cores
-        bsolve_oz(st, R, n, Haug + (size_t)R * R, A, Haug, *oz);
-        return;
-    }
     ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
     bsolve_slices(st, R, n, Haug + (size_t)R * R, A, Haug, bs_sync);
 }

@@ -27,9 +27,6 @@ namespace thc {
 
 constexpr int kOzSlices = 7;    // S: integer digits per value
 constexpr int kOzPanel = 128;   // K of one emulated product (panel width of the LDL^T)
-// Backward solves with at least this many right-hand sides run blocked with emulated
-// updates (bsolve_oz); with fewer the one-launch FP64 column-slice solve is faster.
-constexpr int kOzBsolveMinRows = 128;
 
 // Device workspace of the two-level LDL^T (slices of the two operands of one trailing
 // update and their row exponents).
@@ -76,13 +73,6 @@ cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int l
 cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, int lda,
                      const double* B, const double* B2, int ldb, double* C, int ldc, const double* E,
                      bool symm, const OzWs& ws);
-
-// Backward solve A L = Y of the normal equations (L unit lower in the strictly-lower part of
-// H, R x R, ld R; Y and A n x R, ld R; Y is consumed) in 128-column blocks from the last:
-// each block's substitution in FP64 (k_oz_bsolve_block), then the emulated update of the
-// columns to its left. ws must hold n (rowsA) and R - 128 (rowsB) rows.
-cudaError_t bsolve_oz(cudaStream_t st, int R, int n, double* Y, double* A, const double* H,
-                      const OzWs& ws);
 
 // Device error word of the emulated-product kernel (bounded waits that gave up); read and
 // clear.

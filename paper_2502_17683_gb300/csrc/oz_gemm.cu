@@ -228,64 +228,6 @@ __global__ void k_oz_mirror(int n, double* __restrict__ C, int ldc) {
     }
 }
 
-// One 128-column block J of the backward solve A L = Y (L unit lower, strictly-lower part
-// of H): rows i < n, one warp per row, lane l holding columns j0 + l + 32 q. The block's L
-// (bw x bw) is staged in shared memory; columns are solved from the last to the first,
-// a_c = y_c broadcast from its lane, then y_c' -= a_c L[c][c'] for c' < c. The solved a
-// are written to A and, when a trailing update follows (slices != null), cut into the
-// digit slices of the update's left operand like k_oz_split.
-__global__ void __launch_bounds__(256)
-k_oz_bsolve_block(double* __restrict__ Y, double* __restrict__ A, const double* __restrict__ H, int R,
-                  int n, int j0, int bw, uint16_t* __restrict__ slices, int rows_alloc,
-                  int* __restrict__ exps) {
-    extern __shared__ double Ls[];  // [bw][KP]
-    for (int e = threadIdx.x; e < bw * KP; e += blockDim.x) {
-        const int c = e / KP, cc = e % KP;
-        Ls[e] = (cc < c) ? H[(size_t)(j0 + c) * R + j0 + cc] : 0.0;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, i = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (i >= n) return;
-    double y[KP / 32];
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) {
-        const int col = lane + 32 * q;
-        y[q] = col < bw ? Y[(size_t)i * R + j0 + col] : 0.0;
-    }
-    for (int c = bw - 1; c >= 0; --c) {
-        const int qc = c >> 5;
-        const double yc = qc == 0 ? y[0] : qc == 1 ? y[1] : qc == 2 ? y[2] : y[3];
-        const double a = __shfl_sync(0xffffffffu, yc, c & 31);
-        const double* lrow = Ls + (size_t)c * KP;
-#pragma unroll
-        for (int q = 0; q < KP / 32; ++q) {
-            const int col = lane + 32 * q;
-            if (col < c) y[q] = fma(-a, lrow[col], y[q]);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) {
-        const int col = lane + 32 * q;
-        if (col < bw) A[(size_t)i * R + j0 + col] = y[q];
-    }
-    if (!slices) return;
-    int emax = -2000;
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) emax = max(emax, exp_of(lane + 32 * q < bw ? y[q] : 0.0));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    const int erow = emax == -2000 ? 0 : emax;
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) {
-        const int k = lane + 32 * q;
-        int d[S_];
-        digits_of(k < bw ? y[q] : 0.0, erow, d);
-#pragma unroll
-        for (int a = 0; a < S_; ++a) slices[((size_t)a * rows_alloc + i) * KP + k] = bf16_int(d[a]);
-    }
-    if (lane == 0) exps[i] = erow;
-}
-
 struct UpdArgs {
     double* C;     // C[i][j] at C[i * ldc + j]
     int ldc;
@@ -520,9 +462,7 @@ bool oz_init() {
             return;
         g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
         if (cudaFuncSetAttribute(k_oz_update, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_oz_bsolve_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 KP * KP * (int)sizeof(double)) != cudaSuccess)
+            cudaSuccess)
             return;
         g_ready = true;
     });
@@ -661,32 +601,6 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
         const int nt = cdiv(N, 32);
         k_oz_mirror<<<dim3(nt, nt), 256, 0, st>>>(N, C, ldc);
         count_launch();
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t bsolve_oz(cudaStream_t st, int R, int n, double* Y, double* A, const double* H,
-                      const OzWs& ws) {
-    if (n <= 0) return cudaSuccess;
-    if (n > ws.rowsA || R > ws.rowsB + KP) return cudaErrorInvalidValue;
-    const int nb = cdiv(R, KP);
-    for (int J = nb - 1; J >= 0; --J) {
-        const int j0 = J * KP, bw = std::min(KP, R - j0);
-        {
-            ProfScope prof(st, KC_BSOLVE, (double)n * bw * bw);
-            k_oz_bsolve_block<<<cdiv(n, 8), 256, (size_t)bw * KP * sizeof(double), st>>>(
-                Y, A, H, R, n, j0, bw, J > 0 ? ws.sA : nullptr, ws.rowsA, ws.eA);
-            count_launch();
-        }
-        if (J == 0) break;
-        // y[:, 0:j0] -= a_J L[j0:j0+bw, 0:j0]: right-operand rows c' < j0 are column c' of
-        // L's block row J
-        ProfScope prof(st, KC_OZ, 2.0 * n * (double)j0 * bw);
-        k_oz_split_t<<<cdiv(j0, 32), 256, 0, st>>>(H + (size_t)j0 * R, nullptr, R, j0, 0, bw, ws.sB,
-                                                     ws.rowsB, ws.eB);
-        count_launch();
-        const cudaError_t e = update(st, n, j0, Y, R, ws, false, -1.0);
-        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

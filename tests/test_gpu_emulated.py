@@ -1,7 +1,6 @@
 """The FP64-accurate product on the BF16 tensor cores (thc_cpd_emulated_gemm: exact integer
 digit slices, exact tensor-core digit products, exact 64-bit recombination, one rounding)
-and the normal-equation solve whose trailing updates run on it (THC_CPD_LDL_EMULATED; with
-128 or more right-hand sides the backward solve too runs in blocks with emulated updates),
+and the normal-equation solve whose trailing updates run on it (THC_CPD_LDL_EMULATED),
 against FP64 references.
 
 Bounds. Each row of A and of B keeps its digits down to 2^-55 of its largest entry, so the

@@ -487,14 +487,18 @@ void split(cudaStream_t st, const double* src, int ld, int rows, int K, uint16_t
     count_launch();
 }
 
+// same_ab: the left operand is the right one (a Gram A^T A): its slices and exponents are
+// read from the right operand's buffers.
 cudaError_t update(cudaStream_t st, int mA, int mB, double* C, int ldc, const OzWs& ws, bool lower,
-                   double sign, bool accumulate = true, const double* E = nullptr) {
+                   double sign, bool accumulate = true, const double* E = nullptr, bool same_ab = false) {
     if (mA <= 0 || mB <= 0) return cudaSuccess;
     CUtensorMap ma, mb;
-    if (!slice_map(&ma, ws.sA, mA, ws.rowsA, BM) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN))
+    const uint16_t* sa = same_ab ? ws.sB : ws.sA;
+    const int ra = same_ab ? ws.rowsB : ws.rowsA;
+    if (!slice_map(&ma, sa, mA, ra, BM) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN))
         return cudaErrorInvalidValue;
-    UpdArgs a{C, ldc, mA, mB, ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0, sign,
-              accumulate ? 1 : 0, E};
+    UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0,
+              sign, accumulate ? 1 : 0, E};
     // persistent: one CTA per SM, at most one per active tile
     long active = 0;
     for (int tm = 0; tm < a.tiles_m; ++tm) {
@@ -584,9 +588,13 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
     if (M > ws.rowsA || N > ws.rowsB || (symm && M != N)) return cudaErrorInvalidValue;
     if (K <= 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * N, M, st);
     ProfScope prof(st, KC_OZ, (symm ? 1.0 : 2.0) * M * (double)N * K);
+    // A^T A (a Gram): one operand split serves both sides
+    const bool same_ab = trans_a && A == B && !B2 && lda == ldb && M == N;
     for (int k0 = 0; k0 < K; k0 += KP) {
         const int kb = std::min(KP, K - k0);
-        if (trans_a) {
+        if (same_ab) {
+            // nothing: the left operand is read from the right operand's slices
+        } else if (trans_a) {
             k_oz_split_t<<<cdiv(M, 32), 256, 0, st>>>(A, nullptr, lda, M, k0, kb, ws.sA, ws.rowsA, ws.eA);
             count_launch();
         } else {
@@ -594,7 +602,7 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
         }
         k_oz_split_t<<<cdiv(N, 32), 256, 0, st>>>(B, B2, ldb, N, k0, kb, ws.sB, ws.rowsB, ws.eB);
         count_launch();
-        const cudaError_t e = update(st, M, N, C, ldc, ws, symm, 1.0, k0 > 0, E);
+        const cudaError_t e = update(st, M, N, C, ldc, ws, symm, 1.0, k0 > 0, E, same_ab);
         if (e != cudaSuccess) return e;
     }
     if (symm && N > 1) {

@@ -8,4 +8,6 @@ thc_inputs/ serve both).
 Modules:
   thc_cpd  - explicit tensors, matrix-free MTTKRP, factor-form loss, CP-ALS.
   mlp      - FP64 forward/backward of the extrapolation MLP.
+  exchange - the CPD+THC LT-MP2 exchange energy (single, double, robust).
+  corefit  - the THC core least-squares fit f(Z) from a density-fitting tensor.
 """

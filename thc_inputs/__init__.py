@@ -156,6 +156,27 @@ def make_lt(o: int, v: int, n_alpha: int = 12, seed: int = 0):
     return eps_occ, eps_vir, 2.0 * s_pts, w
 
 
+def make_df(o: int, v: int, Rt: int, naux: int, seed: int = 0, noise: float = 1e-2,
+            decay: float | None = None):
+    """A synthetic density-fitting tensor B (naux x o x v) and THC grid factors (Xo, Xv) for it,
+    built the way the paper builds its THC factors from the DF tensor's order-3 CPD (Sec. 3):
+      Xo, Xv from make_thc (the same draws, so the same grid factors as make_problem),
+      C[X,P] = N(0,1) / sqrt(Rt),
+      B[X,i,a] = sum_P C[X,P] Xo[i,P] Xv[a,P] + noise * rms(that sum) * N(0,1),
+    i.e. an order-3 CPD of rank Rt plus a relative Gaussian perturbation, so that the
+    (o,v,o,v) DF block is close to, but not exactly, a THC block on these factors.
+    Returns (Xo, Xv, B). naux is the auxiliary-basis size (3-4 x (o + v) is typical of DF
+    bases). The CPD assembly is input construction (np.einsum); it is none of the
+    core fit's or of DF-driven CP-ALS's arithmetic."""
+    Xo, Xv, _ = make_thc(o, v, Rt, seed, decay)
+    rng = np.random.default_rng([seed, 0xDF])
+    C = rng.standard_normal((naux, Rt)) / math.sqrt(Rt)
+    B = np.einsum("xp,ip,ap->xia", C, Xo, Xv, optimize=True)
+    rms = float(np.sqrt(np.mean(B * B))) if B.size else 0.0
+    B = B + noise * rms * rng.standard_normal(B.shape)
+    return Xo, Xv, np.ascontiguousarray(B)
+
+
 def round_up(x: int, m: int) -> int:
     return ((x + m - 1) // m) * m
 

@@ -10,4 +10,5 @@ Modules:
   mlp      - FP64 forward/backward of the extrapolation MLP.
   exchange - the CPD+THC LT-MP2 exchange energy (single, double, robust).
   corefit  - the THC core least-squares fit f(Z) from a density-fitting tensor.
+  df_cpd   - DF-driven CP-ALS (the prior-work O(N^3 R) MTTKRP from the DF tensor).
 """

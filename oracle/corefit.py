@@ -52,8 +52,9 @@ def core_fit_explicit(Xo, Xv, B):
 def core_normal_terms(Xo, Xv, B):
     """(S, E): S = (Xo^T Xo) o (Xv^T Xv) (Rt x Rt), E[X,P] = sum_ia B[X,i,a] Xo[i,P] Xv[a,P]."""
     S = (Xo.T @ Xo) * (Xv.T @ Xv)
-    T = np.einsum("xia,ap->xip", B, Xv, optimize=False)   # contract the virtual index
-    E = np.einsum("xip,ip->xp", T, Xo, optimize=False)    # then the occupied one
+    naux, o, v = B.shape
+    T = (B.reshape(naux * o, v) @ Xv).reshape(naux, o, -1)   # contract the virtual index
+    E = np.einsum("xip,ip->xp", T, Xo, optimize=False)       # then the occupied one
     return S, E
 
 

@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--learned-report", action="store_true",
                     help="o=30 v=150 R_thc=720 R_cp=1080, split precision: sweeps and wall-time "
                          "to a 1e-6 fit change, plain vs learned extrapolation")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="run one step (--sweeps sweeps of --config) untimed and exit: the "
+                         "command the ncu captures under profiles/ run")
     ap.add_argument("--batched", action="store_true",
                     help="64 uneven problems (o in [4,40], v=5o, R_thc=4(o+v), R_cp=6(o+v) "
                          "rounded up to 16), 40 sweeps each: batched graph vs one by one")
@@ -108,13 +111,19 @@ def fp64_peaks(dev, sm_max_mhz):
             "derived_tflops": nsm * 2 * 2 * mhz * 1e6 / 1e12, "sm_max_mhz": mhz}
 
 
-# DRAM bytes per launch of the dataflow LDL^T kernel, from one ncu capture of one sweep of
-# the named workload (the four modes' launches averaged; ncu starts every launch from a
-# flushed cache, so this is the cold-cache figure), and the SHA-256 of the kernel's sources
-# (concatenated in this order) it was taken on: reported only while they are unchanged.
+# DRAM bytes per launch of k_ldl_flow (one launch per solve on the dataflow path, one per
+# 128-column panel on the emulated path), keyed by (workload, path), from one ncu capture of
+# one sweep of that workload (all of the sweep's launches averaged; ncu starts every launch
+# from a flushed cache, so this is the cold-cache figure), and the SHA-256 of the kernel's
+# sources (concatenated in this order) it was taken on: reported only while they are
+# unchanged.
 LDL_SOURCES = [os.path.join("paper_2502_17683_gb300", "csrc", f)
                for f in ("ldl_flow.cu", "ldl_common.cuh", "common.cuh")]
-LDL_TRAFFIC = {}
+LDL_TRAFFIC = {
+    # 60 panel launches of sweep 1 (profiles/ldl_flow_panels_o50_v250_Rt1200_R1800_emulated.md)
+    ("c3", "emulated"): {"bytes_per_launch": 1177062,
+                         "sha256": "62e218bd349b094604c55c5e762137d4d9375f1c6e11d99a4d1cb5b4fa2d9da8"},
+}
 
 
 def ldl_sources_sha256():
@@ -126,8 +135,8 @@ def ldl_sources_sha256():
     return h.hexdigest()
 
 
-def ldl_traffic(config):
-    rec = LDL_TRAFFIC.get(config)
+def ldl_traffic(config, path):
+    rec = LDL_TRAFFIC.get((config, path))
     if not rec:
         return None
     try:
@@ -429,6 +438,12 @@ def main():
         for a, a0 in zip(A, A0):
             a.copy_(a0)
 
+    if args.profile_run:
+        out = step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": WORKLOAD, "precision": precision, "fit": out["fit"]}))
+        return
+
     for _ in range(args.warmup):
         reset()
         out = step()
@@ -586,8 +601,8 @@ def main():
         note = (f"measured FP64 FMA rate (library probe kernel); cuBLAS DGEMM measures "
                 f"{f64pk['dgemm_tflops']:.3f}, the unit counts give {f64pk['nsm']} SMs x 2 FMA/clk "
                 f"x 2 flop x {f64pk['sm_max_mhz']:.0f} MHz = {f64pk['derived_tflops']:.3f}")
-        if dom == "cholesky" and ldl_path == "dataflow":
-            traffic = ldl_traffic(args.config)  # the capture of this workload, if current
+        if dom == "cholesky":
+            traffic = ldl_traffic(args.config, ldl_path)  # the capture of this workload, if current
     roofline = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
                 "traffic": traffic, "peak_source": note,

@@ -279,6 +279,38 @@ thc_cpd_status thc_cpd_exchange(int o, int v, int Rt, int R, int nalpha, const d
                                 double* e_single, double* e_double, double* e_robust,
                                 const thc_cpd_opts* opts);
 
+/* THC core least-squares fit (Sec. 3, Computational Details): the core Z (R_thc x R_thc)
+ * minimising f(Z) = 1/2 || G_DF - G_THC(Z) ||^2, where G_DF[i,a,j,b] = sum_X B[X,i,a] B[X,j,b]
+ * is the (o,v,o,v) block of density-fitted integrals and G_THC(Z) the THC block of Eq. THC
+ * on the given grid factors. Solves the normal equations S Z S = E^T E, S = (Xo^T Xo) o
+ * (Xv^T Xv), E[X,P] = sum_ia B[X,i,a] Xo[i,P] Xv[a,P], as Z = F^T F with F = E S^-1 (LDL^T of
+ * S, pseudo-inverse of S when a pivot fails: *used_pinv = 1). The result is symmetric.
+ * Xo (o x Rt), Xv (v x Rt), B (naux x o x v, row-major), Z (Rt x Rt, written): device FP64.
+ * loss: NULL, or host double receiving ||G_DF - G_THC(Z)||^2 (no 1/2) in factor form.
+ * 1 <= R_thc <= 2048; o * v, naux * o, naux * R_thc and naux^2 below 2^31. The GEMMs run on the
+ * FP64 pipes, or with opts->ldl = THC_CPD_LDL_EMULATED as the FP64-accurate emulated products
+ * of the tensor cores (the solve then uses the emulated two-level LDL^T as well).
+ * Allocates its workspace (about 256 MiB plus 2 naux R_thc doubles, plus naux o v and naux^2
+ * doubles with loss) with cudaMallocAsync on opts->stream. Synchronises. */
+thc_cpd_status thc_cpd_core_fit(int o, int v, int Rt, int naux, const double* Xo, const double* Xv,
+                                const double* B, double* Z, double* loss, int* used_pinv,
+                                const thc_cpd_opts* opts);
+
+/* DF-driven CP-ALS (Sec. 2.1, Eq. df_loss), the prior-work variant the THC-driven method
+ * replaces: CP-ALS of G_DF[i,a,j,b] = sum_X B[X,i,a] B[X,j,b] with every MTTKRP formed from
+ * the order-3 DF tensor B (naux x o x v, device, row-major) at O(naux o v R) per mode (four
+ * GEMMs of 2 naux o v R flop per sweep), the same normal-equation solve, normalisation, loss
+ * and stopping rule as thc_cpd_als: A[4] (o x R, v x R, o x R, v x R) start factors in, final
+ * unit-column factors out; lam (R) out; sweeps_done and fit_host (host) out, each may be NULL.
+ * opts->precision must be THC_CPD_FP64; opts->ldl = THC_CPD_LDL_EMULATED runs the GEMMs and the
+ * solve on the emulated FP64 tensor-core path. opts->history: NULL or 2 * max_sweeps host
+ * doubles (loss, fit per sweep). opts->flags_out bit 0: a pseudo-inverse solve was used.
+ * Workspace: about (2 o v + max(o, v) R + 3 R) naux + naux^2 + 5 R^2 doubles (cudaMallocAsync).
+ * 1 <= R <= 2048, 1 <= o, v <= 4096. Synchronises once per sweep. */
+thc_cpd_status thc_cpd_df_als(int o, int v, int naux, int R, const double* B, double* const A[4],
+                              double* lam, int max_sweeps, double tol, int* sweeps_done,
+                              double* fit_host, thc_cpd_opts* opts);
+
 /* Measured FP64 FMA throughput of the device (TFLOP/s, 2 flop per FMA) from a probe kernel
  * of independent FMA chains on every SM (64 warps per SM, best of three timed launches):
  * the roofline denominator of the FP64 kernels (Gram, solve, loss). Synchronises. */

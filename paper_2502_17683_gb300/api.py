@@ -18,7 +18,7 @@ __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc",
            "thc_cpd_als_batched", "thc_cpd_mlp_init", "thc_cpd_mlp_forward", "thc_cpd_mlp_grad",
            "thc_cpd_mlp_train", "thc_cpd_als_trajectory", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam", "thc_cpd_fp64_fma_rate",
-           "thc_cpd_emulated_gemm", "thc_cpd_exchange", "Opts"]
+           "thc_cpd_emulated_gemm", "thc_cpd_exchange", "thc_cpd_core_fit", "thc_cpd_df_als", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -89,6 +89,24 @@ def thc_cpd_exchange(Xo, Xv, Z, A, lam, Lam, Gam, emulated=False, stream=None):
                                   _dev(Gam, "Gam", (na, v)), ctypes.byref(e1), ctypes.byref(e2),
                                   ctypes.byref(er), ctypes.byref(opts)))
     return e1.value, e2.value, er.value
+
+
+def thc_cpd_core_fit(Xo, Xv, B, Z=None, loss=False, emulated=False, stream=None):
+    """THC core least-squares fit: Z (R_thc x R_thc) from the grid factors Xo (o x R_thc),
+    Xv (v x R_thc) and the DF tensor B (naux x o x v). Returns (Z, loss or None, used_pinv);
+    emulated: FP64-accurate tensor-core products and the emulated two-level LDL^T."""
+    o, Rt = Xo.shape
+    v = Xv.shape[0]
+    naux = B.shape[0]
+    if Z is None:
+        Z = torch.empty(Rt, Rt, dtype=torch.float64, device=Xo.device)
+    opts = _opts("fp64", stream, ldl="emulated" if emulated else "auto")
+    lv, pinv = ctypes.c_double(), ctypes.c_int()
+    check(load().thc_cpd_core_fit(o, v, Rt, naux, _dev(Xo, "Xo", (o, Rt)), _dev(Xv, "Xv", (v, Rt)),
+                                  _dev(B, "B", (naux, o, v)), _dev(Z, "Z", (Rt, Rt)),
+                                  ctypes.byref(lv) if loss else None, ctypes.byref(pinv),
+                                  ctypes.byref(opts)))
+    return Z, (lv.value if loss else None), bool(pinv.value)
 
 
 def thc_cpd_emulated_gemm(A, B, C=None, stream=None):
@@ -218,6 +236,28 @@ def thc_cpd_als(Xo, Xv, Z, A, lam, max_sweeps: int, tol: float = 0.0, precision=
                              ctypes.byref(opts)))
     out = dict(sweeps=done.value, loss=loss.value, fit=fit.value, flags=opts.flags_out,
                accepted=opts.accepted_out)
+    if hist is not None:
+        h = list(hist)[: 2 * done.value]
+        out["losses"] = h[0::2]
+        out["fits"] = h[1::2]
+    return out
+
+
+def thc_cpd_df_als(B, A, lam, max_sweeps: int, tol: float = 0.0, emulated=False, history=False,
+                   stream=None):
+    """DF-driven CP-ALS of G_DF = sum_X B[X] (x) B[X] (B: naux x o x v); A (four factors) and lam
+    are updated in place. emulated: FP64-accurate tensor-core GEMMs and the emulated LDL^T."""
+    naux, o, v = B.shape
+    R = A[0].shape[1]
+    fit, done = ctypes.c_double(), ctypes.c_int()
+    hist = (ctypes.c_double * max(1, 2 * max_sweeps))() if history else None
+    opts = _opts("fp64", stream, 0,
+                 ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
+                 ldl="emulated" if emulated else "auto")
+    check(load().thc_cpd_df_als(o, v, naux, R, _dev(B, "B", (naux, o, v)), _ptr4(A, (o, v, o, v), R),
+                                _dev(lam, "lam", (R,)), int(max_sweeps), float(tol),
+                                ctypes.byref(done), ctypes.byref(fit), ctypes.byref(opts)))
+    out = dict(sweeps=done.value, fit=fit.value, flags=opts.flags_out)
     if hist is not None:
         h = list(hist)[: 2 * done.value]
         out["losses"] = h[0::2]

@@ -350,13 +350,16 @@ thc_cpd_status ctx_safe_buffers(Ctx& c) {
 }
 
 // ---- building blocks -----------------------------------------------------------------
+void gemm64(Ctx& c, bool trans_a, int M, int N, int K, const double* A, int lda, const double* B,
+            const double* B2, int ldb, double* C, int ldc, bool symm);
+
 void compute_normG2(Ctx& c) {
     const int o = c.s.o, v = c.s.v, Rt = c.s.Rt;
     // S = (Xo^T Xo) o (Xv^T Xv); U = S Z S; ||G||^2 = sum Z o U
     dgemm(c.st, true, Rt, Rt, o, c.X[0], Rt, c.X[0], nullptr, Rt, c.T, Rt, nullptr, true, c.part, c.part_cap);
     dgemm(c.st, true, Rt, Rt, v, c.X[1], Rt, c.X[1], nullptr, Rt, c.S, Rt, c.T, true, c.part, c.part_cap);
-    dgemm(c.st, false, Rt, Rt, Rt, c.S, Rt, c.Z, nullptr, Rt, c.T, Rt, nullptr, false, c.part, c.part_cap);
-    dgemm(c.st, false, Rt, Rt, Rt, c.T, Rt, c.S, nullptr, Rt, c.U, Rt, nullptr, false, c.part, c.part_cap);
+    gemm64(c, false, Rt, Rt, Rt, c.S, Rt, c.Z, nullptr, Rt, c.T, Rt, false);
+    gemm64(c, false, Rt, Rt, Rt, c.T, Rt, c.S, nullptr, Rt, c.U, Rt, false);
     sum_hadamard_normG2(c.st, (long)Rt * Rt, c.Z, c.U, c.red, c.sc);
 }
 
@@ -1385,23 +1388,14 @@ extern "C" thc_cpd_status thc_cpd_emulated_gemm(int M, int N, int K, const doubl
     return THC_CPD_OK;
 }
 
-thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M, double* A,
-                                 const short* tasks, int ntasks, int* used_pinv,
-                                 const thc_cpd_opts* opts) {
-    if (R < 1 || R > 2048 || n < 1 || n > 4096)
-        return set_err(THC_CPD_ERR_SHAPE, "need 1 <= R <= 2048 and 1 <= n <= 4096 (R=%d n=%d)", R, n);
-    if (!H || !M || !A) return set_err(THC_CPD_ERR_ARG, "H, M and A must be non-null");
-    if (tasks && ntasks < 0) return set_err(THC_CPD_ERR_ARG, "ntasks must be >= 0");
-    if (tasks) {
-        const int bad = flow_task_check(R, n, tasks, ntasks);
-        if (bad >= 0) return set_err(THC_CPD_ERR_ARG, "task %d has an out-of-range type or tile index", bad);
-    }
+namespace thc {
+
+int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, double* A,
+              const short* tasks, int ntasks, int* used_pinv, int ldl) {
     if (used_pinv) *used_pinv = 0;
     if (!flow_prepare(R, n)) return set_err(THC_CPD_ERR_UNSUPPORTED, "no dataflow schedule for R=%d n=%d", R, n);
-    set_wait_limit(opts);
-    cudaStream_t st = stream_of(opts);
     const size_t RR = (size_t)R * R, nR = (size_t)n * R;
-    const bool emu = use_emulated_ldl(opts ? opts->ldl : THC_CPD_LDL_AUTO, R, n) && !tasks &&
+    const bool emu = use_emulated_ldl(ldl, R, n) && !tasks &&
                      oz_prepare(R, n);
     size_t bytes = (emu ? oz_ws_bytes(R + n, R) : 0) + Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
                    Arena::need<double>(std::max(RR, nR)) + Arena::need<double>(R) +
@@ -1466,6 +1460,24 @@ thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M,
         if (used_pinv) *used_pinv = 1;
     }
     return THC_CPD_OK;
+}
+
+}  // namespace thc
+
+thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M, double* A,
+                                 const short* tasks, int ntasks, int* used_pinv,
+                                 const thc_cpd_opts* opts) {
+    if (R < 1 || R > 2048 || n < 1 || n > 4096)
+        return set_err(THC_CPD_ERR_SHAPE, "need 1 <= R <= 2048 and 1 <= n <= 4096 (R=%d n=%d)", R, n);
+    if (!H || !M || !A) return set_err(THC_CPD_ERR_ARG, "H, M and A must be non-null");
+    if (tasks && ntasks < 0) return set_err(THC_CPD_ERR_ARG, "ntasks must be >= 0");
+    if (tasks) {
+        const int bad = flow_task_check(R, n, tasks, ntasks);
+        if (bad >= 0) return set_err(THC_CPD_ERR_ARG, "task %d has an out-of-range type or tile index", bad);
+    }
+    set_wait_limit(opts);
+    return (thc_cpd_status)spd_solve(stream_of(opts), R, n, H, M, A, tasks, ntasks, used_pinv,
+                                     opts ? opts->ldl : THC_CPD_LDL_AUTO);
 }
 
 thc_cpd_status thc_cpd_als_batched(int nprob, thc_cpd_problem* probs, int max_sweeps,

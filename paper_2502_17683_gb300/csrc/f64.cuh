@@ -40,6 +40,15 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
                 int* bs_sync, const OzWs* oz = nullptr);
 
+// A = M H^-1 for H symmetric positive definite (R x R, lower triangle read) and M (n x R),
+// all device pointers, 1 <= R <= 2048, 1 <= n <= 4096: the solve of thc_cpd_ldl_solve (LDL^T
+// with the forward solve fused, dataflow or emulated two-level by `ldl` (thc_cpd_ldl values),
+// backward solve, pseudo-inverse when a pivot fails: *used_pinv = 1). tasks: null or a
+// caller-built dataflow task list (ntasks entries). Allocates its workspace on st and
+// synchronises st. Returns a thc_cpd_status; the message is set on failure.
+int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, double* A,
+              const short* tasks, int ntasks, int* used_pinv, int ldl);
+
 // Dataflow LDL^T (ldl_flow.cu): ints of progress state for R and n <= nmax; plan set-up
 // for (R, n) (false: too large or the task order failed its check; use the blocked path);
 // the launch; the error flag of bounded waits that gave up (read and cleared).
@@ -113,6 +122,9 @@ void trial_point(cudaStream_t st, int n, int R, const double* An, const double* 
 void lam_product(cudaStream_t st, int R, const double* const l[4], double* out);
 // the network's alpha for one 40-feature vector (device pointers)
 void mlp_forward1(cudaStream_t st, const float* P, const float* x, float* alpha);
+
+// out (cols x rows) = in (rows x cols)^T (32 x 32 tiles through shared memory)
+void transpose64(cudaStream_t st, int rows, int cols, const double* in, double* out);
 
 // fill lam with ones
 void fill(cudaStream_t st, double* p, long n, double v);

@@ -772,6 +772,28 @@ void sum_hadamard_normG2(cudaStream_t st, long n, const double* Z, const double*
     k_norm_final<<<1, RED_THREADS, 0, st>>>(red, RED_BLOCKS, sc);
 }
 
+// out (cols x rows) = in (rows x cols)^T through 32 x 32 shared-memory tiles
+__global__ void k_transpose(int rows, int cols, const double* __restrict__ in, double* __restrict__ out) {
+    __shared__ double t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + tx;
+        if (r < rows && c < cols) t[k][tx] = in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + tx;
+        if (r < rows && c < cols) out[(size_t)c * rows + r] = t[tx][k];
+    }
+}
+
+void transpose64(cudaStream_t st, int rows, int cols, const double* in, double* out) {
+    if (rows <= 0 || cols <= 0) return;
+    count_launch();
+    k_transpose<<<dim3(cdiv(cols, 32), cdiv(rows, 32)), 256, 0, st>>>(rows, cols, in, out);
+}
+
 __global__ void k_scalars_init(DevScalars* sc, double normG2) {
     sc->normG2 = normG2;
     sc->loss = nan("");

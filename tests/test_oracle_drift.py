@@ -35,6 +35,9 @@ def test_per_sweep_perturbation_growth_along_the_unconverged_trajectory():
     ref = _fits(p, 0.0, 50)
     d_bf16 = np.abs(_fits(p, 1.5e-5, 50) - ref)
     d_small = np.abs(_fits(p, 1e-6, 50) - ref)
+    for name, d in (("1.5e-5", d_bf16), ("1e-6", d_small)):  # the report's rows (pytest -s)
+        print(f"e {name}: " + " ".join(f"{d[s - 1]:.1e}" for s in (1, 2, 5, 10, 20, 30, 40, 50))
+              + f" max {d.max():.1e}")
     # first sweep: the perturbation enters the fit at second order (exact block minimiser)
     assert d_bf16[0] < 1e-6
     # along the trajectory ALS carries it forward without damping: the drift reaches

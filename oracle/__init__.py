@@ -11,4 +11,5 @@ Modules:
   exchange - the CPD+THC LT-MP2 exchange energy (single, double, robust).
   corefit  - the THC core least-squares fit f(Z) from a density-fitting tensor.
   df_cpd   - DF-driven CP-ALS (the prior-work O(N^3 R) MTTKRP from the DF tensor).
+  nd       - THC-driven CP-ALS of order-d THC-like tensors (two grid-index groups).
 """

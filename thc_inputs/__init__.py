@@ -177,6 +177,22 @@ def make_df(o: int, v: int, Rt: int, naux: int, seed: int = 0, noise: float = 1e
     return Xo, Xv, np.ascontiguousarray(B)
 
 
+def make_nd(dims, Rt: int, R: int, seed: int = 0, decay: float | None = None):
+    """Order-d THC-like inputs: grid factors X_k (dims[k] x Rt) and a core Z (Rt x Rt) by the
+    recipe of make_thc (one weight w_P per grid point shared by every X_k; Z = L diag(exp(-k/s))
+    L^T), and start factors A_k (dims[k] x R) N(0,1). Returns (X list, Z, A tuple)."""
+    rng = np.random.default_rng([seed, 0x4D])
+    s = Rt / 5.0 if decay is None else float(decay)
+    w = 10.0 ** rng.uniform(-2.0, 0.0, size=Rt)
+    scale = 1.0 / math.sqrt(Rt)
+    X = [rng.standard_normal((n, Rt)) * scale * w[None, :] for n in dims]
+    L = rng.standard_normal((Rt, Rt)) * scale
+    d = np.exp(-np.arange(Rt) / s)
+    Z = (L * d[None, :]) @ L.T
+    Z = 0.5 * (Z + Z.T)
+    return X, Z, make_factors(tuple(dims), R, seed)
+
+
 def round_up(x: int, m: int) -> int:
     return ((x + m - 1) // m) * m
 

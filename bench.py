@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--profile-run", action="store_true",
                     help="run one step (--sweeps sweeps of --config) untimed and exit: the "
                          "command the ncu captures under profiles/ run")
+    ap.add_argument("--rows-report", action="store_true",
+                    help="the rows beyond the ALS hot path at the bench sizes: exchange energy, "
+                         "THC core fit, DF- vs THC-driven ALS, order-6 ALS (GPU FP64 and emulated, "
+                         "each beside its oracle on the host cores)")
     ap.add_argument("--batched", action="store_true",
                     help="64 uneven problems (o in [4,40], v=5o, R_thc=4(o+v), R_cp=6(o+v) "
                          "rounded up to 16), 40 sweeps each: batched graph vs one by one")
@@ -347,6 +351,124 @@ def batched_report(args):
     return 0
 
 
+def rows_report(args):
+    """Exchange energy, THC core fit, DF-driven vs THC-driven ALS and order-6 ALS at the bench
+    sizes (o=50 v=250 R_thc=1200 R_cp=1800, naux=1200; order 6: (20,100) x 3, R_thc=480,
+    R_cp=720): GPU time per call (best of 3 after a warm-up; each call synchronises) with the
+    FP64 pipes and with the emulated tensor-core products, the algorithmic FP64 flop rate, and
+    the oracle's time on the host cores for one call (DF-driven and order-6 ALS: one sweep)."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17683_gb300 import api
+    from thc_inputs import make_df, make_factors, make_lt, make_nd, make_problem
+    from oracle import corefit as OC, df_cpd as OD, exchange as OX, nd as ON
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    probe = None
+    try:
+        probe = api.thc_cpd_fp64_fma_rate()
+    except Exception:
+        probe = None
+
+    def gpu_best(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    def cpu_once(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    def row(flops, t64, temu, tcpu, unit_note):
+        out = {"fp64_s": t64, "emulated_s": temu, "oracle_s": tcpu, "flop": flops,
+               "fp64_tflops": flops / t64 / 1e12, "emulated_tflops": flops / temu / 1e12,
+               "emulated_speedup": t64 / temu, "vs_oracle": tcpu / temu, "unit": unit_note}
+        if probe:
+            out["fp64_frac_of_fma_rate"] = out["fp64_tflops"] / probe
+        return out
+
+    rows = {}
+    o, v, Rt, R, naux = 50, 250, 1200, 1800, 1200
+    nmax = max(o, v)
+    # exchange energy (12 Laplace points) on the bench THC block and random CP factors
+    p = make_problem(o, v, Rt, R, seed=0, decay=240.0)
+    rng = np.random.default_rng(0)
+    lam = rng.uniform(0.5, 2.0, R)
+    eo, ev, tq, wq = make_lt(o, v, 12, 0)
+    Lam, Gam = OX.lt_factors(eo, ev, tq, wq)
+    dX = dict(Xo=d(p.Xo), Xv=d(p.Xv), Z=d(p.Z), A=[d(a) for a in p.A], lam=d(lam), Lam=d(Lam), Gam=d(Gam))
+    ex = lambda emu: api.thc_cpd_exchange(dX["Xo"], dX["Xv"], dX["Z"], dX["A"], dX["lam"], dX["Lam"],
+                                          dX["Gam"], emulated=emu)
+    fl = 12 * (4.0 * (o + v) * Rt * R + 2.0 * Rt * Rt * R + 4.0 * o * R * R + 2.0 * v * R * R)
+    tc = cpu_once(lambda: OX.exchange_robust(p.Xo, p.Xv, p.Z, p.A, lam, Lam[:1], Gam[:1])) * 12
+    rows["exchange_energy"] = row(fl, gpu_best(lambda: ex(False)), gpu_best(lambda: ex(True)), tc,
+                                  "one call, 12 quadrature points (oracle: 1 point x 12)")
+    # THC core fit from a DF tensor
+    Xo, Xv, B = make_df(o, v, Rt, naux, seed=1)
+    dC = dict(Xo=d(Xo), Xv=d(Xv), B=d(B))
+    cf = lambda emu: api.thc_cpd_core_fit(dC["Xo"], dC["Xv"], dC["B"], emulated=emu)
+    fl = 2.0 * naux * o * v * Rt + 2.0 * naux * o * Rt + (o + v) * Rt * Rt + Rt ** 3 / 3 + 3.0 * naux * Rt * Rt
+    tc = cpu_once(lambda: OC.core_fit(Xo, Xv, B))
+    rows["core_fit"] = row(fl, gpu_best(lambda: cf(False)), gpu_best(lambda: cf(True)), tc, "one fit")
+    # DF-driven vs THC-driven ALS, 3 sweeps from the same start
+    A0 = make_factors((o, v, o, v), R, 2)
+    dB = d(B)
+
+    def df_run(emu):
+        A = [d(a) for a in A0]
+        lamd = torch.ones(R, dtype=torch.float64, device="cuda")
+        api.thc_cpd_df_als(dB, A, lamd, 3, emulated=emu)
+    fl = 3 * (8.0 * naux * o * v * R + 4 * R ** 3 / 3 + 4.0 * (o + v) * R * R)
+    pc = make_df(20, 100, 480, 480, seed=1)[2]
+    Ac = make_factors((20, 100, 20, 100), 720, 2)
+    tc = cpu_once(lambda: OD.df_als(pc, Ac, 1))
+    rows["df_als"] = row(fl, gpu_best(lambda: df_run(False), 2), gpu_best(lambda: df_run(True), 2), tc,
+                         "3 sweeps at naux=1200 (oracle: 1 sweep at o=20 v=100 naux=480 R_cp=720)")
+    rows["df_als"]["sweeps_per_s_fp64"] = 3 / rows["df_als"]["fp64_s"]
+    rows["df_als"]["sweeps_per_s_emulated"] = 3 / rows["df_als"]["emulated_s"]
+    pt = make_problem(o, v, Rt, R, seed=0, decay=240.0)
+    dT = dict(Xo=d(pt.Xo), Xv=d(pt.Xv), Z=d(pt.Z))
+    thc = {}
+    for prec, ldl in (("fp64", "dataflow"), ("fp64", "emulated"), ("bf16x3", "emulated")):
+        def th():
+            A = [d(a) for a in A0]
+            lamd = torch.ones(R, dtype=torch.float64, device="cuda")
+            api.thc_cpd_als(dT["Xo"], dT["Xv"], dT["Z"], A, lamd, 3, 0.0, precision=prec, ldl=ldl)
+        thc[f"{prec}+{ldl}"] = 3 / gpu_best(th, 2)
+    rows["df_als"]["thc_driven_sweeps_per_s"] = thc
+    # order-6 ALS
+    dims, Rt6, R6 = (20, 100, 20, 100, 20, 100), 480, 720
+    X6, Z6, A6 = make_nd(dims, Rt6, R6, seed=3)
+    dX6, dZ6 = [d(x) for x in X6], d(Z6)
+
+    def nd_run(emu):
+        A = [d(a) for a in A6]
+        lamd = torch.ones(R6, dtype=torch.float64, device="cuda")
+        api.thc_cpd_nd_als(dX6, dZ6, A, lamd, 3, 3, emulated=emu)
+    n6 = sum(dims)
+    fl = 3 * (2.0 * (2 * n6) * Rt6 * R6 + 2 * 2.0 * Rt6 * Rt6 * R6 + n6 * R6 * R6 + 6 * R6 ** 3 / 3 + 2.0 * n6 * R6 * R6)
+    tc = cpu_once(lambda: ON.nd_als(X6, Z6, 3, A6, 1))
+    rows["order6_als"] = row(fl, gpu_best(lambda: nd_run(False), 2), gpu_best(lambda: nd_run(True), 2), tc * 3,
+                             "3 sweeps (oracle: 1 sweep x 3)")
+    rows["order6_als"]["sweeps_per_s_fp64"] = 3 / rows["order6_als"]["fp64_s"]
+    rows["order6_als"]["sweeps_per_s_emulated"] = 3 / rows["order6_als"]["emulated_s"]
+    print(json.dumps({"report": "rows beyond the ALS hot path", "fp64_fma_tflops": probe,
+                      "sizes": {"o": o, "v": v, "R_thc": Rt, "R_cp": R, "naux": naux,
+                                "order6": {"dims": dims, "R_thc": Rt6, "R_cp": R6}},
+                      "rows": rows}))
+    return 0
+
+
 def drift_report(args):
     """Per-sweep |fit - fit_fp64| on o=20 v=100 R_thc=480 R_cp=720 over 50 sweeps from one
     start: the split precisions, and FP64 runs whose start factors carry a relative
@@ -395,6 +517,8 @@ def main():
         return batched_report(args)
     if args.drift_report:
         return drift_report(args)
+    if args.rows_report:
+        return rows_report(args)
 
     import numpy as np
     import torch

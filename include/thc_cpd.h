@@ -311,6 +311,25 @@ thc_cpd_status thc_cpd_df_als(int o, int v, int naux, int R, const double* B, do
                               double* lam, int max_sweeps, double tol, int* sweeps_done,
                               double* fit_host, thc_cpd_opts* opts);
 
+/* THC-driven CP-ALS of an order-d THC-like tensor (Conclusions; the order-4 block of Eq. THC
+ * is the case d = 4, dL = 2, X = (Xo, Xv, Xo, Xv)):
+ *   G[i_0..i_{d-1}] = sum_{P,Q} prod_{k < dL} X_k[i_k,P] Z[P,Q] prod_{k >= dL} X_k[i_k,Q],
+ * CPD Gt = sum_r lam_r prod_k A_k[i_k,r]. dims: host array of the d mode sizes; X, A: host
+ * arrays of d device pointers (X_k dims[k] x Rt, A_k dims[k] x R, row-major FP64); Z: device
+ * Rt x Rt (need not be symmetric). 2 <= d <= 8, 1 <= dL <= d - 1, 1 <= dims[k] <= 4096,
+ * 1 <= R <= 2048. Precision FP64 only; opts->ldl = THC_CPD_LDL_EMULATED runs the GEMMs and the
+ * solve on the emulated FP64 tensor-core path.
+ * thc_cpd_nd_mttkrp: M (dims[mode] x R, device) = the mode-`mode` MTTKRP (lam not applied).
+ * thc_cpd_nd_als: A in/out (unit columns out), lam out, sweeps_done / fit_host host (may be
+ * NULL); solve, normalisation, loss, stopping rule, history and flags_out as thc_cpd_df_als.
+ * Allocate their workspace with cudaMallocAsync; synchronise (the ALS once per sweep). */
+thc_cpd_status thc_cpd_nd_mttkrp(int d, int dL, const int* dims, int Rt, int R, const double* const* X,
+                                 const double* Z, const double* const* A, int mode, double* M,
+                                 const thc_cpd_opts* opts);
+thc_cpd_status thc_cpd_nd_als(int d, int dL, const int* dims, int Rt, int R, const double* const* X,
+                              const double* Z, double* const* A, double* lam, int max_sweeps, double tol,
+                              int* sweeps_done, double* fit_host, thc_cpd_opts* opts);
+
 /* Measured FP64 FMA throughput of the device (TFLOP/s, 2 flop per FMA) from a probe kernel
  * of independent FMA chains on every SM (64 warps per SM, best of three timed launches):
  * the roofline denominator of the FP64 kernels (Gram, solve, loss). Synchronises. */

@@ -24,7 +24,7 @@ EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_mlp_forward", "thc_cpd_mlp_grad", "thc_cpd_mlp_train", "thc_cpd_als_trajectory",
            "thc_cpd_ldl_schedule", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam",
            "thc_cpd_fp64_fma_rate", "thc_cpd_emulated_gemm", "thc_cpd_exchange",
-           "thc_cpd_core_fit", "thc_cpd_df_als")
+           "thc_cpd_core_fit", "thc_cpd_df_als", "thc_cpd_nd_mttkrp", "thc_cpd_nd_als")
 MLP_NPARAM = 6849
 KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm", "tc_emulated")
 
@@ -88,6 +88,8 @@ _SIGS = {
     "thc_cpd_exchange": [I, I, I, I, I, P, P, P, PTR4, P, P, P, DP, DP, DP, OPTS],
     "thc_cpd_core_fit": [I, I, I, I, P, P, P, P, DP, IP, OPTS],
     "thc_cpd_df_als": [I, I, I, I, P, PTR4, P, I, D, IP, DP, OPTS],
+    "thc_cpd_nd_mttkrp": [I, I, IP, I, I, P, P, P, I, P, OPTS],
+    "thc_cpd_nd_als": [I, I, IP, I, I, P, P, P, P, I, D, IP, DP, OPTS],
     "thc_cpd_mlp_adam": [P, P, P, P, I, ctypes.c_float, OPTS],
     "thc_cpd_mlp_train": [P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong,
                           ctypes.POINTER(ctypes.c_float), OPTS],

@@ -18,7 +18,7 @@ __all__ = ["thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_profile_read", "thc_cpd_split_gemm", "thc_cpd_mttkrp_noalloc",
            "thc_cpd_als_batched", "thc_cpd_mlp_init", "thc_cpd_mlp_forward", "thc_cpd_mlp_grad",
            "thc_cpd_mlp_train", "thc_cpd_als_trajectory", "thc_cpd_ldl_solve", "thc_cpd_mlp_adam", "thc_cpd_fp64_fma_rate",
-           "thc_cpd_emulated_gemm", "thc_cpd_exchange", "thc_cpd_core_fit", "thc_cpd_df_als", "Opts"]
+           "thc_cpd_emulated_gemm", "thc_cpd_exchange", "thc_cpd_core_fit", "thc_cpd_df_als", "thc_cpd_nd_mttkrp", "thc_cpd_nd_als", "Opts"]
 
 
 def _dev(t: torch.Tensor, name: str, shape=None) -> int:
@@ -257,6 +257,48 @@ def thc_cpd_df_als(B, A, lam, max_sweeps: int, tol: float = 0.0, emulated=False,
     check(load().thc_cpd_df_als(o, v, naux, R, _dev(B, "B", (naux, o, v)), _ptr4(A, (o, v, o, v), R),
                                 _dev(lam, "lam", (R,)), int(max_sweeps), float(tol),
                                 ctypes.byref(done), ctypes.byref(fit), ctypes.byref(opts)))
+    out = dict(sweeps=done.value, fit=fit.value, flags=opts.flags_out)
+    if hist is not None:
+        h = list(hist)[: 2 * done.value]
+        out["losses"] = h[0::2]
+        out["fits"] = h[1::2]
+    return out
+
+
+def _nd_args(X, Z, A, dL):
+    d = len(X)
+    if len(A) != d:
+        raise ThcCpdError(ERR_ARG, "X and A must hold the same number of modes")
+    Rt = Z.shape[0]
+    R = A[0].shape[1]
+    dims = (ctypes.c_int * d)(*[int(x.shape[0]) for x in X])
+    xs = (ctypes.c_void_p * d)(*[_dev(x, f"X[{k}]", (x.shape[0], Rt)) for k, x in enumerate(X)])
+    As = (ctypes.c_void_p * d)(*[_dev(a, f"A[{k}]", (X[k].shape[0], R)) for k, a in enumerate(A)])
+    return d, int(dL), dims, Rt, R, xs, _dev(Z, "Z", (Rt, Rt)), As
+
+
+def thc_cpd_nd_mttkrp(X, Z, A, dL: int, mode: int, M=None, emulated=False, stream=None):
+    """Order-d MTTKRP of the THC-like tensor (X: d grid factors, modes < dL on P, the rest on Q)."""
+    d, dL, dims, Rt, R, xs, z, As = _nd_args(X, Z, A, dL)
+    if M is None:
+        M = torch.empty(X[mode].shape[0] if 0 <= mode < d else 1, R, dtype=torch.float64, device=Z.device)
+    opts = _opts("fp64", stream, ldl="emulated" if emulated else "auto")
+    check(load().thc_cpd_nd_mttkrp(d, dL, dims, Rt, R, xs, z, As, int(mode), _dev(M, "M"),
+                                   ctypes.byref(opts)))
+    return M
+
+
+def thc_cpd_nd_als(X, Z, A, lam, dL: int, max_sweeps: int, tol: float = 0.0, emulated=False,
+                   history=False, stream=None):
+    """Order-d THC-driven CP-ALS; A (d factors) and lam are updated in place."""
+    d, dL, dims, Rt, R, xs, z, As = _nd_args(X, Z, A, dL)
+    fit, done = ctypes.c_double(), ctypes.c_int()
+    hist = (ctypes.c_double * max(1, 2 * max_sweeps))() if history else None
+    opts = _opts("fp64", stream, 0,
+                 ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None,
+                 ldl="emulated" if emulated else "auto")
+    check(load().thc_cpd_nd_als(d, dL, dims, Rt, R, xs, z, As, _dev(lam, "lam", (R,)), int(max_sweeps),
+                                float(tol), ctypes.byref(done), ctypes.byref(fit), ctypes.byref(opts)))
     out = dict(sweeps=done.value, fit=fit.value, flags=opts.flags_out)
     if hist is not None:
         h = list(hist)[: 2 * done.value]

@@ -161,7 +161,7 @@ extern "C" thc_cpd_status thc_cpd_exchange(int o, int v, int Rt, int R, int nalp
     };
     {
         ProfScope prof(st, emu ? KC_OZ : KC_DGEMM,
-                       (double)nalpha * (8.0 * (o + v) * RtR + 2.0 * Rt * RtR + 6.0 * nmax * RR));
+                       (double)nalpha * (4.0 * (o + v) * RtR + 2.0 * Rt * RtR + (4.0 * o + 2.0 * v) * RR));
         for (int al = 0; al < nalpha; ++al) {
             const double* lA = Lam + (size_t)al * o;
             const double* gA = Gam + (size_t)al * v;

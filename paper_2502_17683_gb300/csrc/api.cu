@@ -272,8 +272,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     // the factorisation: plans (host task lists, uploaded once per shape) are prepared here,
     // never inside a capture
     const int ldl = opts ? opts->ldl : THC_CPD_LDL_AUTO;
-    c.emulated = !(need & NEED_BATCHED) && use_emulated_ldl(ldl, R, nmax) && oz_prepare(R, s.o) &&
-                 oz_prepare(R, s.v);
+    c.emulated = use_emulated_ldl(ldl, R, nmax) && oz_prepare(R, s.o) && oz_prepare(R, s.v);
     if (c.emulated) bytes += oz_ws_bytes(std::max(R + nmax, Rt), R);
     CK(cudaMallocAsync(&c.block, bytes, c.st));
     Arena ar;

@@ -69,7 +69,7 @@ cudaError_t ldl_flow_tasks(cudaStream_t st, int R, int n, double* Haug, double* 
 // The trailing update is the caller's. A plan for (bw, R + n - j0 - bw) must exist
 // (flow_prepare); the pivot threshold uses the whole order R.
 cudaError_t ldl_flow_panel(cudaStream_t st, int R, int n, int j0, int bw, double* Haug, double* P,
-                           double* dinv, DevScalars* sc, int mode, int* sync);
+                           double* dinv, DevScalars* sc, int mode, int* sync, int max_ctas = 0);
 // Index of the first task whose type or tile indices are out of range, or -1.
 int flow_task_check(int R, int n, const short* tasks, int ntasks);
 // Limit of every wait of the dataflow LDL^T and the backward solve launched afterwards from

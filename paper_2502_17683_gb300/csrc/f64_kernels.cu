@@ -568,7 +568,7 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
     const int nrows = R + n;
     const int nJ = cdiv(R, NB);
     if (oz && flow_sync) {
-        ldl_oz(st, R, n, Haug, P, dinv, sc, mode, flow_sync, *oz);
+        ldl_oz(st, R, n, Haug, P, dinv, sc, mode, flow_sync, *oz, flow_ctas);
     } else if (flow_sync && flow_prepare(R, n)) {
         ProfScope prof(st, KC_CHOL, (double)R * R * R / 3.0 + (double)n * R * R);
         ldl_flow(st, R, n, Haug, P, dinv, sc, mode, flow_sync, flow_ctas);

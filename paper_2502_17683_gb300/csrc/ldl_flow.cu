@@ -995,15 +995,20 @@ int flow_task_check(int R, int n, const short* tasks, int ntasks) {
 void flow_set_wait_ns(unsigned long long ns) { t_wait_ns = ns ? ns : kWaitNs; }
 
 cudaError_t ldl_flow_panel(cudaStream_t st, int R, int n, int j0, int bw, double* Haug, double* P,
-                           double* dinv, DevScalars* sc, int mode, int* sync) {
+                           double* dinv, DevScalars* sc, int mode, int* sync, int max_ctas) {
     const int below = R + n - j0 - bw;
     const Plan* p = get_plan(bw, below);
     if (!p) return cudaErrorInvalidValue;
     const int nsync = kSyncHead + (p->nT + p->nM) * (1 + p->nT);
     const size_t off = (size_t)j0 * R + j0;
+    // as ldl_flow: next to other problems (max_ctas > 0) a few CTAs with just the shared
+    // memory they use, one of them for the critical tasks
+    const int ncrit = max_ctas > 0 ? std::min(p->ncrit, 1) : p->ncrit;
+    const int grid = max_ctas > 0 ? std::max(2 + ncrit, std::min(p->grid, max_ctas)) : p->grid;
+    const int smem = max_ctas > 0 ? (int)kFlowSmemUsed : kFlowSmem;
     FlowArgs a{Haug + off, P + off, dinv + j0, bw, bw + below, p->nT, p->nM, R, R, p->tasks,
-               p->ntasks, p->nmain, p->ncrit, sync, nsync, sc, mode, t_wait_ns};
-    k_ldl_flow<<<p->grid, kFlowThreads, kFlowSmem, st>>>(a);
+               p->ntasks, p->nmain, ncrit, sync, nsync, sc, mode, t_wait_ns};
+    k_ldl_flow<<<grid, kFlowThreads, smem, st>>>(a);
     count_launch();
     return cudaGetLastError();
 }

@@ -56,8 +56,9 @@ bool oz_prepare(int R, int n);
 //   Haug[i][j] -= sum_{k in panel} L[i][k] D[k] L[j][k]   (j <= i for H rows; all j < R for M rows)
 // of the rows and columns after the panel. P: R x R (X = L D of the diagonal blocks), dinv:
 // R, sync: flow_sync_ints(R, n) ints (zero; left zero).
+// max_ctas > 0: the panels run on at most that many CTAs (problems side by side).
 cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
-                   DevScalars* sc, int mode, int* sync, const OzWs& ws);
+                   DevScalars* sc, int mode, int* sync, const OzWs& ws, int max_ctas = 0);
 
 // C (M x N, ldc) += sign * A B^T for FP64 row-major A (M x K, lda) and B (N x K, ldb),
 // emulated in K chunks of kOzPanel through the split and tensor-core kernels; lower: rows

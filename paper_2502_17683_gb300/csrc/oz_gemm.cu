@@ -539,7 +539,7 @@ bool oz_prepare(int R, int n) {
 }
 
 cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
-                   DevScalars* sc, int mode, int* sync, const OzWs& ws) {
+                   DevScalars* sc, int mode, int* sync, const OzWs& ws, int max_ctas) {
     for (int j0 = 0; j0 < R; j0 += KP) {
         const int bw = std::min(KP, R - j0);
         const int j1 = j0 + bw;
@@ -548,7 +548,7 @@ cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, doubl
         {
             // the panel's LDL^T and the substitution of every row below it
             ProfScope prof(st, KC_CHOL, (double)bw * bw * bw / 3.0 + (double)mA * bw * bw);
-            e = ldl_flow_panel(st, R, n, j0, bw, Haug, P, dinv, sc, mode, sync);
+            e = ldl_flow_panel(st, R, n, j0, bw, Haug, P, dinv, sc, mode, sync, max_ctas);
         }
         if (e != cudaSuccess) return e;
         if (j1 >= R) break;

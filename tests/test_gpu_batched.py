@@ -90,3 +90,28 @@ def test_dataflow_factorisation_does_not_depend_on_the_grid(api):
         assert r["fit"] == out["fit"]
         for a, c in zip(b["A"], s_["A"]):
             assert torch.equal(a, c)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_batched_emulated_factorisation_equals_single_runs(api, prec):
+    # From R_cp = 1024 the batched driver (ldl auto) factorises with the emulated two-level
+    # LDL^T, its panels on at most 32 CTAs next to the other problems; a single call runs the
+    # same panels on one CTA per SM. The panel kernel's result does not depend on its grid
+    # and the emulated products are deterministic, so both give the same bits, and the
+    # emulated problems sit next to a small problem on the blocked path.
+    shapes = [(29, 145, 704, 1056), (4, 20, 96, 144)]
+    batch = _problems(shapes, 600)
+    solo = _problems(shapes, 600)
+    res = api.thc_cpd_als_batched(batch, 3, 0.0, precision=prec)
+    for (o, v, Rt, R), b, s_, r in zip(shapes, batch, solo, res):
+        out = api.thc_cpd_als(s_["Xo"], s_["Xv"], s_["Z"], s_["A"], s_["lam"], 3, 0.0, precision=prec,
+                              ldl="emulated" if R >= 1024 else "blocked")
+        assert r["sweeps"] == out["sweeps"] == 3
+        assert r["fit"] == out["fit"]
+        for a, c in zip(b["A"], s_["A"]):
+            assert torch.equal(a, c)
+    # and the FP64 run follows the oracle
+    if prec == "fp64":
+        p = batch[0]["host"]
+        ref = O.als(p.Xo, p.Xv, p.Z, p.A, 3)
+        assert abs(res[0]["fit"] - ref["fits"][-1]) <= 1e-10

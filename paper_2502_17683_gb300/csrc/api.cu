@@ -257,7 +257,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     bytes += Arena::need<int>(flow_sync_ints(R, nmax));   // dataflow LDL^T progress
     bytes += Arena::need<int>(bsolve_sync_ints(nmax));    // sliced backward solve progress
     bytes += Arena::need<double>(pc);
-    bytes += Arena::need<double>(loss_red_need() + 2 * kNumSM * 2);
+    bytes += Arena::need<double>(loss_red_need() + 2 * kReduceBlocks);
     bytes += Arena::need<double>(R);
     bytes += 2 * Arena::need<DevScalars>(1);
     if (need & NEED_ALS) {  // two rollback snapshots (pipelined runs alternate)
@@ -290,7 +290,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     CK(cudaMemsetAsync(c.flow_sync, 0, sizeof(int) * flow_sync_ints(R, nmax), c.st));
     CK(cudaMemsetAsync(c.bs_sync, 0, sizeof(int) * bsolve_sync_ints(nmax), c.st));
     c.part = ar.take<double>(pc);
-    c.red = ar.take<double>(loss_red_need() + 2 * kNumSM * 2);
+    c.red = ar.take<double>(loss_red_need() + 2 * kReduceBlocks);
     c.ones = ar.take<double>(R);
     c.sc = ar.take<DevScalars>(1);
     c.sc_snap = ar.take<DevScalars>(1);

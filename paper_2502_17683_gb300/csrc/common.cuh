@@ -8,10 +8,23 @@
 
 namespace thc {
 
-// Launch-time constants sized for GB300: 152 SMs, FP64 throughput about two DFMA per
-// clock per SM, so every FP64 kernel aims for at least two resident CTAs per SM.
-constexpr int kNumSM = 152;
-constexpr int kTargetCTAs = 2 * kNumSM;
+// SMs of the current device (GB300: 152), queried once per device: grids of persistent and
+// grid-stride kernels follow the part they run on.
+inline int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+// Blocks of the fixed-order reductions (loss, norms): a constant, so that the order of the
+// sums, and with it the result's bits, is the same on every device.
+constexpr int kReduceBlocks = 304;
 
 // Device-side scalars of one ALS run (one struct per problem).
 struct DevScalars {

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(CF_THREADS) k_dot_final3(const double* __restr
     }
 }
 
-int grid_for(long n) { return (int)std::min<long>(std::max<long>(cdiv(n, CF_THREADS), 1), 4L * kNumSM); }
+int grid_for(long n) { return (int)std::min<long>(std::max<long>(cdiv(n, CF_THREADS), 1), 4L * num_sms()); }
 
 thc_cpd_status cerr(thc_cpd_status s, const char* fmt, ...) {
     char msg[320];

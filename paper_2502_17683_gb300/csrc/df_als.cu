@@ -36,7 +36,7 @@ namespace {
 
 constexpr int DF_THREADS = 256;
 
-int df_grid(long n) { return (int)std::min<long>(std::max<long>(cdiv(n, DF_THREADS), 1), 4L * kNumSM); }
+int df_grid(long n) { return (int)std::min<long>(std::max<long>(cdiv(n, DF_THREADS), 1), 4L * num_sms()); }
 
 // Bp[(i * naux + X) * v + a] = B[(X * o + i) * v + a]
 __global__ void k_df_permute(int naux, int o, int v, const double* __restrict__ B, double* __restrict__ Bp) {

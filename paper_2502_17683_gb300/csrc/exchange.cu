@@ -156,7 +156,7 @@ extern "C" thc_cpd_status thc_cpd_exchange(int o, int v, int Rt, int R, int nalp
     };
     auto scale = [&](int rows, int n, const double* s, const double* X, double* out) {
         const long total = (long)rows * n;
-        k_scale_rows<<<(int)std::min<long>(cdiv(total, 256), 4L * kNumSM), 256, 0, st>>>(rows, n, s, X, out);
+        k_scale_rows<<<(int)std::min<long>(cdiv(total, 256), 4L * num_sms()), 256, 0, st>>>(rows, n, s, X, out);
         count_launch();
     };
     {

@@ -207,7 +207,7 @@ GemmPlan plan_gemm(int M, int N, int K, bool symm) {
         const int kc = ((cdiv(K, s) + 15) / 16) * 16;
         const int ss = cdiv(K, kc);
         if (ss != s) continue;
-        const double waves = (double)cdiv((long)p.tiles * ss, kNumSM);
+        const double waves = (double)cdiv((long)p.tiles * ss, num_sms());
         const double cost = waves * kc + (ss > 1 ? 0.5 * ss : 0.0);
         if (cost < best) {
             best = cost;
@@ -285,7 +285,7 @@ void dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, 
         dispatch_gemm<64>(st, p, trans_a, hadb, symm, M, N, K, A, lda, B, B2, ldb, C, ldc, E, part);
     if (p.splits > 1) {
         const long total = (long)M * N;
-        int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSM);
+        int blocks = (int)std::min<long>(cdiv(total, 256), 4L * num_sms());
         k_splitk_reduce<<<blocks, 256, 0, st>>>(M, N, p.splits, part, C, ldc, E, symm ? p.BM : 0);
     }
 }
@@ -342,7 +342,7 @@ __global__ void k_hadamard3(int R, const double* __restrict__ Ga, const double* 
 void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const double* Gc,
                double* H, DevScalars* sc) {
     const long n = (long)R * R;
-    int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    int blocks = (int)std::min<long>(cdiv(n, 256), 4L * num_sms());
     ProfScope prof(st, KC_AUX, 2.0 * n, 32.0 * n);
     count_launch();
     k_hadamard3<<<blocks, 256, 0, st>>>(R, Ga, Gb, Gc, H, sc);
@@ -365,7 +365,7 @@ __global__ void k_copy_maxdiag(int R, const double* __restrict__ H, double* __re
 
 void copy_with_maxdiag(cudaStream_t st, int R, const double* H, double* H_out, DevScalars* sc) {
     const long n = (long)R * R;
-    int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    int blocks = (int)std::min<long>(cdiv(n, 256), 4L * num_sms());
     count_launch();
     k_copy_maxdiag<<<blocks, 256, 0, st>>>(R, H, H_out, sc);
 }
@@ -671,11 +671,11 @@ cudaError_t copy_many(cudaStream_t st, int np, const double* const* src, double*
     }
     a.np = np;
     count_launch();
-    k_copy_many<<<(int)std::max<long>(1, std::min<long>(cdiv(total, 256), 2L * kNumSM)), 256, 0, st>>>(a);
+    k_copy_many<<<(int)std::max<long>(1, std::min<long>(cdiv(total, 256), 2L * num_sms())), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-constexpr int RED_BLOCKS = 2 * kNumSM;
+constexpr int RED_BLOCKS = kReduceBlocks;
 constexpr int RED_THREADS = 256;
 
 size_t loss_red_need() { return 2 * RED_BLOCKS; }
@@ -890,7 +890,7 @@ __global__ void k_trial(long n, int R, const double* __restrict__ An, const doub
 void trial_point(cudaStream_t st, int n, int R, const double* An, const double* Ao,
                  const double* ln, const double* lo, bool absorb, double alpha, double* T) {
     const long N = (long)n * R;
-    k_trial<<<(int)std::min<long>(cdiv(N, 256), 4L * kNumSM), 256, 0, st>>>(N, R, An, Ao, ln, lo,
+    k_trial<<<(int)std::min<long>(cdiv(N, 256), 4L * num_sms()), 256, 0, st>>>(N, R, An, Ao, ln, lo,
                                                                            absorb ? 1 : 0, alpha, T);
     count_launch();
 }

@@ -908,7 +908,7 @@ const Plan* get_plan(int R, int n) {
             cudaSuccess)
             return nullptr;
     }
-    int nsm = kNumSM;
+    int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // every SM (measured: 152 CTAs beat 120 and 80 at R = 720; the chain's waits for
     // workers shrink), fewer only when there are fewer tasks than worker groups
@@ -1020,7 +1020,7 @@ cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, doubl
     if (n <= 0) return cudaSuccess;
     const int nJ = cdiv(R, BB), C = cdiv(R, kSlice);
     BsArgs a{Yf, A, H, R, n, nJ, C, sync, t_wait_ns};
-    const int grid = std::min(n * C, kNumSM * 4);
+    const int grid = std::min(n * C, num_sms() * 4);
     k_bsolve_slices<<<grid, kBsThreads, 0, st>>>(a);
     count_launch();
     return cudaGetLastError();

@@ -87,7 +87,7 @@ struct NdCtx {
         for (const double* p : more) pl.p[pl.n++] = p;
         ProfScope prof(st, KC_AUX, (double)count * std::max(pl.n - 1, 0), 8.0 * count * (pl.n + 1));
         count_launch();
-        k_hprod<<<(int)std::min<long>(std::max<long>(cdiv(count, ND_THREADS), 1), 4L * kNumSM), ND_THREADS, 0, st>>>(
+        k_hprod<<<(int)std::min<long>(std::max<long>(cdiv(count, ND_THREADS), 1), 4L * num_sms()), ND_THREADS, 0, st>>>(
             count, pl, out);
     }
     void project(int k, const double* Ak) { gemm(true, Rt, R, n[k], X[k], Rt, Ak, R, W[k], R, false); }

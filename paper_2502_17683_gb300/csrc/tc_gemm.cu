@@ -410,8 +410,8 @@ cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const Split
     // wanted and the tile grid is far smaller than the SM count
     int splits = 1;
     const long tiles = (long)cdiv(N, BN) * mt;
-    if (!ep.out_f32 && !ep.mul && ep.out_f64t && part && tiles * 2 <= kNumSM && nkb >= 4) {
-        splits = (int)std::min<long>(std::min<long>(kNumSM / tiles, nkb / 2),
+    if (!ep.out_f32 && !ep.mul && ep.out_f64t && part && tiles * 2 <= num_sms() && nkb >= 4) {
+        splits = (int)std::min<long>(std::min<long>(num_sms() / tiles, nkb / 2),
                                      (long)(part_cap / ((size_t)N * ep.ld_f64t)));
         splits = std::max(1, splits);
     }
@@ -439,7 +439,7 @@ cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const Split
                  args.ld_split % 4 == 0)
                     ? 4
                     : 0);
-    const int grid = std::min(args.ntiles, kNumSM);  // persistent: at most one CTA per SM
+    const int grid = std::min(args.ntiles, num_sms());  // persistent: at most one CTA per SM
     ProfScope prof(st, KC_TC, 2.0 * M * (double)N * K);
     count_launch(splits > 1 ? 2 : 1);
     static std::once_flag attr_once;
@@ -454,7 +454,7 @@ cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const Split
         k_tc_gemm<false><<<grid, NTHREADS, smem, st>>>(mAh, mAl, mBh, mBl, args);
     if (splits > 1) {
         const long total = (long)N * ep.ld_f64t;
-        k_tc_splitk_reduce<<<(int)std::min<long>(cdiv(total, 256), 4L * kNumSM), 256, 0, st>>>(
+        k_tc_splitk_reduce<<<(int)std::min<long>(cdiv(total, 256), 4L * num_sms()), 256, 0, st>>>(
             part, splits, total, ep.out_f64t);
     }
     return cudaGetLastError();
@@ -619,7 +619,7 @@ __global__ void k_split_hadamard(const float* __restrict__ a, const float* __res
 void split_rows(cudaStream_t st, bool tf32, const double* src, int ld, int rows, int cols,
                 SplitMat& d) {
     const long n = (long)rows * cols;
-    const int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    const int blocks = (int)std::min<long>(cdiv(n, 256), 4L * num_sms());
     count_launch();
     if (tf32)
         k_split_rows<true><<<blocks, 256, 0, st>>>(src, ld, rows, cols, d.hi, d.lo, d.pitch);
@@ -640,7 +640,7 @@ void split_transpose(cudaStream_t st, bool tf32, const double* src, int ld, int 
 void split_hadamard(cudaStream_t st, bool tf32, const float* a, const float* b, int ld, int rows,
                     int cols, SplitMat& d) {
     const long n = (long)rows * cols;
-    const int blocks = (int)std::min<long>(cdiv(n, 256), 4L * kNumSM);
+    const int blocks = (int)std::min<long>(cdiv(n, 256), 4L * num_sms());
     count_launch();
     if (tf32)
         k_split_hadamard<true><<<blocks, 256, 0, st>>>(a, b, ld, rows, cols, d.hi, d.lo, d.pitch);

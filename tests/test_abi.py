@@ -97,3 +97,40 @@ def test_no_cpu_fallback_when_library_missing(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
         finally:
             _lib._lib = saved
+
+
+def test_rows_beyond_the_hot_path_check_their_arguments_before_device_work(lib):
+    from paper_2502_17683_gb300 import _lib
+    from paper_2502_17683_gb300._lib import PTR4, Opts
+    # core fit: shapes, R_thc limit, null pointers
+    f = lib.thc_cpd_core_fit
+    assert f(0, 3, 4, 5, 1, 1, 1, 1, None, None, None) == _lib.ERR_SHAPE
+    assert f(2, 3, 2049, 5, 1, 1, 1, 1, None, None, None) == _lib.ERR_SHAPE
+    assert f(2, 3, 4, 5, 1, None, 1, 1, None, None, None) == _lib.ERR_ARG
+    assert f(2, 3, 4, 5, 1, 1, 1, None, None, None, None) == _lib.ERR_ARG
+    # DF-driven ALS: shapes, null factors, split precision refused, sweeps
+    g = lib.thc_cpd_df_als
+    A = PTR4(1, 1, 1, 1)
+    assert g(2, 3, 4, 0, 1, A, 1, 1, 0.0, None, None, None) == _lib.ERR_SHAPE
+    assert g(2, 3, 4, 2049, 1, A, 1, 1, 0.0, None, None, None) == _lib.ERR_SHAPE
+    assert g(2, 3, 4, 5, 1, PTR4(1, None, 1, 1), 1, 1, 0.0, None, None, None) == _lib.ERR_ARG
+    assert g(2, 3, 4, 5, 1, A, 1, 0, 0.0, None, None, None) == _lib.ERR_ARG
+    opts = Opts()
+    opts.precision = 1
+    assert g(2, 3, 4, 5, 1, A, 1, 1, 0.0, None, None, ctypes.byref(opts)) == _lib.ERR_ARG
+    assert b"FP64" in lib.thc_cpd_last_error()
+    # order d: d and dL ranges, mode range, mode sizes
+    dims = (ctypes.c_int * 3)(3, 4, 5)
+    ptrs = (ctypes.c_void_p * 3)(1, 1, 1)
+    h = lib.thc_cpd_nd_mttkrp
+    assert h(3, 3, dims, 6, 2, ptrs, 1, ptrs, 0, 1, None) == _lib.ERR_SHAPE  # dL = d
+    assert h(9, 1, dims, 6, 2, ptrs, 1, ptrs, 0, 1, None) == _lib.ERR_SHAPE  # d > 8
+    assert h(3, 1, dims, 6, 2, ptrs, 1, ptrs, 3, 1, None) == _lib.ERR_ARG    # mode = d
+    bad = (ctypes.c_int * 3)(3, 0, 5)
+    assert h(3, 1, bad, 6, 2, ptrs, 1, ptrs, 0, 1, None) == _lib.ERR_SHAPE
+    assert lib.thc_cpd_nd_als(3, 1, dims, 6, 2, ptrs, 1, ptrs, None, 1, 0.0, None, None, None) == _lib.ERR_ARG
+    # exchange energy: quadrature size, null quadrature factors
+    e = lib.thc_cpd_exchange
+    d1 = ctypes.c_double()
+    assert e(2, 3, 4, 5, 0, 1, 1, 1, A, 1, 1, 1, ctypes.byref(d1), None, None, None) == _lib.ERR_SHAPE
+    assert e(2, 3, 4, 5, 2, 1, 1, 1, A, 1, None, 1, ctypes.byref(d1), None, None, None) == _lib.ERR_ARG

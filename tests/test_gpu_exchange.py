@@ -74,3 +74,19 @@ def test_exchange_of_an_als_cpd_is_robust_to_first_order(api):
     assert abs(er - xr) <= 1e-11 * abs(e_thc)
     assert abs((er - e_thc) + XX.exchange_explicit(D, D, Lam, Gam)) <= 1e-11 * abs(e_thc)
     assert abs(er - e_thc) < abs(e1 - e_thc)
+
+
+@pytest.mark.parametrize("emulated", [False, True])
+def test_exchange_at_full_size(api, emulated):
+    # (50, 250, 1200, 1800), the decomposition's bench size, two of the 12 quadrature points
+    p, lam, Lam, Gam = _case(50, 250, 1200, 1800, 12, seed=7)
+    Lam, Gam = Lam[[0, 11]], Gam[[0, 11]]
+    d = to_dev(p, torch)
+    e1, e2, er = api.thc_cpd_exchange(d["Xo"], d["Xv"], d["Z"], d["A"], _dev(lam), _dev(Lam), _dev(Gam),
+                                      emulated=emulated)
+    r1, r2, rr = X.exchange_robust(p.Xo, p.Xv, p.Z, p.A, lam, Lam, Gam)
+    s1 = abs(X.exchange_single(np.abs(p.Xo), np.abs(p.Xv), np.abs(p.Z), [np.abs(a) for a in p.A], lam, Lam, Gam))
+    s2 = abs(X.exchange_double([np.abs(a) for a in p.A], lam, Lam, Gam))
+    assert abs(e1 - r1) <= 1e-12 * s1
+    assert abs(e2 - r2) <= 1e-12 * s2
+    assert abs(er - rr) <= 1e-12 * (2 * s1 + s2)

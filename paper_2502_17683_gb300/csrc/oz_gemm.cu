@@ -18,7 +18,6 @@ __device__ int g_oz_error = 0;
 namespace {
 
 constexpr int S = kOzSlices;
-constexpr int S_ = kOzSlices;
 constexpr int KP = kOzPanel;                 // K elements per operand row (2 x 64)
 constexpr int BM = 128;                      // MMA M: rows of the left operand per tile
 constexpr int BN = 32;                       // MMA N: rows of the right operand per tile
@@ -71,7 +70,7 @@ __device__ __forceinline__ void digits_of(double x, int erow, int (&d)[S]) {
     for (int a = S - 1; a > 0; --a) {
         const long long da = ((X + 128) & 255) - 128;
         d[a] = (int)da;
-        X = (X - da) / 256;  // exact: X - da is a multiple of 256
+        X = (X - da) >> 8;  // exact: X - da is a multiple of 256 (arithmetic shift)
     }
     d[0] = (int)X;
 }
@@ -80,135 +79,111 @@ __device__ __forceinline__ uint16_t bf16_int(int d) {
     return __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
 }
 
-// One warp per row r < rows: the values src[r * ld + k] (k < K, zero beyond), their row
-// exponent and their S digit slices out[a][r][k] (k < KP).
-__global__ void __launch_bounds__(256)
+// Row exponent of a row held by a group of 128 threads (4 warps, one value each): the max
+// of the exponent fields, -2000 (no normal value) giving 0. sh: 4 ints per group; every
+// thread of the block must call it (it holds a block barrier).
+__device__ __forceinline__ int group_row_exp(int e, int* sh, int group, int wig) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0) sh[group * 4 + wig] = e;
+    __syncthreads();
+    e = max(max(sh[group * 4], sh[group * 4 + 1]), max(sh[group * 4 + 2], sh[group * 4 + 3]));
+    return e == -2000 ? 0 : e;
+}
+
+// The S digits of one value into slices out[a][row][k] (one BF16 each).
+__device__ __forceinline__ void store_digits(double x, int erow, uint16_t* __restrict__ out, int rows_alloc,
+                                             int row, int k) {
+    int d[S];
+    digits_of(x, erow, d);
+#pragma unroll
+    for (int a = 0; a < S; ++a) out[((size_t)a * rows_alloc + row) * KP + k] = bf16_int(d[a]);
+}
+
+constexpr int SPLIT_ROWS = 2;  // rows per block of the row splits: 128 threads, one value each, per row
+
+// Row r < rows: the values src[r * ld + k] (k < K, zero beyond), their row exponent and
+// their S digit slices out[a][r][k] (k < KP). 128 threads per row, one value each.
+__global__ void __launch_bounds__(128 * SPLIT_ROWS)
 k_oz_split(const double* __restrict__ src, int ld, int rows, int K, uint16_t* __restrict__ out,
            int rows_alloc, int* __restrict__ exps) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= rows) return;
-    const int r = warp;
-    double x[KP / 32];
-    int emax = -2000;
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) {
-        const int k = lane + 32 * q;
-        x[q] = k < K ? src[(size_t)r * ld + k] : 0.0;
-        emax = max(emax, exp_of(x[q]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    const int erow = emax == -2000 ? 0 : emax;
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) {
-        const int k = lane + 32 * q;
-        int d[S];
-        digits_of(x[q], erow, d);
-#pragma unroll
-        for (int a = 0; a < S; ++a) out[((size_t)a * rows_alloc + r) * KP + k] = bf16_int(d[a]);
-    }
-    if (lane == 0) exps[r] = erow;
+    __shared__ int sh[4 * SPLIT_ROWS];
+    const int group = threadIdx.x >> 7, k = threadIdx.x & 127, wig = k >> 5;
+    const int r = blockIdx.x * SPLIT_ROWS + group;
+    const bool live = r < rows;
+    const double x = (live && k < K) ? src[(size_t)r * ld + k] : 0.0;
+    const int erow = group_row_exp(exp_of(x), sh, group, wig);
+    if (!live) return;
+    store_digits(x, erow, out, rows_alloc, r, k);
+    if (k == 0) exps[r] = erow;
 }
 
 // The two operands of an LDL^T trailing update from one read of the rows below the panel:
 // row r < mA of src (its first K entries) gives the left-operand row r, scaled per column k
 // by D_k 2^-m_k, and, for r < mB, the right-operand row r, scaled by 2^m_k (m_k =
 // floor(E(D_k) / 2), D_k = diag[k * (ldd + 1)]), each cut into its S digit slices.
-__global__ void __launch_bounds__(256)
+// 128 threads per row, one column each.
+__global__ void __launch_bounds__(128 * SPLIT_ROWS)
 k_oz_split_ldl(const double* __restrict__ src, int ld, int mA, int mB, int K,
                const double* __restrict__ diag, int ldd, uint16_t* __restrict__ outA, int rowsA,
                int* __restrict__ expsA, uint16_t* __restrict__ outB, int rowsB, int* __restrict__ expsB) {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (r >= mA) return;
-    double xa[KP / 32], xb[KP / 32];
-    int ea = -2000, eb = -2000;
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) {
-        const int k = lane + 32 * q;
-        double a = 0.0, b = 0.0;
-        if (k < K) {
-            const double v = src[(size_t)r * ld + k];
-            const double dk = diag[(size_t)k * (ldd + 1)];
-            const int Ek = exp_of(dk);
-            const int mk = (Ek == -2000) ? 0 : (Ek >> 1);
-            a = v * (dk * pow2(-mk));
-            b = v * pow2(mk);
-        }
-        xa[q] = a;
-        xb[q] = b;
-        ea = max(ea, exp_of(a));
-        eb = max(eb, exp_of(b));
+    __shared__ int sha[4 * SPLIT_ROWS], shb[4 * SPLIT_ROWS];
+    const int group = threadIdx.x >> 7, k = threadIdx.x & 127, wig = k >> 5;
+    const int r = blockIdx.x * SPLIT_ROWS + group;
+    const bool live = r < mA;
+    double a = 0.0, b = 0.0;
+    if (live && k < K) {
+        const double v = src[(size_t)r * ld + k];
+        const double dk = diag[(size_t)k * (ldd + 1)];
+        const int Ek = exp_of(dk);
+        const int mk = (Ek == -2000) ? 0 : (Ek >> 1);
+        a = v * (dk * pow2(-mk));
+        b = v * pow2(mk);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
-        eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
-    }
-    ea = ea == -2000 ? 0 : ea;
-    eb = eb == -2000 ? 0 : eb;
+    const int ea = group_row_exp(exp_of(a), sha, group, wig);
+    const int eb = group_row_exp(exp_of(b), shb, group, wig);
+    if (!live) return;
+    store_digits(a, ea, outA, rowsA, r, k);
     const bool hasB = r < mB;
-#pragma unroll
-    for (int q = 0; q < KP / 32; ++q) {
-        const int k = lane + 32 * q;
-        int d[S];
-        digits_of(xa[q], ea, d);
-#pragma unroll
-        for (int a = 0; a < S; ++a) outA[((size_t)a * rowsA + r) * KP + k] = bf16_int(d[a]);
-        if (hasB) {
-            digits_of(xb[q], eb, d);
-#pragma unroll
-            for (int a = 0; a < S; ++a) outB[((size_t)a * rowsB + r) * KP + k] = bf16_int(d[a]);
-        }
-    }
-    if (lane == 0) {
+    if (hasB) store_digits(b, eb, outB, rowsB, r, k);
+    if (k == 0) {
         expsA[r] = ea;
         if (hasB) expsB[r] = eb;
     }
 }
 
+constexpr int SPLIT_T_ROWS = 8;  // output rows per block of the transposed split (1024 threads)
+
 // Transposed source: output row n < N takes the K chunk [k0, k0 + kb) of column n of the
 // K x N row-major matrix S (ld), times S2 element by element when given (a Hadamard
-// operand): values S[(k0 + k) * ld + n] (* S2[...]). A 128 x 32 slab is staged in shared
-// memory with coalesced reads, then each warp forms four output rows as k_oz_split does.
-__global__ void __launch_bounds__(256)
+// operand): values S[(k0 + k) * ld + n] (* S2[...]). A 128 x 8 slab is staged in shared
+// memory (8 consecutive columns per source row), then 128 threads per output row form its
+// exponent and digits, one value each.
+__global__ void __launch_bounds__(128 * SPLIT_T_ROWS)
 k_oz_split_t(const double* __restrict__ S, const double* __restrict__ S2, int ld, int N, int k0,
              int kb, uint16_t* __restrict__ out, int rows_alloc, int* __restrict__ exps) {
-    __shared__ double tile[KP][33];
-    const int n0 = blockIdx.x * 32, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int kk = warp; kk < KP; kk += 8) {
-        const int n = n0 + lane;
+    __shared__ double tile[KP][SPLIT_T_ROWS + 1];
+    __shared__ int sh[4 * SPLIT_T_ROWS];
+    const int n0 = blockIdx.x * SPLIT_T_ROWS;
+    {
+        const int kk = threadIdx.x / SPLIT_T_ROWS, nn = threadIdx.x % SPLIT_T_ROWS;
+        const int n = n0 + nn;
         double v = 0.0;
         if (kk < kb && n < N) {
             const size_t o = (size_t)(k0 + kk) * ld + n;
             v = S[o];
             if (S2) v *= S2[o];
         }
-        tile[kk][lane] = v;
+        tile[kk][nn] = v;
     }
     __syncthreads();
-    for (int nn = warp * 4; nn < warp * 4 + 4; ++nn) {
-        const int n = n0 + nn;
-        if (n >= N) break;
-        double x[KP / 32];
-        int emax = -2000;
-#pragma unroll
-        for (int q = 0; q < KP / 32; ++q) {
-            x[q] = tile[lane + 32 * q][nn];
-            emax = max(emax, exp_of(x[q]));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        const int erow = emax == -2000 ? 0 : emax;
-#pragma unroll
-        for (int q = 0; q < KP / 32; ++q) {
-            int d[S_];
-            digits_of(x[q], erow, d);
-#pragma unroll
-            for (int a = 0; a < S_; ++a)
-                out[((size_t)a * rows_alloc + n) * KP + lane + 32 * q] = bf16_int(d[a]);
-        }
-        if (lane == 0) exps[n] = erow;
-    }
+    const int group = threadIdx.x >> 7, k = threadIdx.x & 127, wig = k >> 5;
+    const int n = n0 + group;
+    const double x = tile[k][group];
+    const int erow = group_row_exp(exp_of(x), sh, group, wig);
+    if (n >= N) return;
+    store_digits(x, erow, out, rows_alloc, n, k);
+    if (k == 0) exps[n] = erow;
 }
 
 // C[j][i] = C[i][j] for j > i (the upper triangle of a symmetric result from its lower one)
@@ -483,7 +458,7 @@ bool slice_map(CUtensorMap* m, const uint16_t* base, int rows, int rows_alloc, i
 void split(cudaStream_t st, const double* src, int ld, int rows, int K, uint16_t* out, int rows_alloc,
            int* exps) {
     if (rows <= 0) return;
-    k_oz_split<<<cdiv((long)rows * 32, 256), 256, 0, st>>>(src, ld, rows, K, out, rows_alloc, exps);
+    k_oz_split<<<cdiv(rows, SPLIT_ROWS), 128 * SPLIT_ROWS, 0, st>>>(src, ld, rows, K, out, rows_alloc, exps);
     count_launch();
 }
 
@@ -556,7 +531,7 @@ cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, doubl
         const double* diag = Haug + (size_t)j0 * R + j0;
         {
             ProfScope prof(st, KC_OZ, (double)mB * (mB + 1) * bw + 2.0 * (mA - mB) * mB * bw);
-            k_oz_split_ldl<<<cdiv((long)mA * 32, 256), 256, 0, st>>>(below, R, mA, mB, bw, diag, R, ws.sA,
+            k_oz_split_ldl<<<cdiv(mA, SPLIT_ROWS), 128 * SPLIT_ROWS, 0, st>>>(below, R, mA, mB, bw, diag, R, ws.sA,
                                                                    ws.rowsA, ws.eA, ws.sB, ws.rowsB, ws.eB);
             count_launch();
             e = update(st, mA, mB, Haug + (size_t)j1 * R + j1, R, ws, true, -1.0);
@@ -595,12 +570,14 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
         if (same_ab) {
             // nothing: the left operand is read from the right operand's slices
         } else if (trans_a) {
-            k_oz_split_t<<<cdiv(M, 32), 256, 0, st>>>(A, nullptr, lda, M, k0, kb, ws.sA, ws.rowsA, ws.eA);
+            k_oz_split_t<<<cdiv(M, SPLIT_T_ROWS), 128 * SPLIT_T_ROWS, 0, st>>>(A, nullptr, lda, M, k0, kb, ws.sA,
+                                                                               ws.rowsA, ws.eA);
             count_launch();
         } else {
             split(st, A + k0, lda, M, kb, ws.sA, ws.rowsA, ws.eA);
         }
-        k_oz_split_t<<<cdiv(N, 32), 256, 0, st>>>(B, B2, ldb, N, k0, kb, ws.sB, ws.rowsB, ws.eB);
+        k_oz_split_t<<<cdiv(N, SPLIT_T_ROWS), 128 * SPLIT_T_ROWS, 0, st>>>(B, B2, ldb, N, k0, kb, ws.sB, ws.rowsB,
+                                                                           ws.eB);
         count_launch();
         const cudaError_t e = update(st, M, N, C, ldc, ws, symm, 1.0, k0 > 0, E, same_ab);
         if (e != cudaSuccess) return e;

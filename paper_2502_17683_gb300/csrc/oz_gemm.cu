@@ -21,11 +21,14 @@ constexpr int S = kOzSlices;
 constexpr int KP = kOzPanel;                 // K elements per operand row (2 x 64)
 constexpr int BM = 128;                      // MMA M: rows of the left operand per tile
 constexpr int BN = 32;                       // MMA N: rows of the right operand per tile
-constexpr int A_TILE = BM * 128;             // bytes of one 128 x 64 BF16 box (one slice, one K half)
+constexpr int A_TILE = BM * 128;             // bytes of one 128 x 64 BF16 slice (one K half)
+constexpr int A_DEPTH = 2;                   // slices per left-operand TMA box and ring stage
+constexpr int A_STAGE = A_DEPTH * A_TILE;    // 32 KB
+constexpr int A_GROUPS = (S + A_DEPTH - 1) / A_DEPTH;  // stages per K half (the last one half used)
 constexpr int B_HALF = S * BN * 128;         // all right-operand slices of one K half (28 KB)
-constexpr int A_STAGES = 6;
+constexpr int A_STAGES = 4;
 constexpr int B_STAGES = 2;
-constexpr int SMEM_BYTES = 1024 + A_STAGES * A_TILE + B_STAGES * B_HALF + 256;
+constexpr int SMEM_BYTES = 1024 + A_STAGES * A_STAGE + B_STAGES * B_HALF + 256;
 constexpr int ACC_SET = S * BN;              // TMEM columns of one set of S accumulators (224)
 constexpr int TMEM_COLS = 512;               // two sets: the epilogue drains one, the MMAs fill the other
 constexpr int EPI_WARPS = 16;                // four per TMEM lane quarter, 8 columns each
@@ -241,8 +244,8 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             const UpdArgs args) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* asm_ = smem;                               // [A_STAGES] x A_TILE
-    uint8_t* bsm = smem + A_STAGES * A_TILE;            // [B_STAGES] x B_HALF
+    uint8_t* asm_ = smem;                               // [A_STAGES] x A_STAGE
+    uint8_t* bsm = smem + A_STAGES * A_STAGE;           // [B_STAGES] x B_HALF
     uint64_t* afull = (uint64_t*)(bsm + B_STAGES * B_HALF);
     uint64_t* aempty = afull + A_STAGES;
     uint64_t* bfull = aempty + A_STAGES;
@@ -288,14 +291,16 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                 const int sb = ib % B_STAGES;
                 if (!oz_wait(&bempty[sb], ((ib / B_STAGES) & 1) ^ 1, 1)) { ok = false; break; }
                 mbar_expect_tx(&bfull[sb], (uint32_t)B_HALF);
-                for (int b = 0; b < S; ++b)
-                    tma_load_3d(bsm + sb * B_HALF + b * (BN * 128), &mapB, &bfull[sb], 64 * c, n0, b);
+                // all S right slices in one box, stacked (slice b at rows 32 b ..)
+                tma_load_3d(bsm + sb * B_HALF, &mapB, &bfull[sb], 64 * c, n0, 0);
                 ++ib;
-                for (int a = 0; a < S; ++a, ++ia) {
+                for (int g = 0; g < A_GROUPS; ++g, ++ia) {
+                    // slices 2g, 2g + 1 in one box (past the last slice the box is zero-filled;
+                    // its bytes still count)
                     const int sa = ia % A_STAGES;
                     if (!oz_wait(&aempty[sa], ((ia / A_STAGES) & 1) ^ 1, 1)) { ok = false; break; }
-                    mbar_expect_tx(&afull[sa], (uint32_t)A_TILE);
-                    tma_load_3d(asm_ + sa * A_TILE, &mapA, &afull[sa], 64 * c, m0, a);
+                    mbar_expect_tx(&afull[sa], (uint32_t)A_STAGE);
+                    tma_load_3d(asm_ + sa * A_STAGE, &mapA, &afull[sa], 64 * c, m0, A_DEPTH * g);
                 }
             }
         }
@@ -317,21 +322,26 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             for (int c = 0; c < 2 && ok; ++c) {
                 const int sb = ib % B_STAGES;
                 if (!oz_wait(&bfull[sb], (ib / B_STAGES) & 1, 3)) { ok = false; break; }
-                for (int a = 0; a < S; ++a, ++ia) {
+                const uint64_t bd = sw128_desc(smem_u32(bsm + sb * B_HALF));
+                for (int g = 0; g < A_GROUPS; ++g, ++ia) {
                     const int sa = ia % A_STAGES;
                     if (!oz_wait(&afull[sa], (ia / A_STAGES) & 1, 4)) { ok = false; break; }
                     tc_fence_after();
-                    // the right slices b = 0..S-1-a lie stacked in the stage (rows 32 b ..), so
-                    // one MMA of N = 32 (S - a) with its accumulator base at column 32 a puts
-                    // A_a B_b^T at columns 32 (a + b): accumulator a + b, for every b at once
-                    const uint64_t ad = sw128_desc(smem_u32(asm_ + sa * A_TILE));
-                    const uint64_t bd = sw128_desc(smem_u32(bsm + sb * B_HALF));
-                    const uint32_t idesc_a = make_idesc(false, BM, BN * (S - a));
-                    const uint32_t acc = acc0 + (uint32_t)(a * BN);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {  // 4 x 16 elements (32 bytes) per 64-wide box
-                        const uint64_t o = (uint64_t)(kk * 32) >> 4;
-                        tc_mma<false>(acc, ad + o, bd + o, idesc_a, (c | a | kk) ? 1u : 0u);
+                    for (int s2 = 0; s2 < A_DEPTH; ++s2) {
+                        const int a = A_DEPTH * g + s2;
+                        if (a >= S) break;
+                        // the right slices b = 0..S-1-a lie stacked in the stage (rows 32 b ..), so
+                        // one MMA of N = 32 (S - a) with its accumulator base at column 32 a puts
+                        // A_a B_b^T at columns 32 (a + b): accumulator a + b, for every b at once
+                        const uint64_t ad = sw128_desc(smem_u32(asm_ + sa * A_STAGE + s2 * A_TILE));
+                        const uint32_t idesc_a = make_idesc(false, BM, BN * (S - a));
+                        const uint32_t acc = acc0 + (uint32_t)(a * BN);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {  // 4 x 16 elements (32 bytes) per 64-wide box
+                            const uint64_t o = (uint64_t)(kk * 32) >> 4;
+                            tc_mma<false>(acc, ad + o, bd + o, idesc_a, (c | a | kk) ? 1u : 0u);
+                        }
                     }
                     tc_commit(&aempty[sa]);
                 }
@@ -444,11 +454,11 @@ bool oz_init() {
     return g_ready;
 }
 
-// 3-D map over the digit slices [S][rows_alloc][KP] (BF16): box 64 (K) x box_rows x 1.
-bool slice_map(CUtensorMap* m, const uint16_t* base, int rows, int rows_alloc, int box_rows) {
+// 3-D map over the digit slices [S][rows_alloc][KP] (BF16): box 64 (K) x box_rows x depth.
+bool slice_map(CUtensorMap* m, const uint16_t* base, int rows, int rows_alloc, int box_rows, int depth) {
     cuuint64_t dims[3] = {(cuuint64_t)KP, (cuuint64_t)rows, (cuuint64_t)S};
     cuuint64_t strides[2] = {(cuuint64_t)KP * 2, (cuuint64_t)rows_alloc * KP * 2};
-    cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)box_rows, (cuuint32_t)depth};
     cuuint32_t estr[3] = {1, 1, 1};
     return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -470,7 +480,7 @@ cudaError_t update(cudaStream_t st, int mA, int mB, double* C, int ldc, const Oz
     CUtensorMap ma, mb;
     const uint16_t* sa = same_ab ? ws.sB : ws.sA;
     const int ra = same_ab ? ws.rowsB : ws.rowsA;
-    if (!slice_map(&ma, sa, mA, ra, BM) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN))
+    if (!slice_map(&ma, sa, mA, ra, BM, A_DEPTH) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN, S))
         return cudaErrorInvalidValue;
     UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0,
               sign, accumulate ? 1 : 0, E};

@@ -78,6 +78,27 @@ __device__ __forceinline__ void digits_of(double x, int erow, int (&d)[S]) {
     d[0] = (int)X;
 }
 
+// V 2^e rounded once to FP64 (to nearest, ties to even), its sign flipped by neg (0 or the
+// sign bit): the IEEE 754 binary64 encoding of the normalised magnitude assembled in integer
+// arithmetic, so that of each output element only the final addition runs on the FP64 pipe
+// (an int64 conversion costs as much there as an FMA). |V| < 2^63. Below the normal range
+// the term is dropped (signed zero), above it the result is infinite.
+__device__ __forceinline__ double scaled_i64(long long V, int e, unsigned long long neg) {
+    const unsigned long long sgn = ((unsigned long long)V & 0x8000000000000000ULL) ^ neg;
+    const unsigned long long u = V < 0 ? 0ULL - (unsigned long long)V : (unsigned long long)V;
+    if (u == 0) return __longlong_as_double((long long)sgn);
+    const int lz = __clzll((long long)u);
+    const unsigned long long m = u << lz;   // leading one at bit 63
+    unsigned long long mant = m >> 11;      // 53 bits, leading one at bit 52
+    const unsigned rem = (unsigned)(m & 0x7FFULL);
+    mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ULL))) ? 1ULL : 0ULL;
+    const int be = 1023 + 63 - lz + e;      // biased exponent of the result
+    if (be < 1) return __longlong_as_double((long long)sgn);
+    if (be > 2046) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ULL));
+    // a rounding carry into bit 53 moves into the exponent field
+    return __longlong_as_double((long long)(sgn | (((unsigned long long)(be - 1) << 52) + mant)));
+}
+
 __device__ __forceinline__ uint16_t bf16_int(int d) {
     return __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
 }
@@ -354,7 +375,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     } else if (warp >= 2) {
         // ---- epilogue: a lane quarter q and 8 columns h of each tile ----
         const int q = warp & 3, h = (warp - 2) >> 2;  // h = 0..3
-        const long long sign_bit = args.sign < 0.0 ? (long long)0x8000000000000000ULL : 0LL;
+        const unsigned long long sign_bit = args.sign < 0.0 ? 0x8000000000000000ULL : 0ULL;
         int i = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int m0, n0;
@@ -385,7 +406,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                 if (!rowok || !ok) goto done_tile;
                 // the 8 elements side by side, without branches, so that their conversions and
                 // FP64 operations overlap; only the stores are masked
-                double tv[8], sc[8];
+                double tv[8];
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     long long acc[S];
@@ -395,18 +416,19 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                     const long long hi = acc[0] * 65536 + acc[1] * 256 + acc[2];
                     const long long lo = acc[3] * 16777216 + acc[4] * 65536 + acc[5] * 256 + acc[6];
                     const int sh = (hi >= (1LL << 29) || hi <= -(1LL << 29)) ? 8 : 0;
-                    tv[jj] = (double)(hi * (1LL << (32 - sh)) + (lo >> sh));
-                    // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48), times the sign, as an exact
-                    // power of two built from its bits (below 2^-1022 the term is dropped)
-                    const int e = min(ea + eb[jj] - 62 + sh, 1023);
-                    const long long bits = e < -1022 ? 0LL : ((long long)(e + 1023) << 52) | sign_bit;
-                    sc[jj] = __longlong_as_double(bits);
+                    // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48), times the sign, rounded once
+                    tv[jj] = scaled_i64(hi * (1LL << (32 - sh)) + (lo >> sh), ea + eb[jj] - 62 + sh, sign_bit);
                 }
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     const int j = n0 + 8 * h + jj;
-                    const double f = args.E ? args.E[(size_t)row * args.ldc + min(j, args.mB - 1)] * sc[jj] : sc[jj];
-                    const double out = args.accumulate ? fma(f, tv[jj], cv[jj]) : f * tv[jj];
+                    double out;
+                    if (args.E) {
+                        const double f = args.E[(size_t)row * args.ldc + min(j, args.mB - 1)];
+                        out = args.accumulate ? fma(f, tv[jj], cv[jj]) : f * tv[jj];
+                    } else {
+                        out = args.accumulate ? cv[jj] + tv[jj] : tv[jj];
+                    }
                     if (j < args.mB && !(args.lower && row < args.mB && j > row)) crow[j] = out;
                 }
             }

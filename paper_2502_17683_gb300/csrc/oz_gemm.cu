@@ -239,6 +239,7 @@ struct UpdArgs {
     double sign;   // C (+)= sign * E o (A B^T); +1 or -1
     int accumulate;  // 0: C is overwritten
     const double* E;  // optional Hadamard factor of the product, indexed like C
+    int khalves;      // 64-wide K halves that hold data (1 when the chunk's K <= 64)
 };
 
 // Tile (tm, tn) of the update is skipped when it lies entirely above the diagonal of a
@@ -308,7 +309,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int m0, n0;
             if (!tile_active(args, t, m0, n0)) continue;
-            for (int c = 0; c < 2 && ok; ++c) {
+            for (int c = 0; c < args.khalves && ok; ++c) {
                 const int sb = ib % B_STAGES;
                 if (!oz_wait(&bempty[sb], ((ib / B_STAGES) & 1) ^ 1, 1)) { ok = false; break; }
                 mbar_expect_tx(&bfull[sb], (uint32_t)B_HALF);
@@ -340,7 +341,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             if (i >= 2 && !oz_wait(&accempty[set], ((i >> 1) - 1) & 1, 5)) { ok = false; break; }
             tc_fence_after();
             const uint32_t acc0 = tmem + (uint32_t)(set * ACC_SET);
-            for (int c = 0; c < 2 && ok; ++c) {
+            for (int c = 0; c < args.khalves && ok; ++c) {
                 const int sb = ib % B_STAGES;
                 if (!oz_wait(&bfull[sb], (ib / B_STAGES) & 1, 3)) { ok = false; break; }
                 const uint64_t bd = sw128_desc(smem_u32(bsm + sb * B_HALF));
@@ -496,7 +497,7 @@ void split(cudaStream_t st, const double* src, int ld, int rows, int K, uint16_t
 
 // same_ab: the left operand is the right one (a Gram A^T A): its slices and exponents are
 // read from the right operand's buffers.
-cudaError_t update(cudaStream_t st, int mA, int mB, double* C, int ldc, const OzWs& ws, bool lower,
+cudaError_t update(cudaStream_t st, int mA, int mB, int kb, double* C, int ldc, const OzWs& ws, bool lower,
                    double sign, bool accumulate = true, const double* E = nullptr, bool same_ab = false) {
     if (mA <= 0 || mB <= 0) return cudaSuccess;
     CUtensorMap ma, mb;
@@ -505,7 +506,7 @@ cudaError_t update(cudaStream_t st, int mA, int mB, double* C, int ldc, const Oz
     if (!slice_map(&ma, sa, mA, ra, BM, A_DEPTH) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN, S))
         return cudaErrorInvalidValue;
     UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0,
-              sign, accumulate ? 1 : 0, E};
+              sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1};
     // persistent: one CTA per SM, at most one per active tile
     long active = 0;
     for (int tm = 0; tm < a.tiles_m; ++tm) {
@@ -564,9 +565,9 @@ cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, doubl
         {
             ProfScope prof(st, KC_OZ, (double)mB * (mB + 1) * bw + 2.0 * (mA - mB) * mB * bw);
             k_oz_split_ldl<<<cdiv(mA, SPLIT_ROWS), 128 * SPLIT_ROWS, 0, st>>>(below, R, mA, mB, bw, diag, R, ws.sA,
-                                                                   ws.rowsA, ws.eA, ws.sB, ws.rowsB, ws.eB);
+                                                                           ws.rowsA, ws.eA, ws.sB, ws.rowsB, ws.eB);
             count_launch();
-            e = update(st, mA, mB, Haug + (size_t)j1 * R + j1, R, ws, true, -1.0);
+            e = update(st, mA, mB, bw, Haug + (size_t)j1 * R + j1, R, ws, true, -1.0);
         }
         if (e != cudaSuccess) return e;
     }
@@ -581,7 +582,7 @@ cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int l
         const int kb = std::min(KP, K - k0);
         split(st, A + k0, lda, M, kb, ws.sA, ws.rowsA, ws.eA);
         split(st, B + k0, ldb, N, kb, ws.sB, ws.rowsB, ws.eB);
-        const cudaError_t e = update(st, M, N, C, ldc, ws, lower, sign);
+        const cudaError_t e = update(st, M, N, kb, C, ldc, ws, lower, sign);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -611,7 +612,7 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
         k_oz_split_t<<<cdiv(N, SPLIT_T_ROWS), 128 * SPLIT_T_ROWS, 0, st>>>(B, B2, ldb, N, k0, kb, ws.sB, ws.rowsB,
                                                                            ws.eB);
         count_launch();
-        const cudaError_t e = update(st, M, N, C, ldc, ws, symm, 1.0, k0 > 0, E, same_ab);
+        const cudaError_t e = update(st, M, N, kb, C, ldc, ws, symm, 1.0, k0 > 0, E, same_ab);
         if (e != cudaSuccess) return e;
     }
     if (symm && N > 1) {

@@ -1440,10 +1440,8 @@ int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, d
         else
             CK(ldl_flow(st, R, n, Haug, P, dinv, sc, 0, fsync));
     }
-    {
-        ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
-        CK(bsolve_slices(st, R, n, Haug + RR, A, Haug, bsync));
-    }
+    backward_solve(st, R, n, Haug, A, bsync, emu ? &oz : nullptr);
+    CK(cudaGetLastError());
     DevScalars* h = host_scalars();
     if (!h) return set_err(THC_CPD_ERR_ALLOC, "pinned host buffer allocation failed");
     CK(cudaMemcpyAsync(h, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));

@@ -39,6 +39,11 @@ struct OzWs;
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
                 int* bs_sync, const OzWs* oz = nullptr);
+// The backward solve A L = Y of a factorised Haug (Y in its rows R..R+n): with an emulated
+// factorisation's workspace (oz) and n >= 128, split at a column h0: the trailing block
+// first, the coupling Y1 -= A2 L21 as an emulated product, then the leading block.
+void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int* bs_sync,
+                    const OzWs* oz = nullptr);
 
 // A = M H^-1 for H symmetric positive definite (R x R, lower triangle read) and M (n x R),
 // all device pointers, 1 <= R <= 2048, 1 <= n <= 4096: the solve of thc_cpd_ldl_solve (LDL^T
@@ -81,9 +86,11 @@ void copy_with_maxdiag(cudaStream_t st, int R, const double* H, double* H_out, D
 
 // Backward solve A L = Y (unit lower L in the strictly-lower part of H, R x R; Y and A n x R)
 // by column slices claimed from a ticket (ldl_flow.cu); sync: bsolve_sync_ints(n) ints.
+// ld: row pitch of Y, A and H (0: R), so that a diagonal block of a larger factor can be
+// solved on its own.
 size_t bsolve_sync_ints(int nmax);
 cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, double* A,
-                          const double* H, int* sync);
+                          const double* H, int* sync, int ld = 0);
 
 // lam_r = ||A[:,r]||_2; A[:,r] /= lam_r (lam_r = 0 leaves the column); scratch >= R doubles.
 void normalise_columns(cudaStream_t st, int n, int R, double* A, double* lam, double* scratch);

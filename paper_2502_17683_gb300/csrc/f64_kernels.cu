@@ -562,6 +562,18 @@ k_ldl_update(double* __restrict__ H, const double* __restrict__ P, double* __res
     factor_block(H, R, j1, jbn, dinv, sc, mode, S);
 }
 
+// Column where the backward solve of an emulated factorisation splits (0: it does not).
+// With n >= 128 right-hand sides the solve is bound by the FP64 pipe, so the coupling
+// between the two halves (half of its flops) goes to the tensor cores; with fewer it is
+// bound by each row's substitution chain, which a split only lengthens. Measured on GB300,
+// BF16x3 sweeps/s at (o, v, R_cp) = (50, 250, 1800): 110.0 unsplit, 116.7 with the v modes
+// split, 114.9 with all four; at (30, 150, 1080): 234.1 either way.
+constexpr int kBsSplitMinN = 128;
+int bsolve_split_point(int R, int n) {
+    if (n < kBsSplitMinN || R < 4 * kOzPanel) return 0;
+    return (R / 2 / kOzPanel) * kOzPanel;
+}
+
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
                 int* bs_sync, const OzWs* oz) {
@@ -593,9 +605,28 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
             }
         }
     }
+    backward_solve(st, R, n, Haug, A, bs_sync, oz);
+}
+
+void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int* bs_sync, const OzWs* oz) {
     if (n <= 0) return;
+    double* Y = Haug + (size_t)R * R;
+    const int h0 = oz ? bsolve_split_point(R, n) : 0;
+    if (h0 > 0) {
+        // A = [A1 A2], L = [L11 0; L21 L22]: A2 L22 = Y2, then A1 L11 = Y1 - A2 L21 with the
+        // coupling term (half of the solve's flops) as an emulated tensor-core product
+        const int R2 = R - h0;
+        {
+            ProfScope prof(st, KC_BSOLVE, (double)n * R2 * R2);
+            bsolve_slices(st, R2, n, Y + h0, A + h0, Haug + (size_t)h0 * R + h0, bs_sync, R);
+        }
+        oz_gemm_sub(st, n, h0, R2, A + h0, R, Haug + (size_t)h0 * R, R, Y, R, *oz);
+        ProfScope prof(st, KC_BSOLVE, (double)n * h0 * h0);
+        bsolve_slices(st, h0, n, Y, A, Haug, bs_sync, R);
+        return;
+    }
     ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
-    bsolve_slices(st, R, n, Haug + (size_t)R * R, A, Haug, bs_sync);
+    bsolve_slices(st, R, n, Y, A, Haug, bs_sync);
 }
 
 // ------------------------------------------------------------------------------------

@@ -664,6 +664,7 @@ struct BsArgs {
     double* A;
     const double* H;
     int R, n, nJ, C;
+    int ld;     // row pitch of Yf, A and H (R for a whole solve)
     int* sync;  // [0] ticket, [1] abort, [2] CTAs done, [3 + r] prog of row r; zero at entry
     unsigned long long wait_ns;
 };
@@ -697,13 +698,14 @@ __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
         const int Jlo = c * kSliceBlocks, Jhi = min(a.nJ, Jlo + kSliceBlocks);
         const int q = cs + tid;  // this thread's column
         const bool qv = q < ce;
-        double y = qv ? a.Yf[(size_t)r * R + q] : 0.0;
+        const size_t ld = a.ld;
+        double y = qv ? a.Yf[(size_t)r * ld + q] : 0.0;
         // this warp's diagonal block (if it owns one): column `lane` of L_JJ, in registers
         const int Jw = Jlo + w, c0w = Jw * BB, jbw = min(BB, R - c0w);
         double lc[BB];
 #pragma unroll
         for (int k = 0; k < BB; ++k)
-            lc[k] = (Jw < Jhi && k > lane && k < jbw) ? __ldg(a.H + (size_t)(c0w + k) * R + c0w + lane)
+            lc[k] = (Jw < Jhi && k > lane && k < jbw) ? __ldg(a.H + (size_t)(c0w + k) * ld + c0w + lane)
                                                      : 0.0;
         // a_K of the higher blocks, as they are published; the L rows are loaded first
         bool good = true;
@@ -713,7 +715,7 @@ __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
             double hv[BB], av[BB];
 #pragma unroll
             for (int k = 0; k < BB; ++k)
-                hv[k] = (k < kb && qv) ? __ldg(a.H + (size_t)(k0 + k) * R + q) : 0.0;
+                hv[k] = (k < kb && qv) ? __ldg(a.H + (size_t)(k0 + k) * ld + q) : 0.0;
             if (K < published) {
                 if (tid == 0) {
                     const int* const pc[1] = {&prog[r]};
@@ -728,7 +730,7 @@ __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
                 if (!good) break;
             }
 #pragma unroll
-            for (int k = 0; k < BB; ++k) av[k] = k < kb ? __ldcg(a.A + (size_t)r * R + k0 + k) : 0.0;
+            for (int k = 0; k < BB; ++k) av[k] = k < kb ? __ldcg(a.A + (size_t)r * ld + k0 + k) : 0.0;
             y -= dot32(av, hv);
         }
         if (!good) break;
@@ -748,7 +750,7 @@ __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
                 }
                 y = v;
                 as[b][lane] = v;
-                if (lane < jb) a.A[(size_t)r * R + c0 + lane] = v;
+                if (lane < jb) a.A[(size_t)r * ld + c0 + lane] = v;
             }
             __syncthreads();
             if (mine) {
@@ -760,7 +762,7 @@ __global__ void __launch_bounds__(kBsThreads) k_bsolve_slices(BsArgs a) {
                 double hv[BB];
 #pragma unroll
                 for (int k = 0; k < BB; ++k)
-                    hv[k] = k < jb ? __ldg(a.H + (size_t)(c0 + k) * R + q) : 0.0;
+                    hv[k] = k < jb ? __ldg(a.H + (size_t)(c0 + k) * ld + q) : 0.0;
                 y -= dot32(as[b], hv);
             }
         }
@@ -1016,10 +1018,10 @@ cudaError_t ldl_flow_panel(cudaStream_t st, int R, int n, int j0, int bw, double
 size_t bsolve_sync_ints(int nmax) { return 3 + (size_t)nmax; }
 
 cudaError_t bsolve_slices(cudaStream_t st, int R, int n, const double* Yf, double* A,
-                          const double* H, int* sync) {
+                          const double* H, int* sync, int ld) {
     if (n <= 0) return cudaSuccess;
     const int nJ = cdiv(R, BB), C = cdiv(R, kSlice);
-    BsArgs a{Yf, A, H, R, n, nJ, C, sync, t_wait_ns};
+    BsArgs a{Yf, A, H, R, n, nJ, C, ld > 0 ? ld : R, sync, t_wait_ns};
     const int grid = std::min(n * C, num_sms() * 4);
     k_bsolve_slices<<<grid, kBsThreads, 0, st>>>(a);
     count_launch();

@@ -54,7 +54,8 @@ bool oz_prepare(int R, int n);
 // M in the rest), same result layout as ldl_flow: panels of kOzPanel columns factorised by
 // the dataflow kernel (ldl_flow_panel), each followed by the emulated FP64 trailing update
 //   Haug[i][j] -= sum_{k in panel} L[i][k] D[k] L[j][k]   (j <= i for H rows; all j < R for M rows)
-// of the rows and columns after the panel. P: R x R (X = L D of the diagonal blocks), dinv:
+// of the rows and columns after the panel; the last few hundred columns (oz_gemm.cu,
+// kTailCols) as one dataflow factorisation of the trailing block. P: R x R (X = L D of the diagonal blocks), dinv:
 // R, sync: flow_sync_ints(R, n) ints (zero; left zero).
 // max_ctas > 0: the panels run on at most that many CTAs (problems side by side).
 cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, double* dinv,
@@ -74,6 +75,12 @@ cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int l
 cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const double* A, int lda,
                      const double* B, const double* B2, int ldb, double* C, int ldc, const double* E,
                      bool symm, const OzWs& ws);
+
+// C (M x N, ldc) -= A B for row-major FP64 A (M x K, lda) and B (K x N, ldb), emulated in K
+// chunks of kOzPanel (the coupling term of a split backward solve). ws must hold M (rowsA)
+// and N (rowsB) rows.
+cudaError_t oz_gemm_sub(cudaStream_t st, int M, int N, int K, const double* A, int lda, const double* B,
+                        int ldb, double* C, int ldc, const OzWs& ws);
 
 // Device error word of the emulated-product kernel (bounded waits that gave up); read and
 // clear.

@@ -124,9 +124,10 @@ def fp64_peaks(dev, sm_max_mhz):
 LDL_SOURCES = [os.path.join("paper_2502_17683_gb300", "csrc", f)
                for f in ("ldl_flow.cu", "ldl_common.cuh", "common.cuh")]
 LDL_TRAFFIC = {
-    # 60 panel launches of sweep 1 (profiles/ldl_flow_panels_o50_v250_Rt1200_R1800_emulated.md)
-    ("c3", "emulated"): {"bytes_per_launch": 1176789,
-                         "sha256": "e9e1311de890e5114fe0a6a110f6f970d5205ea5c7d6d1e32265edbc54396101"},
+    # 44 launches of sweep 1: 40 panels and 4 tails
+    # (profiles/ldl_flow_panels_o50_v250_Rt1200_R1800_emulated.md)
+    ("c3", "emulated"): {"bytes_per_launch": 1582598,
+                         "sha256": "57c4b1c3f6b6a30ce677f5e61077b862c4fbc7c2d464ae8a9c7cf63a08a3768c"},
 }
 
 
@@ -705,7 +706,7 @@ def main():
     # the LDL^T is one launch per solve on the dataflow path; per launch = per solve
     kernel = {"cholesky": "k_ldl_flow (LDL^T + forward solve, one launch per mode)"
               if ldl_path == "dataflow" else
-              ("k_ldl_flow panels of the emulated two-level LDL^T (one launch per 128 columns)"
+              ("k_ldl_flow panels of the emulated two-level LDL^T (one launch per 128 columns, one for the last 520)"
                if ldl_path == "emulated" else "blocked LDL^T launches (per mode)"),
               "backward_solve": "k_bsolve_slices", "fp64_gemm": "k_dgemm",
               "tc_gemm": "k_tc_gemm", "elementwise": "element-wise kernels",

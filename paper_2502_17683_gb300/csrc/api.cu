@@ -273,7 +273,9 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     // never inside a capture
     const int ldl = opts ? opts->ldl : THC_CPD_LDL_AUTO;
     c.emulated = use_emulated_ldl(ldl, R, nmax) && oz_prepare(R, s.o) && oz_prepare(R, s.v);
-    if (c.emulated) bytes += oz_ws_bytes(std::max(R + nmax, Rt), R);
+    int oz_ra = std::max(R + nmax, Rt), oz_rb = R;
+    if (c.emulated) bsolve_ws_rows(R, nmax, &oz_ra, &oz_rb);
+    if (c.emulated) bytes += oz_ws_bytes(oz_ra, oz_rb);
     CK(cudaMallocAsync(&c.block, bytes, c.st));
     Arena ar;
     ar.base = (char*)c.block;
@@ -313,7 +315,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
         mixed_ws_carve(c.mx, ar, tf32, s.o, s.v, Rt, R);
         CK(mixed_setup(c.mx, c.st, Xo, Xv, Z));
     }
-    if (c.emulated) oz_ws_carve(c.oz, ar, std::max(R + nmax, Rt), R);
+    if (c.emulated) oz_ws_carve(c.oz, ar, oz_ra, oz_rb);
     fill(c.st, c.ones, R, 1.0);
     c.dataflow = c.emulated || ldl == THC_CPD_LDL_DATAFLOW ||
                  (ldl == THC_CPD_LDL_AUTO && !(need & NEED_BATCHED));
@@ -1364,7 +1366,11 @@ extern "C" thc_cpd_status thc_cpd_emulated_gemm(int M, int N, int K, const doubl
     if (!oz_available())
         return set_err(THC_CPD_ERR_UNSUPPORTED, "the emulated product needs an sm_103 device");
     cudaStream_t st = stream_of(opts);
-    const size_t bytes = oz_ws_bytes(M, N);
+    // room for every K chunk's digits (one update launch) unless that would pass 65536 rows
+    const long nch = cdiv(K, kOzPanel);
+    const bool all = nch * (M + N) <= 65536;
+    const int rowsA = all ? (int)(nch * M) : M, rowsB = all ? (int)(nch * N) : N;
+    const size_t bytes = oz_ws_bytes(rowsA, rowsB);
     struct Ws {
         void* p = nullptr;
         cudaStream_t st;
@@ -1378,7 +1384,7 @@ extern "C" thc_cpd_status thc_cpd_emulated_gemm(int M, int N, int K, const doubl
     ar.base = (char*)ws.p;
     ar.cap = bytes;
     OzWs oz;
-    oz_ws_carve(oz, ar, M, N);
+    oz_ws_carve(oz, ar, rowsA, rowsB);
     CK(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * N, M, st));
     CK(oz_gemm(st, M, N, K, A, lda, B, ldb, C, ldc, 1.0, false, oz));
     CK(cudaStreamSynchronize(st));
@@ -1396,7 +1402,9 @@ int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, d
     const size_t RR = (size_t)R * R, nR = (size_t)n * R;
     const bool emu = use_emulated_ldl(ldl, R, n) && !tasks &&
                      oz_prepare(R, n);
-    size_t bytes = (emu ? oz_ws_bytes(R + n, R) : 0) + Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
+    int oz_ra = R + n, oz_rb = R;
+    if (emu) bsolve_ws_rows(R, n, &oz_ra, &oz_rb);
+    size_t bytes = (emu ? oz_ws_bytes(oz_ra, oz_rb) : 0) + Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
                    Arena::need<double>(std::max(RR, nR)) + Arena::need<double>(R) +
                    Arena::need<int>(flow_sync_ints(R, n)) + Arena::need<int>(bsolve_sync_ints(n)) +
                    Arena::need<DevScalars>(1) + Arena::need<short>(4 * (size_t)std::max(ntasks, 1));
@@ -1424,7 +1432,7 @@ int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, d
     DevScalars* sc = ar.take<DevScalars>(1);
     void* dtasks = ar.take<short>(4 * (size_t)std::max(ntasks, 1));
     OzWs oz;
-    if (emu) oz_ws_carve(oz, ar, R + n, R);
+    if (emu) oz_ws_carve(oz, ar, oz_ra, oz_rb);
     CK(cudaMemsetAsync(fsync, 0, sizeof(int) * flow_sync_ints(R, n), st));
     CK(cudaMemsetAsync(bsync, 0, sizeof(int) * bsolve_sync_ints(n), st));
     scalars_init(st, sc, 0.0);

@@ -40,10 +40,16 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
                 int* bs_sync, const OzWs* oz = nullptr);
 // The backward solve A L = Y of a factorised Haug (Y in its rows R..R+n): with an emulated
-// factorisation's workspace (oz) and n >= 128, split at a column h0: the trailing block
-// first, the coupling Y1 -= A2 L21 as an emulated product, then the leading block.
+// factorisation's workspace (oz) and n >= 128, a block of >= 768 columns is split at a
+// column h0: the trailing block first, the coupling Y1 -= A2 L21 as an emulated product,
+// then the leading block, each of them split again by the same rule.
 void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int* bs_sync,
                     const OzWs* oz = nullptr);
+// Raises *rowsA / *rowsB (emulated-product workspace rows, oz_ws_carve) to what the split
+// backward solve of an R x R factor with up to nmax right-hand sides needs to form each
+// coupling product in one launch (all its K chunks' digits at once); with fewer rows the
+// products run chunk by chunk.
+void bsolve_ws_rows(int R, int nmax, int* rowsA, int* rowsB);
 
 // A = M H^-1 for H symmetric positive definite (R x R, lower triangle read) and M (n x R),
 // all device pointers, 1 <= R <= 2048, 1 <= n <= 4096: the solve of thc_cpd_ldl_solve (LDL^T

@@ -562,16 +562,19 @@ k_ldl_update(double* __restrict__ H, const double* __restrict__ P, double* __res
     factor_block(H, R, j1, jbn, dinv, sc, mode, S);
 }
 
-// Column where the backward solve of an emulated factorisation splits (0: it does not).
-// With n >= 128 right-hand sides the solve is bound by the FP64 pipe, so the coupling
-// between the two halves (half of its flops) goes to the tensor cores; with fewer it is
-// bound by each row's substitution chain, which a split only lengthens. Measured on GB300,
-// BF16x3 sweeps/s at (o, v, R_cp) = (50, 250, 1800): 110.0 unsplit, 116.7 with the v modes
-// split, 114.9 with all four; at (30, 150, 1080): 234.1 either way.
+// Column where a block of m columns of the backward solve of an emulated factorisation
+// splits (0: it does not). With n >= 128 right-hand sides the solve is bound by the FP64
+// pipe, so the coupling between the two halves (half of the block's flops) goes to the
+// tensor cores; with fewer it is bound by each row's substitution chain, which a split only
+// lengthens. Blocks of fewer than 768 columns are not split (their coupling products are
+// too small to fill the GPU). Measured on GB300, BF16x3 sweeps/s at (o, v, R_cp) = (50,
+// 250, 1800): 110.0 unsplit, 116.3 halves, 118.5 quarters, 118.4 eighths (116.7 with the
+// o modes split as well, n = 50: 114.9); at (30, 150, 1080): 232.9 halves, 230.5 quarters.
 constexpr int kBsSplitMinN = 128;
-int bsolve_split_point(int R, int n) {
-    if (n < kBsSplitMinN || R < 4 * kOzPanel) return 0;
-    return (R / 2 / kOzPanel) * kOzPanel;
+constexpr int kBsSplitMinCols = 6 * kOzPanel;
+int bsolve_split_point(int m, int n) {
+    if (n < kBsSplitMinN || m < kBsSplitMinCols) return 0;
+    return (m / 2 / kOzPanel) * kOzPanel;
 }
 
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
@@ -608,25 +611,51 @@ void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* 
     backward_solve(st, R, n, Haug, A, bs_sync, oz);
 }
 
-void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int* bs_sync, const OzWs* oz) {
-    if (n <= 0) return;
+namespace {
+// Columns [c0, c0 + m) of A L = Y (L, Y, A with row pitch R), the columns after them already
+// applied to Y: the block as one solve, or split at h into its trailing and leading parts
+// with the coupling Y[:, c0 .. c0 + h) -= A[:, c0 + h .. c0 + m) L[c0 + h .. c0 + m, c0 .. c0 + h)
+// as an emulated product between them.
+void bsolve_block(cudaStream_t st, int R, int c0, int m, int n, double* Haug, double* A, int* bs_sync,
+                  const OzWs* oz) {
     double* Y = Haug + (size_t)R * R;
-    const int h0 = oz ? bsolve_split_point(R, n) : 0;
-    if (h0 > 0) {
-        // A = [A1 A2], L = [L11 0; L21 L22]: A2 L22 = Y2, then A1 L11 = Y1 - A2 L21 with the
-        // coupling term (half of the solve's flops) as an emulated tensor-core product
-        const int R2 = R - h0;
-        {
-            ProfScope prof(st, KC_BSOLVE, (double)n * R2 * R2);
-            bsolve_slices(st, R2, n, Y + h0, A + h0, Haug + (size_t)h0 * R + h0, bs_sync, R);
-        }
-        oz_gemm_sub(st, n, h0, R2, A + h0, R, Haug + (size_t)h0 * R, R, Y, R, *oz);
-        ProfScope prof(st, KC_BSOLVE, (double)n * h0 * h0);
-        bsolve_slices(st, h0, n, Y, A, Haug, bs_sync, R);
+    const int h = oz ? bsolve_split_point(m, n) : 0;
+    if (h == 0) {
+        ProfScope prof(st, KC_BSOLVE, (double)n * m * m);
+        bsolve_slices(st, m, n, Y + c0, A + c0, Haug + (size_t)c0 * R + c0, bs_sync, R);
         return;
     }
-    ProfScope prof(st, KC_BSOLVE, (double)n * R * R);
-    bsolve_slices(st, R, n, Y, A, Haug, bs_sync);
+    bsolve_block(st, R, c0 + h, m - h, n, Haug, A, bs_sync, oz);
+    oz_gemm_sub(st, n, h, m - h, A + c0 + h, R, Haug + (size_t)(c0 + h) * R + c0, R, Y + c0, R, *oz);
+    bsolve_block(st, R, c0, h, n, Haug, A, bs_sync, oz);
+}
+}  // namespace
+
+namespace {
+void coupling_rows(int m, int n, long* ra, long* rb) {
+    const int h = bsolve_split_point(m, n);
+    if (h == 0) return;
+    const long nch = cdiv(m - h, kOzPanel);
+    *ra = std::max(*ra, nch * n);
+    *rb = std::max(*rb, nch * h);
+    coupling_rows(m - h, n, ra, rb);
+    coupling_rows(h, n, ra, rb);
+}
+}  // namespace
+
+void bsolve_ws_rows(int R, int nmax, int* rowsA, int* rowsB) {
+    long ra = 0, rb = 0;
+    coupling_rows(R, nmax, &ra, &rb);
+    *rowsA = std::max<long>(*rowsA, ra);
+    *rowsB = std::max<long>(*rowsB, rb);
+}
+
+void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int* bs_sync, const OzWs* oz) {
+    if (n <= 0) return;
+    // A = [A1 A2], L = [L11 0; L21 L22]: A2 L22 = Y2, then A1 L11 = Y1 - A2 L21 with the
+    // coupling term (half of the block's flops) as an emulated tensor-core product, each
+    // half split again while it is large enough
+    bsolve_block(st, R, 0, R, n, Haug, A, bs_sync, oz);
 }
 
 // ------------------------------------------------------------------------------------

@@ -127,13 +127,19 @@ __device__ __forceinline__ void store_digits(double x, int erow, uint16_t* __res
 constexpr int SPLIT_ROWS = 2;  // rows per block of the row splits: 128 threads, one value each, per row
 
 // Row r < rows: the values src[r * ld + k] (k < K, zero beyond), their row exponent and
-// their S digit slices out[a][r][k] (k < KP). 128 threads per row, one value each.
+// their S digit slices out[a][r][k] (k < KP). 128 threads per row, one value each. K chunk
+// c = blockIdx.y (values KP c ..) goes to slices out[S c + a] and exponents exps[rows_alloc c ..].
 __global__ void __launch_bounds__(128 * SPLIT_ROWS)
 k_oz_split(const double* __restrict__ src, int ld, int rows, int K, uint16_t* __restrict__ out,
            int rows_alloc, int* __restrict__ exps) {
     __shared__ int sh[4 * SPLIT_ROWS];
     const int group = threadIdx.x >> 7, k = threadIdx.x & 127, wig = k >> 5;
     const int r = blockIdx.x * SPLIT_ROWS + group;
+    const int ch = blockIdx.y;
+    src += (size_t)ch * KP;
+    K -= ch * KP;
+    out += (size_t)ch * S * rows_alloc * KP;
+    exps += (size_t)ch * rows_alloc;
     const bool live = r < rows;
     const double x = (live && k < K) ? src[(size_t)r * ld + k] : 0.0;
     const int erow = group_row_exp(exp_of(x), sh, group, wig);
@@ -182,12 +188,18 @@ constexpr int SPLIT_T_ROWS = 8;  // output rows per block of the transposed spli
 // K x N row-major matrix S (ld), times S2 element by element when given (a Hadamard
 // operand): values S[(k0 + k) * ld + n] (* S2[...]). A 128 x 8 slab is staged in shared
 // memory (8 consecutive columns per source row), then 128 threads per output row form its
-// exponent and digits, one value each.
+// exponent and digits, one value each. Chunk c = blockIdx.y takes rows k0 + KP c .. (of the
+// kb left) into slices out[S c + a] and exponents exps[rows_alloc c ..].
 __global__ void __launch_bounds__(128 * SPLIT_T_ROWS)
 k_oz_split_t(const double* __restrict__ S, const double* __restrict__ S2, int ld, int N, int k0,
              int kb, uint16_t* __restrict__ out, int rows_alloc, int* __restrict__ exps) {
     __shared__ double tile[KP][SPLIT_T_ROWS + 1];
     __shared__ int sh[4 * SPLIT_T_ROWS];
+    const int ch = blockIdx.y;
+    k0 += ch * KP;
+    kb -= ch * KP;
+    out += (size_t)ch * kOzSlices * rows_alloc * KP;  // (S is the source matrix here)
+    exps += (size_t)ch * rows_alloc;
     const int n0 = blockIdx.x * SPLIT_T_ROWS;
     {
         const int kk = threadIdx.x / SPLIT_T_ROWS, nn = threadIdx.x % SPLIT_T_ROWS;
@@ -239,7 +251,9 @@ struct UpdArgs {
     double sign;   // C (+)= sign * E o (A B^T); +1 or -1
     int accumulate;  // 0: C is overwritten
     const double* E;  // optional Hadamard factor of the product, indexed like C
-    int khalves;      // 64-wide K halves that hold data (1 when the chunk's K <= 64)
+    int khalves;      // 64-wide K halves that hold data in the last chunk (1 when its K <= 64)
+    int nchunks;      // K chunks of KP; chunk c's slices are planes S c .. S c + S - 1 of the maps
+    int eA_cs, eB_cs; // offsets between the chunks' exponent rows
 };
 
 // Tile (tm, tn) of the update is skipped when it lies entirely above the diagonal of a
@@ -309,21 +323,24 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int m0, n0;
             if (!tile_active(args, t, m0, n0)) continue;
-            for (int c = 0; c < args.khalves && ok; ++c) {
+            for (int ch = 0; ch < args.nchunks && ok; ++ch) {
+            const int nh = ch == args.nchunks - 1 ? args.khalves : 2;
+            for (int c = 0; c < nh && ok; ++c) {
                 const int sb = ib % B_STAGES;
                 if (!oz_wait(&bempty[sb], ((ib / B_STAGES) & 1) ^ 1, 1)) { ok = false; break; }
                 mbar_expect_tx(&bfull[sb], (uint32_t)B_HALF);
                 // all S right slices in one box, stacked (slice b at rows 32 b ..)
-                tma_load_3d(bsm + sb * B_HALF, &mapB, &bfull[sb], 64 * c, n0, 0);
+                tma_load_3d(bsm + sb * B_HALF, &mapB, &bfull[sb], 64 * c, n0, S * ch);
                 ++ib;
                 for (int g = 0; g < A_GROUPS; ++g, ++ia) {
-                    // slices 2g, 2g + 1 in one box (past the last slice the box is zero-filled;
-                    // its bytes still count)
+                    // slices 2g, 2g + 1 in one box (past the chunk's last slice the box holds
+                    // the next chunk's first, or zeros; its bytes still count, the MMAs skip it)
                     const int sa = ia % A_STAGES;
                     if (!oz_wait(&aempty[sa], ((ia / A_STAGES) & 1) ^ 1, 1)) { ok = false; break; }
                     mbar_expect_tx(&afull[sa], (uint32_t)A_STAGE);
-                    tma_load_3d(asm_ + sa * A_STAGE, &mapA, &afull[sa], 64 * c, m0, A_DEPTH * g);
+                    tma_load_3d(asm_ + sa * A_STAGE, &mapA, &afull[sa], 64 * c, m0, S * ch + A_DEPTH * g);
                 }
+            }
             }
         }
         // every copy issued has landed before the CTA may leave
@@ -336,12 +353,15 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int m0, n0;
             if (!tile_active(args, t, m0, n0)) continue;
+            // one accumulator set per (tile, K chunk), alternating
+            for (int ch = 0; ch < args.nchunks && ok; ++ch) {
+            const int nh = ch == args.nchunks - 1 ? args.khalves : 2;
             const int set = i & 1;
-            // accumulator set `set` is free once the epilogue has drained tile i - 2
+            // accumulator set `set` is free once the epilogue has drained tile-chunk i - 2
             if (i >= 2 && !oz_wait(&accempty[set], ((i >> 1) - 1) & 1, 5)) { ok = false; break; }
             tc_fence_after();
             const uint32_t acc0 = tmem + (uint32_t)(set * ACC_SET);
-            for (int c = 0; c < args.khalves && ok; ++c) {
+            for (int c = 0; c < nh && ok; ++c) {
                 const int sb = ib % B_STAGES;
                 if (!oz_wait(&bfull[sb], (ib / B_STAGES) & 1, 3)) { ok = false; break; }
                 const uint64_t bd = sw128_desc(smem_u32(bsm + sb * B_HALF));
@@ -372,6 +392,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             }
             tc_commit(&accfull[set]);  // also after a failed wait: arrives once the issued MMAs are done
             ++i;
+            }
         }
     } else if (warp >= 2) {
         // ---- epilogue: a lane quarter q and 8 columns h of each tile ----
@@ -381,12 +402,16 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int m0, n0;
             if (!tile_active(args, t, m0, n0)) continue;
+            for (int ch = 0; ch < args.nchunks; ++ch) {
+            // chunks after the first add to what the previous one wrote (same thread, same elements)
+            const bool accum = args.accumulate || ch > 0;
+            const int* eBc = args.eB + (size_t)ch * args.eB_cs;
             const int set = i & 1;
             const bool ok = oz_wait(&accfull[set], (i >> 1) & 1, 6);
             tc_fence_after();
             const int row = m0 + 32 * q + lane;
             const bool rowok = row < args.mA;
-            const int ea = rowok ? args.eA[row] : 0;
+            const int ea = rowok ? args.eA[(size_t)ch * args.eA_cs + row] : 0;
             double* crow = args.C + (size_t)row * args.ldc;
             const uint32_t tbase = tmem + (uint32_t)(set * ACC_SET + 8 * h) + ((uint32_t)(32 * q) << 16);
             {
@@ -400,8 +425,8 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     const int j = n0 + 8 * h + jj;
-                    cv[jj] = (ok && rowok && j < args.mB && args.accumulate) ? crow[j] : 0.0;
-                    eb[jj] = j < args.mB ? __ldg(args.eB + j) : 0;
+                    cv[jj] = (ok && rowok && j < args.mB && accum) ? crow[j] : 0.0;
+                    eb[jj] = j < args.mB ? __ldg(eBc + j) : 0;
                 }
                 tmem_ld_wait(r);
                 if (!rowok || !ok) goto done_tile;
@@ -426,9 +451,9 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
                     double out;
                     if (args.E) {
                         const double f = args.E[(size_t)row * args.ldc + min(j, args.mB - 1)];
-                        out = args.accumulate ? fma(f, tv[jj], cv[jj]) : f * tv[jj];
+                        out = accum ? fma(f, tv[jj], cv[jj]) : f * tv[jj];
                     } else {
-                        out = args.accumulate ? cv[jj] + tv[jj] : tv[jj];
+                        out = accum ? cv[jj] + tv[jj] : tv[jj];
                     }
                     if (j < args.mB && !(args.lower && row < args.mB && j > row)) crow[j] = out;
                 }
@@ -439,6 +464,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[set]);
             ++i;
+            }
         }
     }
     tc_fence_before();
@@ -477,9 +503,11 @@ bool oz_init() {
     return g_ready;
 }
 
-// 3-D map over the digit slices [S][rows_alloc][KP] (BF16): box 64 (K) x box_rows x depth.
-bool slice_map(CUtensorMap* m, const uint16_t* base, int rows, int rows_alloc, int box_rows, int depth) {
-    cuuint64_t dims[3] = {(cuuint64_t)KP, (cuuint64_t)rows, (cuuint64_t)S};
+// 3-D map over the digit slices [planes][rows_alloc][KP] (BF16; S planes per K chunk):
+// box 64 (K) x box_rows x depth.
+bool slice_map(CUtensorMap* m, const uint16_t* base, int rows, int rows_alloc, int box_rows, int depth,
+               int planes = S) {
+    cuuint64_t dims[3] = {(cuuint64_t)KP, (cuuint64_t)rows, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)KP * 2, (cuuint64_t)rows_alloc * KP * 2};
     cuuint32_t box[3] = {64, (cuuint32_t)box_rows, (cuuint32_t)depth};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -497,16 +525,20 @@ void split(cudaStream_t st, const double* src, int ld, int rows, int K, uint16_t
 
 // same_ab: the left operand is the right one (a Gram A^T A): its slices and exponents are
 // read from the right operand's buffers.
+// nchunks > 1: K = KP (nchunks - 1) + kb in one launch, the chunks' slices laid out
+// [chunk][S][mA][KP] and [chunk][S][mB][KP] (exponents [chunk][mA], [chunk][mB]).
 cudaError_t update(cudaStream_t st, int mA, int mB, int kb, double* C, int ldc, const OzWs& ws, bool lower,
-                   double sign, bool accumulate = true, const double* E = nullptr, bool same_ab = false) {
+                   double sign, bool accumulate = true, const double* E = nullptr, bool same_ab = false,
+                   int nchunks = 1) {
     if (mA <= 0 || mB <= 0) return cudaSuccess;
     CUtensorMap ma, mb;
     const uint16_t* sa = same_ab ? ws.sB : ws.sA;
-    const int ra = same_ab ? ws.rowsB : ws.rowsA;
-    if (!slice_map(&ma, sa, mA, ra, BM, A_DEPTH) || !slice_map(&mb, ws.sB, mB, ws.rowsB, BN, S))
+    const int ra = nchunks > 1 ? mA : (same_ab ? ws.rowsB : ws.rowsA);
+    const int rb = nchunks > 1 ? mB : ws.rowsB;
+    if (!slice_map(&ma, sa, mA, ra, BM, A_DEPTH, S * nchunks) || !slice_map(&mb, ws.sB, mB, rb, BN, S, S * nchunks))
         return cudaErrorInvalidValue;
     UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0,
-              sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1};
+              sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1, nchunks, ra, rb};
     // persistent: one CTA per SM, at most one per active tile
     long active = 0;
     for (int tm = 0; tm < a.tiles_m; ++tm) {
@@ -593,6 +625,15 @@ cudaError_t oz_gemm(cudaStream_t st, int M, int N, int K, const double* A, int l
                     int ldb, double* C, int ldc, double sign, bool lower, const OzWs& ws) {
     if (!oz_init()) return cudaErrorNotSupported;
     if (M > ws.rowsA || N > ws.rowsB) return cudaErrorInvalidValue;
+    const int nch = cdiv(K, KP);
+    if (nch > 1 && (long)nch * M <= ws.rowsA && (long)nch * N <= ws.rowsB) {
+        // every chunk's digits at once, then one update launch over all chunks
+        k_oz_split<<<dim3(cdiv(M, SPLIT_ROWS), nch), 128 * SPLIT_ROWS, 0, st>>>(A, lda, M, K, ws.sA, M, ws.eA);
+        k_oz_split<<<dim3(cdiv(N, SPLIT_ROWS), nch), 128 * SPLIT_ROWS, 0, st>>>(B, ldb, N, K, ws.sB, N, ws.eB);
+        count_launch(2);
+        const cudaError_t e = update(st, M, N, K - KP * (nch - 1), C, ldc, ws, lower, sign, true, nullptr, false, nch);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     for (int k0 = 0; k0 < K; k0 += KP) {
         const int kb = std::min(KP, K - k0);
         split(st, A + k0, lda, M, kb, ws.sA, ws.rowsA, ws.eA);
@@ -613,6 +654,23 @@ cudaError_t oz_dgemm(cudaStream_t st, bool trans_a, int M, int N, int K, const d
     ProfScope prof(st, KC_OZ, (symm ? 1.0 : 2.0) * M * (double)N * K);
     // A^T A (a Gram): one operand split serves both sides
     const bool same_ab = trans_a && A == B && !B2 && lda == ldb && M == N;
+    const int nch = cdiv(K, KP);
+    if (nch > 1 && (same_ab || (long)nch * M <= ws.rowsA) && (long)nch * N <= ws.rowsB) {
+        // every chunk's digits at once, then one update launch over all chunks
+        if (!same_ab) {
+            if (trans_a)
+                k_oz_split_t<<<dim3(cdiv(M, SPLIT_T_ROWS), nch), 128 * SPLIT_T_ROWS, 0, st>>>(A, nullptr, lda, M, 0, K,
+                                                                                             ws.sA, M, ws.eA);
+            else
+                k_oz_split<<<dim3(cdiv(M, SPLIT_ROWS), nch), 128 * SPLIT_ROWS, 0, st>>>(A, lda, M, K, ws.sA, M, ws.eA);
+            count_launch();
+        }
+        k_oz_split_t<<<dim3(cdiv(N, SPLIT_T_ROWS), nch), 128 * SPLIT_T_ROWS, 0, st>>>(B, B2, ldb, N, 0, K, ws.sB,
+                                                                                     N, ws.eB);
+        count_launch();
+        const cudaError_t e = update(st, M, N, K - KP * (nch - 1), C, ldc, ws, symm, 1.0, false, E, same_ab, nch);
+        if (e != cudaSuccess) return e;
+    } else
     for (int k0 = 0; k0 < K; k0 += KP) {
         const int kb = std::min(KP, K - k0);
         if (same_ab) {
@@ -644,6 +702,16 @@ cudaError_t oz_gemm_sub(cudaStream_t st, int M, int N, int K, const double* A, i
     if (!oz_init()) return cudaErrorNotSupported;
     if (M > ws.rowsA || N > ws.rowsB) return cudaErrorInvalidValue;
     ProfScope prof(st, KC_OZ, 2.0 * M * (double)N * K);
+    const int nch = cdiv(K, KP);
+    if (nch > 1 && (long)nch * M <= ws.rowsA && (long)nch * N <= ws.rowsB) {
+        // every chunk's digits at once, then one update launch over all chunks
+        k_oz_split<<<dim3(cdiv(M, SPLIT_ROWS), nch), 128 * SPLIT_ROWS, 0, st>>>(A, lda, M, K, ws.sA, M, ws.eA);
+        k_oz_split_t<<<dim3(cdiv(N, SPLIT_T_ROWS), nch), 128 * SPLIT_T_ROWS, 0, st>>>(B, nullptr, ldb, N, 0, K,
+                                                                                     ws.sB, N, ws.eB);
+        count_launch(2);
+        const cudaError_t e = update(st, M, N, K - KP * (nch - 1), C, ldc, ws, false, -1.0, true, nullptr, false, nch);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     for (int k0 = 0; k0 < K; k0 += KP) {
         const int kb = std::min(KP, K - k0);
         split(st, A + k0, lda, M, kb, ws.sA, ws.rowsA, ws.eA);

@@ -81,9 +81,10 @@ def _normal_equations(R, n, seed, dims=(9, 40, 9)):
     return H, rng.standard_normal((n, R))
 
 
-# (720, 200), (1080, 150) and (1800, 250) take the split backward solve (n >= 128, R >= 512)
-@pytest.mark.parametrize("R,n", [(129, 3), (300, 50), (300, 200), (720, 100), (720, 200), (1080, 150),
-                                 (1800, 250)])
+# the backward solve splits blocks of >= 768 columns when n >= 128: (800, 200) and (1080, 150)
+# once, (1800, 250) twice (quarters); (720, 200) stays whole
+@pytest.mark.parametrize("R,n", [(129, 3), (300, 50), (300, 200), (720, 100), (720, 200), (800, 200),
+                                 (1080, 150), (1800, 250)])
 def test_emulated_ldl_solve_matches_oracle(api, R, n):
     H, M = _normal_equations(R, n, seed=R)
     Aref, used_ref = O.solve_normal_equations(M, H)

@@ -274,8 +274,9 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     const int ldl = opts ? opts->ldl : THC_CPD_LDL_AUTO;
     c.emulated = use_emulated_ldl(ldl, R, nmax) && oz_prepare(R, s.o) && oz_prepare(R, s.v);
     int oz_ra = std::max(R + nmax, Rt), oz_rb = R;
-    if (c.emulated) bsolve_ws_rows(R, nmax, &oz_ra, &oz_rb);
-    if (c.emulated) bytes += oz_ws_bytes(oz_ra, oz_rb);
+    size_t oz_part = 0;
+    if (c.emulated) bsolve_ws_rows(R, nmax, &oz_ra, &oz_rb, &oz_part);
+    if (c.emulated) bytes += oz_ws_bytes(oz_ra, oz_rb, oz_part);
     CK(cudaMallocAsync(&c.block, bytes, c.st));
     Arena ar;
     ar.base = (char*)c.block;
@@ -315,7 +316,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
         mixed_ws_carve(c.mx, ar, tf32, s.o, s.v, Rt, R);
         CK(mixed_setup(c.mx, c.st, Xo, Xv, Z));
     }
-    if (c.emulated) oz_ws_carve(c.oz, ar, oz_ra, oz_rb);
+    if (c.emulated) oz_ws_carve(c.oz, ar, oz_ra, oz_rb, oz_part);
     fill(c.st, c.ones, R, 1.0);
     c.dataflow = c.emulated || ldl == THC_CPD_LDL_DATAFLOW ||
                  (ldl == THC_CPD_LDL_AUTO && !(need & NEED_BATCHED));
@@ -1403,8 +1404,9 @@ int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, d
     const bool emu = use_emulated_ldl(ldl, R, n) && !tasks &&
                      oz_prepare(R, n);
     int oz_ra = R + n, oz_rb = R;
-    if (emu) bsolve_ws_rows(R, n, &oz_ra, &oz_rb);
-    size_t bytes = (emu ? oz_ws_bytes(oz_ra, oz_rb) : 0) + Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
+    size_t oz_part = 0;
+    if (emu) bsolve_ws_rows(R, n, &oz_ra, &oz_rb, &oz_part);
+    size_t bytes = (emu ? oz_ws_bytes(oz_ra, oz_rb, oz_part) : 0) + Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
                    Arena::need<double>(std::max(RR, nR)) + Arena::need<double>(R) +
                    Arena::need<int>(flow_sync_ints(R, n)) + Arena::need<int>(bsolve_sync_ints(n)) +
                    Arena::need<DevScalars>(1) + Arena::need<short>(4 * (size_t)std::max(ntasks, 1));
@@ -1432,7 +1434,7 @@ int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, d
     DevScalars* sc = ar.take<DevScalars>(1);
     void* dtasks = ar.take<short>(4 * (size_t)std::max(ntasks, 1));
     OzWs oz;
-    if (emu) oz_ws_carve(oz, ar, oz_ra, oz_rb);
+    if (emu) oz_ws_carve(oz, ar, oz_ra, oz_rb, oz_part);
     CK(cudaMemsetAsync(fsync, 0, sizeof(int) * flow_sync_ints(R, n), st));
     CK(cudaMemsetAsync(bsync, 0, sizeof(int) * bsolve_sync_ints(n), st));
     scalars_init(st, sc, 0.0);

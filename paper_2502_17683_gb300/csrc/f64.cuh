@@ -47,9 +47,9 @@ void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int*
                     const OzWs* oz = nullptr);
 // Raises *rowsA / *rowsB (emulated-product workspace rows, oz_ws_carve) to what the split
 // backward solve of an R x R factor with up to nmax right-hand sides needs to form each
-// coupling product in one launch (all its K chunks' digits at once); with fewer rows the
-// products run chunk by chunk.
-void bsolve_ws_rows(int R, int nmax, int* rowsA, int* rowsB);
+// coupling product in one launch (all its K chunks' digits at once), and *part_doubles to
+// its split-K partial sums; with less the products run chunk by chunk / unsplit.
+void bsolve_ws_rows(int R, int nmax, int* rowsA, int* rowsB, size_t* part_doubles);
 
 // A = M H^-1 for H symmetric positive definite (R x R, lower triangle read) and M (n x R),
 // all device pointers, 1 <= R <= 2048, 1 <= n <= 4096: the solve of thc_cpd_ldl_solve (LDL^T

@@ -632,22 +632,27 @@ void bsolve_block(cudaStream_t st, int R, int c0, int m, int n, double* Haug, do
 }  // namespace
 
 namespace {
-void coupling_rows(int m, int n, long* ra, long* rb) {
+void coupling_rows(int m, int n, long* ra, long* rb, long* part) {
     const int h = bsolve_split_point(m, n);
     if (h == 0) return;
     const long nch = cdiv(m - h, kOzPanel);
     *ra = std::max(*ra, nch * n);
     *rb = std::max(*rb, nch * h);
-    coupling_rows(m - h, n, ra, rb);
-    coupling_rows(h, n, ra, rb);
+    // the K groups oz_gemm_sub forms for an n x h product (128 x 32 tiles)
+    const long tiles = (long)cdiv(n, 128) * cdiv(h, 32);
+    const long groups = std::min<long>(nch, std::max<long>(1, num_sms() / tiles));
+    *part = std::max(*part, (groups - 1) * n * (long)h);
+    coupling_rows(m - h, n, ra, rb, part);
+    coupling_rows(h, n, ra, rb, part);
 }
 }  // namespace
 
-void bsolve_ws_rows(int R, int nmax, int* rowsA, int* rowsB) {
-    long ra = 0, rb = 0;
-    coupling_rows(R, nmax, &ra, &rb);
+void bsolve_ws_rows(int R, int nmax, int* rowsA, int* rowsB, size_t* part_doubles) {
+    long ra = 0, rb = 0, part = 0;
+    coupling_rows(R, nmax, &ra, &rb, &part);
     *rowsA = std::max<long>(*rowsA, ra);
     *rowsB = std::max<long>(*rowsB, rb);
+    *part_doubles = std::max<size_t>(*part_doubles, (size_t)part);
 }
 
 void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int* bs_sync, const OzWs* oz) {

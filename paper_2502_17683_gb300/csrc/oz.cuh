@@ -36,12 +36,16 @@ struct OzWs {
     int* eA = nullptr;
     int* eB = nullptr;
     int rowsA = 0, rowsB = 0;
+    double* part = nullptr;  // split-K partial sums of a product (optional)
+    size_t part_cap = 0;     // doubles at part
 };
 
 // Workspace for left operands of up to rowsA rows and right operands of up to rowsB rows
-// (the LDL^T of an R x R matrix with n appended rows: rowsA = R + n, rowsB = R).
-size_t oz_ws_bytes(int rowsA, int rowsB);
-void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB);
+// (the LDL^T of an R x R matrix with n appended rows: rowsA = R + n, rowsB = R; a product
+// of several K chunks in one launch takes chunks x rows), and part_doubles doubles of
+// split-K partial sums.
+size_t oz_ws_bytes(int rowsA, int rowsB, size_t part_doubles = 0);
+void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB, size_t part_doubles = 0);
 
 // The tensor-core kernels can run on the current device (sm_103, enough shared memory).
 bool oz_available();

@@ -254,6 +254,9 @@ struct UpdArgs {
     int khalves;      // 64-wide K halves that hold data in the last chunk (1 when its K <= 64)
     int nchunks;      // K chunks of KP; chunk c's slices are planes S c .. S c + S - 1 of the maps
     int eA_cs, eB_cs; // offsets between the chunks' exponent rows
+    int kgroups;      // split K: work item (group g, tile) takes chunks [g cpg, (g + 1) cpg); group 0
+    int cpg;          // adds into C, group g > 0 writes its sum to part + (g - 1) mA mB (ld mB)
+    double* part;     // (kgroups > 1 only without E and lower)
 };
 
 // Tile (tm, tn) of the update is skipped when it lies entirely above the diagonal of a
@@ -291,6 +294,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = args.tiles_m * args.tiles_n;
+    const int nwork = ntiles * args.kgroups;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < A_STAGES; ++i) {
@@ -320,10 +324,11 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         // ---- TMA producer ----
         int ia = 0, ib = 0;  // positions in the two rings, over all tiles of this CTA
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+            const int t = w % ntiles, g0 = (w / ntiles) * args.cpg, g1 = min(args.nchunks, g0 + args.cpg);
             int m0, n0;
             if (!tile_active(args, t, m0, n0)) continue;
-            for (int ch = 0; ch < args.nchunks && ok; ++ch) {
+            for (int ch = g0; ch < g1 && ok; ++ch) {
             const int nh = ch == args.nchunks - 1 ? args.khalves : 2;
             for (int c = 0; c < nh && ok; ++c) {
                 const int sb = ib % B_STAGES;
@@ -350,11 +355,12 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         // ---- MMA issuer ----
         int ia = 0, ib = 0, i = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+            const int t = w % ntiles, g0 = (w / ntiles) * args.cpg, g1 = min(args.nchunks, g0 + args.cpg);
             int m0, n0;
             if (!tile_active(args, t, m0, n0)) continue;
             // one accumulator set per (tile, K chunk), alternating
-            for (int ch = 0; ch < args.nchunks && ok; ++ch) {
+            for (int ch = g0; ch < g1 && ok; ++ch) {
             const int nh = ch == args.nchunks - 1 ? args.khalves : 2;
             const int set = i & 1;
             // accumulator set `set` is free once the epilogue has drained tile-chunk i - 2
@@ -399,12 +405,16 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         const int q = warp & 3, h = (warp - 2) >> 2;  // h = 0..3
         const unsigned long long sign_bit = args.sign < 0.0 ? 0x8000000000000000ULL : 0ULL;
         int i = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+            const int t = w % ntiles, grp = w / ntiles, g0 = grp * args.cpg, g1 = min(args.nchunks, g0 + args.cpg);
             int m0, n0;
             if (!tile_active(args, t, m0, n0)) continue;
-            for (int ch = 0; ch < args.nchunks; ++ch) {
-            // chunks after the first add to what the previous one wrote (same thread, same elements)
-            const bool accum = args.accumulate || ch > 0;
+            // group 0 into C, the others into their partial sums
+            double* const cbase = grp == 0 ? args.C : args.part + (size_t)(grp - 1) * args.mA * args.mB;
+            const int cld = grp == 0 ? args.ldc : args.mB;
+            for (int ch = g0; ch < g1; ++ch) {
+            // chunks after the group's first add to what the previous one wrote (same thread, same elements)
+            const bool accum = (grp == 0 && args.accumulate) || ch > g0;
             const int* eBc = args.eB + (size_t)ch * args.eB_cs;
             const int set = i & 1;
             const bool ok = oz_wait(&accfull[set], (i >> 1) & 1, 6);
@@ -412,7 +422,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             const int row = m0 + 32 * q + lane;
             const bool rowok = row < args.mA;
             const int ea = rowok ? args.eA[(size_t)ch * args.eA_cs + row] : 0;
-            double* crow = args.C + (size_t)row * args.ldc;
+            double* crow = cbase + (size_t)row * cld;
             const uint32_t tbase = tmem + (uint32_t)(set * ACC_SET + 8 * h) + ((uint32_t)(32 * q) << 16);
             {
                 uint32_t r[S][8];
@@ -475,6 +485,18 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     }
 }
 
+// C[i][j] += part[0][i][j] + part[1][i][j] + ... (the split-K partial sums, fixed order)
+__global__ void k_oz_add_parts(double* __restrict__ C, int ldc, int M, int N, const double* __restrict__ part,
+                               int nparts) {
+    const long total = (long)M * N;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        double* c = C + (e / N) * (long)ldc + e % N;
+        double v = *c;
+        for (int p = 0; p < nparts; ++p) v += part[p * total + e];
+        *c = v;
+    }
+}
+
 // ---- host ----------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
@@ -527,9 +549,11 @@ void split(cudaStream_t st, const double* src, int ld, int rows, int K, uint16_t
 // read from the right operand's buffers.
 // nchunks > 1: K = KP (nchunks - 1) + kb in one launch, the chunks' slices laid out
 // [chunk][S][mA][KP] and [chunk][S][mB][KP] (exponents [chunk][mA], [chunk][mB]).
+// kgroups > 1 (with nchunks > 1, no E, not lower): the chunks in kgroups groups on separate
+// CTAs, all groups but the first summed in ws.part, then added to C in order.
 cudaError_t update(cudaStream_t st, int mA, int mB, int kb, double* C, int ldc, const OzWs& ws, bool lower,
                    double sign, bool accumulate = true, const double* E = nullptr, bool same_ab = false,
-                   int nchunks = 1) {
+                   int nchunks = 1, int kgroups = 1) {
     if (mA <= 0 || mB <= 0) return cudaSuccess;
     CUtensorMap ma, mb;
     const uint16_t* sa = same_ab ? ws.sB : ws.sA;
@@ -537,36 +561,48 @@ cudaError_t update(cudaStream_t st, int mA, int mB, int kb, double* C, int ldc, 
     const int rb = nchunks > 1 ? mB : ws.rowsB;
     if (!slice_map(&ma, sa, mA, ra, BM, A_DEPTH, S * nchunks) || !slice_map(&mb, ws.sB, mB, rb, BN, S, S * nchunks))
         return cudaErrorInvalidValue;
+    if (kgroups > 1 && (E || lower || nchunks < 2 || !ws.part ||
+                        (size_t)(kgroups - 1) * mA * mB > ws.part_cap))
+        kgroups = 1;
+    const int cpg = cdiv(nchunks, std::max(1, kgroups));
+    kgroups = cdiv(nchunks, cpg);
     UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0,
-              sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1, nchunks, ra, rb};
+              sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1, nchunks, ra, rb, kgroups, cpg, ws.part};
     // persistent: one CTA per SM, at most one per active tile
     long active = 0;
     for (int tm = 0; tm < a.tiles_m; ++tm) {
         const int m0 = tm * BM;
         active += (lower && m0 + BM - 1 < mB) ? std::min<long>(a.tiles_n, (m0 + BM - 1) / BN + 1) : a.tiles_n;
     }
-    const int grid = (int)std::max<long>(1, std::min<long>(active, g_num_sm));
+    const int grid = (int)std::max<long>(1, std::min<long>(active * kgroups, g_num_sm));
     k_oz_update<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, a);
     count_launch();
+    if (kgroups > 1) {
+        k_oz_add_parts<<<(int)std::min<long>(cdiv((long)mA * mB, 256), 4L * g_num_sm), 256, 0, st>>>(
+            C, ldc, mA, mB, ws.part, kgroups - 1);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t oz_ws_bytes(int rowsA, int rowsB) {
+size_t oz_ws_bytes(int rowsA, int rowsB, size_t part_doubles) {
     return Arena::need<uint16_t>((size_t)S * rowsA * KP) + Arena::need<uint16_t>((size_t)S * rowsB * KP) +
-           Arena::need<int>(rowsA) + Arena::need<int>(rowsB);
+           Arena::need<int>(rowsA) + Arena::need<int>(rowsB) + (part_doubles ? Arena::need<double>(part_doubles) : 0);
 }
 
 bool oz_available() { return oz_init(); }
 
-void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB) {
+void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB, size_t part_doubles) {
     w.rowsA = rowsA;
     w.rowsB = rowsB;
     w.sA = ar.take<uint16_t>((size_t)S * w.rowsA * KP);
     w.sB = ar.take<uint16_t>((size_t)S * w.rowsB * KP);
     w.eA = ar.take<int>(w.rowsA);
     w.eB = ar.take<int>(w.rowsB);
+    w.part = part_doubles ? ar.take<double>(part_doubles) : nullptr;
+    w.part_cap = part_doubles;
 }
 
 // Once at most this many columns are left, the rest of the factorisation runs as one
@@ -709,7 +745,11 @@ cudaError_t oz_gemm_sub(cudaStream_t st, int M, int N, int K, const double* A, i
         k_oz_split_t<<<dim3(cdiv(N, SPLIT_T_ROWS), nch), 128 * SPLIT_T_ROWS, 0, st>>>(B, nullptr, ldb, N, 0, K,
                                                                                      ws.sB, N, ws.eB);
         count_launch(2);
-        const cudaError_t e = update(st, M, N, K - KP * (nch - 1), C, ldc, ws, false, -1.0, true, nullptr, false, nch);
+        // split K over CTAs when the tiles alone leave most SMs idle
+        const long tiles = (long)cdiv(M, BM) * cdiv(N, BN);
+        const int groups = (int)std::min<long>(nch, std::max<long>(1, g_num_sm / tiles));
+        const cudaError_t e =
+            update(st, M, N, K - KP * (nch - 1), C, ldc, ws, false, -1.0, true, nullptr, false, nch, groups);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
     for (int k0 = 0; k0 < K; k0 += KP) {

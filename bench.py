@@ -709,7 +709,8 @@ def main():
               ("k_ldl_flow panels of the emulated two-level LDL^T (one launch per 128 columns, one for the last 520)"
                if ldl_path == "emulated" else "blocked LDL^T launches (per mode)"),
               "backward_solve": "k_bsolve_slices", "fp64_gemm": "k_dgemm",
-              "tc_gemm": "k_tc_gemm", "elementwise": "element-wise kernels",
+              "tc_gemm": "k_tc_gemm", "tc_zgemm": "k_tc_gemm (Z contraction)",
+              "elementwise": "element-wise kernels",
               "tc_emulated": "k_oz_split + k_oz_update (emulated FP64 products)"}[dom]
     traffic = None
     if dom == "tc_gemm":
@@ -745,16 +746,26 @@ def main():
             "vs_fp64_probe": useful / f64pk["probe_tflops"],
             "note": "k_oz_split + k_oz_update: Grams and LDL^T trailing updates as exact "
                     "integer-digit products (7 x 7 slices, 28 kept) on the BF16 tensor cores"}
-    tc = prof.get("tc_gemm", {"ms": 0.0})
-    if tc["ms"] > 0:
-        useful = tc["flops"] / (tc["ms"] / 1000.0) / 1e12
+    # the split MTTKRP: projections and back-projections (tc_gemm) and the Z contraction
+    # (tc_zgemm), together and the Z contraction alone
+    tcp = prof.get("tc_gemm", {"ms": 0.0, "flops": 0.0})
+    tcz = prof.get("tc_zgemm", {"ms": 0.0, "flops": 0.0})
+    if tcp["ms"] + tcz["ms"] > 0:
         pk16 = pk["bf16_tflops_sustained"]
         issued_peak = pk16 if precision == "bf16x3" else pk16 * NOMINAL["tf32"] / NOMINAL["bf16"]
+        ms_all, fl_all = tcp["ms"] + tcz["ms"], tcp["flops"] + tcz["flops"]
+        useful = fl_all / (ms_all / 1000.0) / 1e12
         roofline["mttkrp_tensor_core"] = {
             "useful_tflops": useful, "issued_tflops": 3.0 * useful, "peak": issued_peak,
             "frac_issued": 3.0 * useful / issued_peak,
             "peak_source": f"{pk_kind} bf16 sustained" + ("" if precision == "bf16x3" else
                                                           " x nominal tf32/bf16 ratio")}
+        if tcz["ms"] > 0:
+            uz = tcz["flops"] / (tcz["ms"] / 1000.0) / 1e12
+            roofline["mttkrp_tensor_core"]["z_contraction"] = {
+                "useful_tflops": uz, "issued_tflops": 3.0 * uz, "frac_issued": 3.0 * uz / issued_peak,
+                "ms_per_sweep": tcz["ms"] / W["sweeps"],
+                "note": "Y = Z (W o W) on the tensor cores, 2 R_thc^2 R_cp flop per launch, two per sweep"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,

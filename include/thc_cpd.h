@@ -230,9 +230,10 @@ long thc_cpd_launch_count(void);
 /* Per kernel class: summed CUDA-event time of the launch groups, their algorithmic
  * FLOPs and bytes, and the number of groups. Classes: 0 FP64 GEMM, 1 Cholesky
  * (factorisation with the fused forward solve; on the emulated path its FP64 panels),
- * 2 backward solve, 3 element-wise and reduction kernels, 4 split tensor-core GEMM,
- * 5 FP64-accurate emulated products on the tensor cores (digit split and product; FLOPs
- * counted as the FP64 work they replace). */
+ * 2 backward solve, 3 element-wise and reduction kernels, 4 split tensor-core GEMM
+ * (projections and back-projections), 5 FP64-accurate emulated products on the tensor
+ * cores (digit split and product; FLOPs counted as the FP64 work they replace), 6 the
+ * split tensor-core Z contraction of the MTTKRP (Eq. THC's core). */
 typedef struct thc_cpd_kstat {
     double ms;
     double flops;
@@ -245,7 +246,7 @@ typedef struct thc_cpd_kstat {
  * timed runs whose throughput is reported. */
 void thc_cpd_profile(int enable);
 
-/* Fills out[0..min(max_classes,6)) (waits for the recorded events); returns the count
+/* Fills out[0..min(max_classes,7)) (waits for the recorded events); returns the count
  * filled or -1 on a CUDA error. */
 int thc_cpd_profile_read(thc_cpd_kstat* out, int max_classes);
 

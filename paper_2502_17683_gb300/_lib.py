@@ -26,7 +26,8 @@ EXPORTS = ("thc_cpd_thc_norm2", "thc_cpd_mttkrp", "thc_cpd_loss", "thc_cpd_als_s
            "thc_cpd_fp64_fma_rate", "thc_cpd_emulated_gemm", "thc_cpd_exchange",
            "thc_cpd_core_fit", "thc_cpd_df_als", "thc_cpd_nd_mttkrp", "thc_cpd_nd_als")
 MLP_NPARAM = 6849
-KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm", "tc_emulated")
+KCLASS_NAMES = ("fp64_gemm", "cholesky", "backward_solve", "elementwise", "tc_gemm", "tc_emulated",
+                "tc_zgemm")
 
 
 class ThcCpdError(RuntimeError):

@@ -2,6 +2,7 @@
 #include <algorithm>
 
 #include "mixed.cuh"
+#include "prof.cuh"
 
 namespace thc {
 
@@ -92,6 +93,7 @@ cudaError_t mixed_project(MixedWs& mx, cudaStream_t st, int k, const double* Ak,
 
 cudaError_t mixed_zgemm(MixedWs& mx, cudaStream_t st, int half) {
     TcEpilogue ep;
+    ep.prof_class = KC_TCZ;
     ep.out_f32 = mx.Yf;
     ep.ld_f32 = mx.Rt;
     ep.mul = half == 0 ? mx.Wt[1] : mx.Wt[3];

@@ -5,7 +5,7 @@
 
 namespace thc {
 
-enum KClass { KC_DGEMM = 0, KC_CHOL = 1, KC_BSOLVE = 2, KC_AUX = 3, KC_TC = 4, KC_OZ = 5, KC_N = 6 };
+enum KClass { KC_DGEMM = 0, KC_CHOL = 1, KC_BSOLVE = 2, KC_AUX = 3, KC_TC = 4, KC_OZ = 5, KC_TCZ = 6, KC_N = 7 };
 
 void count_launch(int n = 1);
 bool prof_on();

@@ -440,7 +440,7 @@ cudaError_t tc_launch(cudaStream_t st, bool tf32, const SplitMat& A, const Split
                     ? 4
                     : 0);
     const int grid = std::min(args.ntiles, num_sms());  // persistent: at most one CTA per SM
-    ProfScope prof(st, KC_TC, 2.0 * M * (double)N * K);
+    ProfScope prof(st, ep.prof_class, 2.0 * M * (double)N * K);
     count_launch(splits > 1 ? 2 : 1);
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {

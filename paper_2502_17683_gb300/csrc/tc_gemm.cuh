@@ -29,6 +29,7 @@ struct TcEpilogue {
     SplitMat* out_split = nullptr;
     double* out_f64t = nullptr;  // D^T as FP64: out_f64t[n * ld_f64t + m]
     int ld_f64t = 0;
+    int prof_class = 4;          // kernel class of the launch in the profile (KC_TC)
 };
 
 bool tc_available();

@@ -116,18 +116,18 @@ def fp64_peaks(dev, sm_max_mhz):
 
 
 # DRAM bytes per launch of k_ldl_flow (one launch per solve on the dataflow path, one per
-# 128-column panel on the emulated path), keyed by (workload, path), from one ncu capture of
+# panel on the emulated path), keyed by (workload, path), from one ncu capture of
 # one sweep of that workload (all of the sweep's launches averaged; ncu starts every launch
 # from a flushed cache, so this is the cold-cache figure), and the SHA-256 of the kernel's
 # sources (concatenated in this order) it was taken on: reported only while they are
 # unchanged.
 LDL_SOURCES = [os.path.join("paper_2502_17683_gb300", "csrc", f)
-               for f in ("ldl_flow.cu", "ldl_common.cuh", "common.cuh")]
+               for f in ("ldl_flow.cu", "ldl_common.cuh", "common.cuh", "oz_gemm.cu")]
 LDL_TRAFFIC = {
-    # 44 launches of sweep 1: 40 panels and 4 tails
+    # 24 launches of sweep 1: 20 panels of 256 columns and 4 tails
     # (profiles/ldl_flow_panels_o50_v250_Rt1200_R1800_emulated.md)
-    ("c3", "emulated"): {"bytes_per_launch": 1582598,
-                         "sha256": "57c4b1c3f6b6a30ce677f5e61077b862c4fbc7c2d464ae8a9c7cf63a08a3768c"},
+    ("c3", "emulated"): {"bytes_per_launch": 2810539,
+                         "sha256": "4ffe1cf6ff0f5fb0dc9e90215efa7e5fe09e935194a4f3d1199c4e823fa48168"},
 }
 
 
@@ -706,7 +706,7 @@ def main():
     # the LDL^T is one launch per solve on the dataflow path; per launch = per solve
     kernel = {"cholesky": "k_ldl_flow (LDL^T + forward solve, one launch per mode)"
               if ldl_path == "dataflow" else
-              ("k_ldl_flow panels of the emulated two-level LDL^T (one launch per 128 columns, one for the last 520)"
+              ("k_ldl_flow panels of the emulated two-level LDL^T (one launch per 256 columns, one for the last 520)"
                if ldl_path == "emulated" else "blocked LDL^T launches (per mode)"),
               "backward_solve": "k_bsolve_slices", "fp64_gemm": "k_dgemm",
               "tc_gemm": "k_tc_gemm", "tc_zgemm": "k_tc_gemm (Z contraction)",

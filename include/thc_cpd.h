@@ -95,10 +95,11 @@ typedef enum {
     THC_CPD_LDL_AUTO = 0,
     THC_CPD_LDL_BLOCKED = 1,   /* one launch per 32-column block step */
     THC_CPD_LDL_DATAFLOW = 2,  /* one persistent launch (R <= 2048; blocked beyond) */
-    THC_CPD_LDL_EMULATED = 3   /* two-level: 128-column panels by the dataflow kernel, each
+    THC_CPD_LDL_EMULATED = 3   /* two-level: 256-column panels by the dataflow kernel, each
                                   trailing update as an FP64-accurate product on the BF16
                                   tensor cores (exact integer slices, see
-                                  thc_cpd_emulated_gemm); the factorisation stays FP64 in
+                                  thc_cpd_emulated_gemm), the last few hundred columns in
+                                  one dataflow launch; the factorisation stays FP64 in
                                   every value it stores (R <= 4096; dataflow otherwise) */
 } thc_cpd_ldl;
 

@@ -276,6 +276,7 @@ thc_cpd_status ctx_init(Ctx& c, const Shape& s, const double* Xo, const double* 
     int oz_ra = std::max(R + nmax, Rt), oz_rb = R;
     size_t oz_part = 0;
     if (c.emulated) bsolve_ws_rows(R, nmax, &oz_ra, &oz_rb, &oz_part);
+    if (c.emulated) oz_ldl_ws_rows(R, nmax, &oz_ra, &oz_rb);
     if (c.emulated) bytes += oz_ws_bytes(oz_ra, oz_rb, oz_part);
     CK(cudaMallocAsync(&c.block, bytes, c.st));
     Arena ar;
@@ -1406,6 +1407,7 @@ int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, d
     int oz_ra = R + n, oz_rb = R;
     size_t oz_part = 0;
     if (emu) bsolve_ws_rows(R, n, &oz_ra, &oz_rb, &oz_part);
+    if (emu) oz_ldl_ws_rows(R, n, &oz_ra, &oz_rb);
     size_t bytes = (emu ? oz_ws_bytes(oz_ra, oz_rb, oz_part) : 0) + Arena::need<double>(RR + nR) + 3 * Arena::need<double>(RR) + Arena::need<double>(R) +
                    Arena::need<double>(std::max(RR, nR)) + Arena::need<double>(R) +
                    Arena::need<int>(flow_sync_ints(R, n)) + Arena::need<int>(bsolve_sync_ints(n)) +

@@ -47,6 +47,11 @@ struct OzWs {
 size_t oz_ws_bytes(int rowsA, int rowsB, size_t part_doubles = 0);
 void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB, size_t part_doubles = 0);
 
+// Raises *rowsA / *rowsB to the rows the two-level LDL^T of an R x R matrix with up to
+// nmax appended rows needs for its trailing updates when its panels are wider than
+// kOzPanel (all of a panel's chunks split at once).
+void oz_ldl_ws_rows(int R, int nmax, int* rowsA, int* rowsB);
+
 // The tensor-core kernels can run on the current device (sm_103, enough shared memory).
 bool oz_available();
 
@@ -55,7 +60,7 @@ bool oz_available();
 bool oz_prepare(int R, int n);
 
 // Two-level LDL^T of Haug ((R + n) x R, ld R; H in the first R rows, lower triangle read,
-// M in the rest), same result layout as ldl_flow: panels of kOzPanel columns factorised by
+// M in the rest), same result layout as ldl_flow: panels of 2 kOzPanel columns factorised by
 // the dataflow kernel (ldl_flow_panel), each followed by the emulated FP64 trailing update
 //   Haug[i][j] -= sum_{k in panel} L[i][k] D[k] L[j][k]   (j <= i for H rows; all j < R for M rows)
 // of the rows and columns after the panel; the last few hundred columns (oz_gemm.cu,

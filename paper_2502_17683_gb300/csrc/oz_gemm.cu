@@ -160,6 +160,15 @@ k_oz_split_ldl(const double* __restrict__ src, int ld, int mA, int mB, int K,
     __shared__ int sha[4 * SPLIT_ROWS], shb[4 * SPLIT_ROWS];
     const int group = threadIdx.x >> 7, k = threadIdx.x & 127, wig = k >> 5;
     const int r = blockIdx.x * SPLIT_ROWS + group;
+    // K chunk ch = blockIdx.y of a wider panel: its columns, their D, its slices and exponents
+    const int ch = blockIdx.y;
+    src += (size_t)ch * KP;
+    diag += (size_t)ch * KP * (ldd + 1);
+    K -= ch * KP;
+    outA += (size_t)ch * S * rowsA * KP;
+    expsA += (size_t)ch * rowsA;
+    outB += (size_t)ch * S * rowsB * KP;
+    expsB += (size_t)ch * rowsB;
     const bool live = r < mA;
     double a = 0.0, b = 0.0;
     if (live && k < K) {
@@ -424,51 +433,50 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
             const int ea = rowok ? args.eA[(size_t)ch * args.eA_cs + row] : 0;
             double* crow = cbase + (size_t)row * cld;
             const uint32_t tbase = tmem + (uint32_t)(set * ACC_SET + 8 * h) + ((uint32_t)(32 * q) << 16);
-            {
-                uint32_t r[S][8];
+            // two halves of 4 columns; every lane takes part in each tensor-memory load (a
+            // warp-wide instruction), only the arithmetic and the stores are masked per lane
+#pragma unroll 1
+            for (int hh = 0; hh < 2; ++hh) {
+                const int jc = n0 + 8 * h + 4 * hh;
+                uint32_t r[S][4];
 #pragma unroll
-                for (int g = 0; g < S; ++g) tmem_ld8_nowait(tbase + (uint32_t)(g * BN), r[g]);
-                // the row's 8 outputs and the column exponents are fetched while the
-                // tensor-memory loads are in flight
-                double cv[8];
-                int eb[8];
+                for (int g = 0; g < S; ++g) tmem_ld4_nowait(tbase + (uint32_t)(g * BN + 4 * hh), r[g]);
+                double cv[4];
+                int eb[4];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = n0 + 8 * h + jj;
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int j = jc + jj;
                     cv[jj] = (ok && rowok && j < args.mB && accum) ? crow[j] : 0.0;
                     eb[jj] = j < args.mB ? __ldg(eBc + j) : 0;
                 }
                 tmem_ld_wait(r);
-                if (!rowok || !ok) goto done_tile;
-                // the 8 elements side by side, without branches, so that their conversions and
-                // FP64 operations overlap; only the stores are masked
-                double tv[8];
+                if (rowok && ok) {
+                    double tv[4];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    long long acc[S];
+                    for (int jj = 0; jj < 4; ++jj) {
+                        long long acc[S];
 #pragma unroll
-                    for (int g = 0; g < S; ++g) acc[g] = (long long)__float2int_rn(__uint_as_float(r[g][jj]));
-                    // V = sum_g acc_g 2^(8 (S - 1 - g)) = hi 2^32 + lo, exact in 64-bit parts
-                    const long long hi = acc[0] * 65536 + acc[1] * 256 + acc[2];
-                    const long long lo = acc[3] * 16777216 + acc[4] * 65536 + acc[5] * 256 + acc[6];
-                    const int sh = (hi >= (1LL << 29) || hi <= -(1LL << 29)) ? 8 : 0;
-                    // sum_k A_ik B_jk = V 2^(eA_i + eB_j - 14 - 48), times the sign, rounded once
-                    tv[jj] = scaled_i64(hi * (1LL << (32 - sh)) + (lo >> sh), ea + eb[jj] - 62 + sh, sign_bit);
-                }
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = n0 + 8 * h + jj;
-                    double out;
-                    if (args.E) {
-                        const double f = args.E[(size_t)row * args.ldc + min(j, args.mB - 1)];
-                        out = accum ? fma(f, tv[jj], cv[jj]) : f * tv[jj];
-                    } else {
-                        out = accum ? cv[jj] + tv[jj] : tv[jj];
+                        for (int g = 0; g < S; ++g) acc[g] = (long long)__float2int_rn(__uint_as_float(r[g][jj]));
+                        const long long hi = acc[0] * 65536 + acc[1] * 256 + acc[2];
+                        const long long lo = acc[3] * 16777216 + acc[4] * 65536 + acc[5] * 256 + acc[6];
+                        const int sh = (hi >= (1LL << 29) || hi <= -(1LL << 29)) ? 8 : 0;
+                        tv[jj] = scaled_i64(hi * (1LL << (32 - sh)) + (lo >> sh), ea + eb[jj] - 62 + sh, sign_bit);
                     }
-                    if (j < args.mB && !(args.lower && row < args.mB && j > row)) crow[j] = out;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = jc + jj;
+                        double out;
+                        if (args.E) {
+                            const double f = args.E[(size_t)row * args.ldc + min(j, args.mB - 1)];
+                            out = accum ? fma(f, tv[jj], cv[jj]) : f * tv[jj];
+                        } else {
+                            out = accum ? cv[jj] + tv[jj] : tv[jj];
+                        }
+                        if (j < args.mB && !(args.lower && row < args.mB && j > row)) crow[j] = out;
+                    }
                 }
+                __syncwarp();
             }
-        done_tile:
             // every TMEM read of this tile has completed (tcgen05.wait::ld)
             tc_fence_before();
             __syncwarp();
@@ -607,16 +615,31 @@ void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB, size_t part_doubles) 
 
 // Once at most this many columns are left, the rest of the factorisation runs as one
 // dataflow launch (its FP64 trailing updates still hide behind its pivot chain there)
-// instead of further 128-column panels, each followed by a digit split and an update
-// launch that the next panel waits for. Measured on GB300, BF16x3 sweeps/s: 106.9 / 108.5 /
-// 110.1 / 110.1 / 105.7 at R_cp = 1800 for 8 (none) / 264 / 520 / 776 / 1032 columns,
-// 221.9 / 226.5 / 233.7 at R_cp = 1080 for 56 / 312 / 440.
+// instead of further panels, each followed by a digit split and an update launch that the
+// next panel waits for. Measured on GB300 with 128-column panels, BF16x3 sweeps/s: 106.9 /
+// 108.5 / 110.1 / 110.1 / 105.7 at R_cp = 1800 for 8 (none) / 264 / 520 / 776 / 1032
+// columns, 221.9 / 226.5 / 233.7 at R_cp = 1080 for 56 / 312 / 440.
 constexpr int kTailCols = 520;
 
-// Width of the panel that starts at column j0: kOzPanel, or everything left once at most
+// Panels of two K chunks: half as many panel boundaries (digit split and update launch, which
+// the next panel waits for), each update over both chunks in one launch. BF16x3 sweeps/s on
+// GB300: 120.2 / 121.3 / 115.6 at R_cp = 1800 for 128 / 256 / 384 columns (the panel's FP64
+// substitution work outgrows its pivot chain at 384), 235.8 / 238.1 at R_cp = 1080.
+constexpr int kPanelCols = 2 * KP;
+int panel_cols() { return kPanelCols; }
+
+// Width of the panel that starts at column j0: kPanelCols, or everything left once at most
 // kTailCols columns remain.
 int panel_width(int R, int j0) {
-    return R - j0 <= kTailCols ? R - j0 : std::min(KP, R - j0);
+    return R - j0 <= kTailCols ? R - j0 : std::min(panel_cols(), R - j0);
+}
+
+void oz_ldl_ws_rows(int R, int nmax, int* rowsA, int* rowsB) {
+    const int pc = std::min(panel_cols(), R);
+    const long nch = cdiv(pc, KP);
+    if (nch < 2 || R - pc <= 0) return;
+    *rowsA = (int)std::max<long>(*rowsA, nch * (R + nmax - pc));
+    *rowsB = (int)std::max<long>(*rowsB, nch * (R - pc));
 }
 
 bool oz_prepare(int R, int n) {
@@ -647,10 +670,24 @@ cudaError_t ldl_oz(cudaStream_t st, int R, int n, double* Haug, double* P, doubl
         const double* diag = Haug + (size_t)j0 * R + j0;
         {
             ProfScope prof(st, KC_OZ, (double)mB * (mB + 1) * bw + 2.0 * (mA - mB) * mB * bw);
-            k_oz_split_ldl<<<cdiv(mA, SPLIT_ROWS), 128 * SPLIT_ROWS, 0, st>>>(below, R, mA, mB, bw, diag, R, ws.sA,
-                                                                           ws.rowsA, ws.eA, ws.sB, ws.rowsB, ws.eB);
-            count_launch();
-            e = update(st, mA, mB, bw, Haug + (size_t)j1 * R + j1, R, ws, true, -1.0);
+            const int nch = cdiv(bw, KP);
+            if (nch > 1 && (long)nch * mA <= ws.rowsA && (long)nch * mB <= ws.rowsB) {
+                // a wider panel: all its chunks split at once, one update launch over them
+                k_oz_split_ldl<<<dim3(cdiv(mA, SPLIT_ROWS), nch), 128 * SPLIT_ROWS, 0, st>>>(
+                    below, R, mA, mB, bw, diag, R, ws.sA, mA, ws.eA, ws.sB, mB, ws.eB);
+                count_launch();
+                e = update(st, mA, mB, bw - KP * (nch - 1), Haug + (size_t)j1 * R + j1, R, ws, true, -1.0, true,
+                           nullptr, false, nch);
+            } else {
+                for (int k0 = 0; k0 < bw && e == cudaSuccess; k0 += KP) {
+                    const int kb = std::min(KP, bw - k0);
+                    k_oz_split_ldl<<<cdiv(mA, SPLIT_ROWS), 128 * SPLIT_ROWS, 0, st>>>(
+                        below + k0, R, mA, mB, kb, diag + (size_t)k0 * (R + 1), R, ws.sA, ws.rowsA, ws.eA, ws.sB,
+                        ws.rowsB, ws.eB);
+                    count_launch();
+                    e = update(st, mA, mB, kb, Haug + (size_t)j1 * R + j1, R, ws, true, -1.0);
+                }
+            }
         }
         if (e != cudaSuccess) return e;
     }

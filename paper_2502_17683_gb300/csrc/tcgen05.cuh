@@ -123,6 +123,12 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
         : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+
 template <int N, int C>
 __device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[N][C]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");

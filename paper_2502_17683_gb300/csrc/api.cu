@@ -443,6 +443,7 @@ void refresh_state(Ctx& c, const double* const A[4]) {
 // One mode update. M_k is formed in the Haug rows; returns with A[k], lam, G_k, W_k new.
 thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool safe,
                            int* used_pinv) {
+    NvtxRange nvtx_range("thc_cpd mode update");
     const int R = c.s.R, n = c.s.n[k];
     double* Mrows = c.Haug + (size_t)R * R;
     if (c.prec == THC_CPD_FP64)
@@ -485,6 +486,7 @@ thc_cpd_status mode_update(Ctx& c, double* const A[4], double* lam, int k, bool 
 // One sweep over modes 0..3 (+ the FP64 loss when eval_loss).
 thc_cpd_status sweep(Ctx& c, double* const A[4], double* lam, bool safe, bool eval_loss,
                      double tol, int* used_pinv) {
+    NvtxRange nvtx_range("thc_cpd sweep");
     for (int k = 0; k < 4; ++k) {
         if (k == 0 || k == 2) {
             if (c.prec == THC_CPD_FP64)
@@ -513,6 +515,7 @@ thc_cpd_status sweep(Ctx& c, double* const A[4], double* lam, bool safe, bool ev
 // ordered after / before the caller's stream with events.
 thc_cpd_status fast_sweep(Ctx& c, double* const A[4], double* lam, bool eval, double tol,
                           bool* use_graph) {
+    NvtxRange nvtx_range("thc_cpd sweep (graph)");
     if (*use_graph) {
         const int gi = eval ? 1 : 0;
         if (c.gexec[gi] && c.gprec[gi] != c.prec) {
@@ -729,6 +732,7 @@ thc_cpd_status run_als(int o, int v, int Rt, int R, const double* Xo, const doub
                        const double* Z, double* const A[4], double* lam, int max_sweeps,
                        double tol, double normG2, int* sweeps_done, double* loss_host,
                        double* fit_host, thc_cpd_opts* opts, LearnArgs* la = nullptr) {
+    NvtxRange nvtx_range("thc_cpd_als");
     Shape s;
     CKS(check_shape(o, v, Rt, R, &s));
     CKS(check_ptrs(Xo, Xv, Z, A));
@@ -1225,6 +1229,7 @@ thc_cpd_status thc_cpd_thc_norm2(int o, int v, int Rt, const double* Xo, const d
 thc_cpd_status thc_cpd_mttkrp(int o, int v, int Rt, int R, const double* Xo, const double* Xv,
                               const double* Z, const double* const A[4], int mode, double* M,
                               const thc_cpd_opts* opts) {
+    NvtxRange nvtx_range("thc_cpd_mttkrp");
     Shape s;
     CKS((thc_cpd_status)check_mttkrp_args(o, v, Rt, R, Xo, Xv, Z, A, mode, M));
     CKS(check_shape(o, v, Rt, R, &s));
@@ -1301,6 +1306,7 @@ thc_cpd_status thc_cpd_loss(int o, int v, int Rt, int R, const double* Xo, const
                             const double* Z, const double* const A[4], const double* lam,
                             double normG2, double* loss_host, double* fit_host,
                             const thc_cpd_opts* opts) {
+    NvtxRange nvtx_range("thc_cpd_loss");
     Shape s;
     CKS(check_shape(o, v, Rt, R, &s));
     CKS(check_ptrs(Xo, Xv, Z, A));
@@ -1476,6 +1482,7 @@ int spd_solve(cudaStream_t st, int R, int n, const double* H, const double* M, d
 thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M, double* A,
                                  const short* tasks, int ntasks, int* used_pinv,
                                  const thc_cpd_opts* opts) {
+    NvtxRange nvtx_range("thc_cpd_ldl_solve");
     if (R < 1 || R > 2048 || n < 1 || n > 4096)
         return set_err(THC_CPD_ERR_SHAPE, "need 1 <= R <= 2048 and 1 <= n <= 4096 (R=%d n=%d)", R, n);
     if (!H || !M || !A) return set_err(THC_CPD_ERR_ARG, "H, M and A must be non-null");
@@ -1491,5 +1498,6 @@ thc_cpd_status thc_cpd_ldl_solve(int R, int n, const double* H, const double* M,
 
 thc_cpd_status thc_cpd_als_batched(int nprob, thc_cpd_problem* probs, int max_sweeps,
                                               double tol, thc_cpd_opts* opts) {
+    NvtxRange nvtx_range("thc_cpd_als_batched");
     return run_batched(nprob, probs, max_sweeps, tol, opts);
 }

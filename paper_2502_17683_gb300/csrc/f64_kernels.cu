@@ -580,6 +580,7 @@ int bsolve_split_point(int m, int n) {
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,
                 DevScalars* sc, int mode, int* counters, int* flow_sync, int flow_ctas,
                 int* bs_sync, const OzWs* oz) {
+    NvtxRange nvtx_range("thc_cpd LDL^T and solve");
     const int nrows = R + n;
     const int nJ = cdiv(R, NB);
     if (oz && flow_sync) {
@@ -656,6 +657,7 @@ void bsolve_ws_rows(int R, int nmax, int* rowsA, int* rowsB, size_t* part_double
 }
 
 void backward_solve(cudaStream_t st, int R, int n, double* Haug, double* A, int* bs_sync, const OzWs* oz) {
+    NvtxRange nvtx_range("thc_cpd backward solve");
     if (n <= 0) return;
     // A = [A1 A2], L = [L11 0; L21 L22]: A2 L22 = Y2, then A1 L11 = Y1 - A2 L21 with the
     // coupling term (half of the block's flops) as an emulated tensor-core product, each

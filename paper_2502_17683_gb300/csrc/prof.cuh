@@ -2,6 +2,7 @@
 // reporting). Timing is off unless thc_cpd_profile(1) was called.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace thc {
 
@@ -18,6 +19,15 @@ struct ProfScope {
     cudaEvent_t e0 = nullptr;
     ProfScope(cudaStream_t s, int c, double f, double b = 0.0);
     ~ProfScope();
+};
+
+// A named range on the host timeline (NVTX v3, header-only): shown by profilers that record
+// NVTX (nsys timelines, ncu's --nvtx-include filters), a no-op when none is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 }  // namespace thc

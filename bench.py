@@ -127,7 +127,7 @@ LDL_TRAFFIC = {
     # 24 launches of sweep 1: 20 panels of 256 columns and 4 tails
     # (profiles/ldl_flow_panels_o50_v250_Rt1200_R1800_emulated.md)
     ("c3", "emulated"): {"bytes_per_launch": 2810539,
-                         "sha256": "4ffe1cf6ff0f5fb0dc9e90215efa7e5fe09e935194a4f3d1199c4e823fa48168"},
+                         "sha256": "d4fe1f7983a34ebc9d52ed87a80a50247ec709071fc7e27f586c614579620be6"},
 }
 
 

@@ -95,7 +95,7 @@ typedef enum {
     THC_CPD_LDL_AUTO = 0,
     THC_CPD_LDL_BLOCKED = 1,   /* one launch per 32-column block step */
     THC_CPD_LDL_DATAFLOW = 2,  /* one persistent launch (R <= 2048; blocked beyond) */
-    THC_CPD_LDL_EMULATED = 3   /* two-level: 256-column panels by the dataflow kernel, each
+    THC_CPD_LDL_EMULATED = 3   /* two-level: 256-column panels (128 below R = 1536) by the dataflow kernel, each
                                   trailing update as an FP64-accurate product on the BF16
                                   tensor cores (exact integer slices, see
                                   thc_cpd_emulated_gemm), the last few hundred columns in

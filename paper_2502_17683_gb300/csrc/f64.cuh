@@ -33,7 +33,7 @@ void hadamard3(cudaStream_t st, int R, const double* Ga, const double* Gb, const
 //   with only the shared memory they use (problems running side by side).
 //   bs_sync: bsolve_sync_ints(n) ints, the progress counters of the backward solve (by
 //   column slices, ldl_flow.cu); zero before the first use, left zero by each launch.
-//   oz: with it (and flow_sync) the factorisation runs in 256-column panels with emulated
+//   oz: with it (and flow_sync) the factorisation runs in 256- (below R = 1536: 128-) column panels with emulated
 //   FP64 tensor-core trailing updates (ldl_oz, oz.cuh).
 struct OzWs;
 void chol_solve(cudaStream_t st, int R, int n, double* Haug, double* A, double* P, double* dinv,

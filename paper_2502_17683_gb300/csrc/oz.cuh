@@ -60,7 +60,7 @@ bool oz_available();
 bool oz_prepare(int R, int n);
 
 // Two-level LDL^T of Haug ((R + n) x R, ld R; H in the first R rows, lower triangle read,
-// M in the rest), same result layout as ldl_flow: panels of 2 kOzPanel columns factorised by
+// M in the rest), same result layout as ldl_flow: panels of 2 kOzPanel columns (kOzPanel below R = 1536) factorised by
 // the dataflow kernel (ldl_flow_panel), each followed by the emulated FP64 trailing update
 //   Haug[i][j] -= sum_{k in panel} L[i][k] D[k] L[j][k]   (j <= i for H rows; all j < R for M rows)
 // of the rows and columns after the panel; the last few hundred columns (oz_gemm.cu,

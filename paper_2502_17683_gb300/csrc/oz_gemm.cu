@@ -621,21 +621,24 @@ void oz_ws_carve(OzWs& w, Arena& ar, int rowsA, int rowsB, size_t part_doubles) 
 // columns, 221.9 / 226.5 / 233.7 at R_cp = 1080 for 56 / 312 / 440.
 constexpr int kTailCols = 520;
 
-// Panels of two K chunks: half as many panel boundaries (digit split and update launch, which
-// the next panel waits for), each update over both chunks in one launch. BF16x3 sweeps/s on
-// GB300: 120.2 / 121.3 / 115.6 at R_cp = 1800 for 128 / 256 / 384 columns (the panel's FP64
-// substitution work outgrows its pivot chain at 384), 235.8 / 238.1 at R_cp = 1080.
-constexpr int kPanelCols = 2 * KP;
-int panel_cols() { return kPanelCols; }
+// From R = 1536, panels of two K chunks: half as many panel boundaries (digit split and
+// update launch, which the next panel waits for), each update over both chunks in one
+// launch. BF16x3 sweeps/s on GB300: 120.2 / 121.3 / 115.6 at R_cp = 1800 for 128 / 256 / 384
+// columns (the panel's FP64 substitution work outgrows its pivot chain at 384), 235.8 /
+// 238.1 at R_cp = 1080; but the 64-problem batch (R_cp <= 1440, panels on at most 32 CTAs
+// beside the other problems, where that FP64 work is no longer hidden) took 3.86 s with
+// 256 against 3.73 s with 128. The width depends on R alone, so a problem factorises the
+// same way (same bits) in the batched driver and alone.
+int panel_cols(int R) { return R >= 1536 ? 2 * KP : KP; }
 
-// Width of the panel that starts at column j0: kPanelCols, or everything left once at most
-// kTailCols columns remain.
+// Width of the panel that starts at column j0: panel_cols(R), or everything left once at
+// most kTailCols columns remain.
 int panel_width(int R, int j0) {
-    return R - j0 <= kTailCols ? R - j0 : std::min(panel_cols(), R - j0);
+    return R - j0 <= kTailCols ? R - j0 : std::min(panel_cols(R), R - j0);
 }
 
 void oz_ldl_ws_rows(int R, int nmax, int* rowsA, int* rowsB) {
-    const int pc = std::min(panel_cols(), R);
+    const int pc = std::min(panel_cols(R), R);
     const long nch = cdiv(pc, KP);
     if (nch < 2 || R - pc <= 0) return;
     *rowsA = (int)std::max<long>(*rowsA, nch * (R + nmax - pc));

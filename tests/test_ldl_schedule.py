@@ -44,8 +44,11 @@ def _expected(R, n):
     return s
 
 
+# ... and the shapes the emulated factorisation launches at R_cp = 1800: 256-column panels over
+# the rows below them (up to 1794 with n = 250), 128-column ones, and the 520-column tail
 @pytest.mark.parametrize("R,n", [(720, 20), (720, 100), (80, 5), (17, 1), (16, 3), (5, 4),
-                                 (33, 40), (144, 20), (100, 0), (31, 33), (1800, 250)])
+                                 (33, 40), (144, 20), (100, 0), (31, 33), (1800, 250),
+                                 (256, 1794), (128, 1922), (520, 250), (520, 50)])
 def test_schedule_complete_and_ordered(api, R, n):
     tasks = api.thc_cpd_ldl_schedule(R, n)
     nT, nM = _tiles(R, n)

@@ -127,7 +127,7 @@ LDL_TRAFFIC = {
     # 24 launches of sweep 1: 20 panels of 256 columns and 4 tails
     # (profiles/ldl_flow_panels_o50_v250_Rt1200_R1800_emulated.md)
     ("c3", "emulated"): {"bytes_per_launch": 2810539,
-                         "sha256": "d4fe1f7983a34ebc9d52ed87a80a50247ec709071fc7e27f586c614579620be6"},
+                         "sha256": "d500c1bb36ad00280917f668ba7225549564f3851c6883c992b128115fc96ff4"},
 }
 
 

@@ -576,7 +576,7 @@ cudaError_t update(cudaStream_t st, int mA, int mB, int kb, double* C, int ldc, 
     kgroups = cdiv(nchunks, cpg);
     UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0,
               sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1, nchunks, ra, rb, kgroups, cpg, ws.part};
-    // persistent: one CTA per SM, at most one per active tile
+    // persistent: one CTA per SM, at most one per active (tile, K group) work item
     long active = 0;
     for (int tm = 0; tm < a.tiles_m; ++tm) {
         const int m0 = tm * BM;

@@ -263,17 +263,30 @@ struct UpdArgs {
     int khalves;      // 64-wide K halves that hold data in the last chunk (1 when its K <= 64)
     int nchunks;      // K chunks of KP; chunk c's slices are planes S c .. S c + S - 1 of the maps
     int eA_cs, eB_cs; // offsets between the chunks' exponent rows
+    int nactive;      // active tiles (tile_of's index range)
     int kgroups;      // split K: work item (group g, tile) takes chunks [g cpg, (g + 1) cpg); group 0
     int cpg;          // adds into C, group g > 0 writes its sum to part + (g - 1) mA mB (ld mB)
     double* part;     // (kgroups > 1 only without E and lower)
 };
 
-// Tile (tm, tn) of the update is skipped when it lies entirely above the diagonal of a
-// lower-only (symmetric or LDL^T trailing) block.
-__device__ __forceinline__ bool tile_active(const UpdArgs& a, int t, int& m0, int& n0) {
-    m0 = (t / a.tiles_n) * BM;
-    n0 = (t % a.tiles_n) * BN;
-    return !(a.lower && m0 + BM - 1 < a.mB && n0 > m0 + BM - 1);
+// Active tiles of row block tm: on a lower-only (symmetric or LDL^T trailing) block, rows
+// that lie within the first mB stop at the diagonal; below them every tile is active.
+__host__ __device__ __forceinline__ int row_tiles(int tm, int tiles_n, int mB, bool lower) {
+    const int m0 = tm * BM;
+    return (lower && m0 + BM - 1 < mB) ? min(tiles_n, (m0 + BM - 1) / BN + 1) : tiles_n;
+}
+
+// The active tile of compact index u (row by row, so that the CTAs' shares of a lower block
+// differ by at most one tile; tiles above the diagonal are never handed out).
+__device__ __forceinline__ void tile_of(const UpdArgs& a, int u, int& m0, int& n0) {
+    int tm = 0;
+    for (;; ++tm) {
+        const int c = row_tiles(tm, a.tiles_n, a.mB, a.lower != 0);
+        if (u < c || tm == a.tiles_m - 1) break;
+        u -= c;
+    }
+    m0 = tm * BM;
+    n0 = u * BN;
 }
 
 // C (+)= sign * E o (A B^T) from the digit slices, one 128 x 32 output tile at a time, each
@@ -302,7 +315,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
     uint64_t* accempty = accfull + 2;                   // [2]
     uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = args.tiles_m * args.tiles_n;
+    const int ntiles = args.nactive;
     const int nwork = ntiles * args.kgroups;
 
     if (threadIdx.x == 0) {
@@ -336,7 +349,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
             const int t = w % ntiles, g0 = (w / ntiles) * args.cpg, g1 = min(args.nchunks, g0 + args.cpg);
             int m0, n0;
-            if (!tile_active(args, t, m0, n0)) continue;
+            tile_of(args, t, m0, n0);
             for (int ch = g0; ch < g1 && ok; ++ch) {
             const int nh = ch == args.nchunks - 1 ? args.khalves : 2;
             for (int c = 0; c < nh && ok; ++c) {
@@ -367,7 +380,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
             const int t = w % ntiles, g0 = (w / ntiles) * args.cpg, g1 = min(args.nchunks, g0 + args.cpg);
             int m0, n0;
-            if (!tile_active(args, t, m0, n0)) continue;
+            tile_of(args, t, m0, n0);
             // one accumulator set per (tile, K chunk), alternating
             for (int ch = g0; ch < g1 && ok; ++ch) {
             const int nh = ch == args.nchunks - 1 ? args.khalves : 2;
@@ -417,7 +430,7 @@ k_oz_update(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
         for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
             const int t = w % ntiles, grp = w / ntiles, g0 = grp * args.cpg, g1 = min(args.nchunks, g0 + args.cpg);
             int m0, n0;
-            if (!tile_active(args, t, m0, n0)) continue;
+            tile_of(args, t, m0, n0);
             // group 0 into C, the others into their partial sums
             double* const cbase = grp == 0 ? args.C : args.part + (size_t)(grp - 1) * args.mA * args.mB;
             const int cld = grp == 0 ? args.ldc : args.mB;
@@ -574,14 +587,12 @@ cudaError_t update(cudaStream_t st, int mA, int mB, int kb, double* C, int ldc, 
         kgroups = 1;
     const int cpg = cdiv(nchunks, std::max(1, kgroups));
     kgroups = cdiv(nchunks, cpg);
-    UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, cdiv(mA, BM), cdiv(mB, BN), lower ? 1 : 0,
-              sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1, nchunks, ra, rb, kgroups, cpg, ws.part};
-    // persistent: one CTA per SM, at most one per active (tile, K group) work item
+    const int tiles_m = cdiv(mA, BM), tiles_n = cdiv(mB, BN);
     long active = 0;
-    for (int tm = 0; tm < a.tiles_m; ++tm) {
-        const int m0 = tm * BM;
-        active += (lower && m0 + BM - 1 < mB) ? std::min<long>(a.tiles_n, (m0 + BM - 1) / BN + 1) : a.tiles_n;
-    }
+    for (int tm = 0; tm < tiles_m; ++tm) active += row_tiles(tm, tiles_n, mB, lower);
+    UpdArgs a{C, ldc, mA, mB, same_ab ? ws.eB : ws.eA, ws.eB, tiles_m, tiles_n, lower ? 1 : 0,
+              sign, accumulate ? 1 : 0, E, kb > 64 ? 2 : 1, nchunks, ra, rb, (int)active, kgroups, cpg, ws.part};
+    // persistent: one CTA per SM, at most one per active (tile, K group) work item
     const int grid = (int)std::max<long>(1, std::min<long>(active * kgroups, g_num_sm));
     k_oz_update<<<grid, NTHREADS, SMEM_BYTES, st>>>(ma, mb, a);
     count_launch();

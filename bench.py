@@ -127,7 +127,7 @@ LDL_TRAFFIC = {
     # 24 launches of sweep 1: 20 panels of 256 columns and 4 tails
     # (profiles/ldl_flow_panels_o50_v250_Rt1200_R1800_emulated.md)
     ("c3", "emulated"): {"bytes_per_launch": 2810539,
-                         "sha256": "d500c1bb36ad00280917f668ba7225549564f3851c6883c992b128115fc96ff4"},
+                         "sha256": "d4600829b64cd367ddca378d58a8afd98a7b436117a55d9636a58fae6d451452"},
 }
 
 

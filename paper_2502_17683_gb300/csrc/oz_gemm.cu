@@ -277,16 +277,25 @@ __host__ __device__ __forceinline__ int row_tiles(int tm, int tiles_n, int mB, b
 }
 
 // The active tile of compact index u (row by row, so that the CTAs' shares of a lower block
-// differ by at most one tile; tiles above the diagonal are never handed out).
+// differ by at most one tile; tiles above the diagonal are never handed out). Only the rows
+// of a lower block that end within its first mB columns (at most mB / BM of them) have
+// fewer tiles than tiles_n; they are walked, every later row is full.
 __device__ __forceinline__ void tile_of(const UpdArgs& a, int u, int& m0, int& n0) {
     int tm = 0;
-    for (;; ++tm) {
-        const int c = row_tiles(tm, a.tiles_n, a.mB, a.lower != 0);
-        if (u < c || tm == a.tiles_m - 1) break;
-        u -= c;
+    if (a.lower) {
+        for (; tm < a.tiles_m && tm * BM + BM - 1 < a.mB; ++tm) {
+            const int c = row_tiles(tm, a.tiles_n, a.mB, true);
+            if (u < c) {
+                m0 = tm * BM;
+                n0 = u * BN;
+                return;
+            }
+            u -= c;
+        }
     }
+    tm += u / a.tiles_n;
     m0 = tm * BM;
-    n0 = u * BN;
+    n0 = (u % a.tiles_n) * BN;
 }
 
 // C (+)= sign * E o (A B^T) from the digit slices, one 128 x 32 output tile at a time, each
